@@ -1,0 +1,437 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: published
+known-answer vectors, exhaustive enumeration, closed forms, invariants, exact
+Boltzmann distributions, or an independent high-precision evaluation.  None of
+them retypes the oracle's own formula.
+"""
+import decimal
+import itertools
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+from oracle import oracle as o
+from paper_2501_17267_gb300 import workloads as wl
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------- RNG
+
+def test_philox_known_answers():
+    """Philox4x32-10 against the Random123 known-answer vectors (SC'11 reference)."""
+    n = 0
+    with open(os.path.join(GOLDEN, "philox4x32_10_kat.txt")) as f:
+        for line in f:
+            if line.startswith("#") or not line.strip():
+                continue
+            v = [int(t, 16) for t in line.split()]
+            out = o.philox(v[0:4], v[4:6])
+            assert list(out) == v[6:10]
+            n += 1
+    assert n == 3
+
+
+def test_init_spins_are_balanced():
+    N, R = 4096, 8
+    s = np.array([[o.init_spin(7, 3, i, r) for i in range(N)] for r in range(R)])
+    assert set(np.unique(s)) == {-1, 1}
+    frac = (s == 1).mean()
+    assert abs(frac - 0.5) < 5 * math.sqrt(0.25 / s.size)
+    # replicas differ from one another (distinct Philox words)
+    assert not np.array_equal(s[0], s[1])
+
+
+# --------------------------------------------------------------------------- cube geometry
+
+def test_cube_edges_are_the_twelve_unit_edges():
+    edges = {tuple(sorted(o.cube_edge(e))) for e in range(12)}
+    assert len(edges) == 12
+    for u, v in edges:
+        assert bin(u ^ v).count("1") == 1  # differ in exactly one coordinate
+    every = {(u, v) for u in range(8) for v in range(u + 1, 8) if bin(u ^ v).count("1") == 1}
+    assert edges == every
+
+
+def test_cube_symmetries_form_the_octahedral_group():
+    maps = set()
+    adj = {(u, v) for u in range(8) for v in range(8) if bin(u ^ v).count("1") == 1}
+    for g in range(48):
+        m = tuple(o.cube_symmetry(g, c) for c in range(8))
+        assert sorted(m) == list(range(8))
+        assert {(m[u], m[v]) for u, v in adj} == adj  # adjacency preserved
+        maps.add(m)
+    assert len(maps) == 48  # all distinct: the full symmetry group of the cube
+
+
+def _faces():
+    """Six faces as sets of edge indices, derived here from corner coordinates."""
+    faces = []
+    for axis in range(3):
+        for val in (0, 1):
+            es = []
+            for e in range(12):
+                u, v = o.cube_edge(e)
+                if ((u >> axis) & 1) == val and ((v >> axis) & 1) == val:
+                    es.append(e)
+            assert len(es) == 4
+            faces.append((axis, val, es))
+    return faces
+
+
+@pytest.mark.parametrize("cls,nfrus,emin,deg", [
+    (o.CLASS_F22, 2, -10, 2),  # one unsatisfiable edge -> -12 + 2*1
+    (o.CLASS_F42, 4, -8, 4),   # two -> -12 + 2*2
+    (o.CLASS_F6, 6, -6, 16),   # three -> -12 + 2*3
+])
+def test_tile_classes(cls, nfrus, emin, deg):
+    """Class = set of frustrated faces (Sec. II tile classes read as F22/F42/F6).
+
+    A face is frustrated iff the product of its four couplings is negative; with
+    |J| = 1 the minimum energy is -12 + 2 m, m the fewest edges whose removal
+    unfrustrates every face (1, 2, 3 for these patterns)."""
+    J = o.tile_template(cls)
+    assert set(np.abs(J)) == {1}
+    frus = [(a, v) for a, v, es in _faces() if np.prod(J[es].astype(int)) < 0]
+    assert len(frus) == nfrus
+    if cls == o.CLASS_F22:
+        assert frus[0][0] != frus[1][0]  # the two faces are adjacent (different axes)
+    if cls == o.CLASS_F42:
+        unf = [(a, v) for a, v, es in _faces() if (a, v) not in frus]
+        assert unf[0][0] == unf[1][0]  # the two unfrustrated faces are opposite
+    e, d = o.tile_bruteforce(J)
+    assert (e, d) == (emin, deg)
+    # brute force independent of the oracle's enumerator
+    best = min(_tile_energy_py(J, st) for st in range(256))
+    assert best == emin
+    # the all-+1 corner state is a ground state of the template (planted state)
+    assert o.tile_energy(J, 0) == emin
+
+
+def _tile_energy_py(J, st):
+    E = 0
+    for e in range(12):
+        u, v = o.cube_edge(e)
+        E += int(J[e]) * (1 - 2 * ((st >> u) & 1)) * (1 - 2 * ((st >> v) & 1))
+    return E
+
+
+def test_symmetry_preserves_class():
+    for cls in range(3):
+        J = o.tile_template(cls)
+        e0 = o.tile_bruteforce(J)
+        for g in range(48):
+            # the mapped tile as a coupling list on canonical edges
+            Jg = np.zeros(12, dtype=np.int8)
+            idx = {tuple(sorted(o.cube_edge(e))): e for e in range(12)}
+            for e in range(12):
+                u, v = o.cube_edge(e)
+                gu, gv = o.cube_symmetry(g, u), o.cube_symmetry(g, v)
+                Jg[idx[tuple(sorted((gu, gv)))]] = J[e]
+            assert o.tile_bruteforce(Jg) == e0
+
+
+# --------------------------------------------------------------------------- tiles partition
+
+@pytest.mark.parametrize("L", [2, 4, 6])
+def test_tiles_partition_the_edges(L):
+    """Unit cubes at all-even and all-odd origins cover every lattice edge once."""
+    N = L ** 3
+    count = np.zeros((N, 3), dtype=int)
+    origins = [(a, b, c) for a in range(0, L, 2) for b in range(0, L, 2) for c in range(0, L, 2)]
+    origins += [(a + 1, b + 1, c + 1) for a, b, c in origins]
+    assert len(origins) == N // 4
+    for ox, oy, oz in origins:
+        for dx, dy, dz in itertools.product((0, 1), repeat=3):
+            x, y, z = (ox + dx) % L, (oy + dy) % L, (oz + dz) % L
+            i = x + L * (y + L * z)
+            for d, inside in enumerate((dx == 0, dy == 0, dz == 0)):
+                if inside:
+                    count[i, d] += 1
+    assert (count == 1).all()
+
+
+# --------------------------------------------------------------------------- instances
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+@pytest.mark.parametrize("cp", [wl.UNIFORM, (0, 0, 1), (1, 0, 0), (0.2, 0, 0.8)])
+def test_l2_exhaustive_ground_state(seed, cp):
+    """L=2: all 2^8 global states; the minimum equals E_gs and the planted state reaches it."""
+    J3, tau, egs = o.generate(2, seed, cp, gauge=True)
+    energies = []
+    for st in range(256):
+        s = np.array([1 - 2 * ((st >> i) & 1) for i in range(8)], dtype=np.int8)
+        energies.append(o.energy(2, J3, s))
+    assert min(energies) == egs
+    assert o.energy(2, J3, tau) == egs
+
+
+@pytest.mark.parametrize("L", [4, 6, 10])
+def test_planted_state_reaches_egs_and_bounds(L):
+    J3, tau, egs = o.generate(L, 11 + L, wl.UNIFORM, gauge=True)
+    assert o.energy(L, J3, tau) == egs
+    assert egs < 0
+    assert set(np.unique(J3)) <= {-1, 1}
+    for k in range(20):
+        s = wl.random_spins(100 + k, L ** 3)
+        assert o.energy(L, J3, s) >= egs
+
+
+def test_egs_is_sum_of_tile_minima():
+    """Without gauge the planted state is all +1 and E_gs = sum of tile minima,
+    so E_gs/tiles lies between the F6 minimum (-6) and the F22 minimum (-10)."""
+    L = 8
+    for cp, per_tile in [((1, 0, 0), -10), ((0, 1, 0), -8), ((0, 0, 1), -6)]:
+        J3, tau, egs = o.generate(L, 5, cp, gauge=False)
+        assert (tau == 1).all()
+        assert egs == per_tile * (L ** 3 // 4)
+        assert o.energy(L, J3, np.ones(L ** 3, np.int8)) == egs
+
+
+def test_class_frequencies():
+    """Uniform class draw: per-tile energy mean = (-10-8-6)/3 = -8."""
+    L = 16
+    J3, tau, egs = o.generate(L, 99, wl.UNIFORM, gauge=False)
+    ntiles = L ** 3 // 4
+    # each tile minimum is -10, -8 or -6 -> E_gs = -8 ntiles + fluctuation
+    sd = math.sqrt(ntiles * (4 + 0 + 4) / 3)
+    assert abs(egs + 8 * ntiles) < 5 * sd
+
+
+def test_gauge_invariance():
+    """Gauge scrambling: J' = J tau_i tau_j and E_J'(s tau) = E_J(s)."""
+    L = 6
+    J_plain, _, egs0 = o.generate(L, 42, wl.UNIFORM, gauge=False)
+    J_g, tau, egs1 = o.generate(L, 42, wl.UNIFORM, gauge=True)
+    assert egs0 == egs1
+    assert (tau == -1).any() and (tau == 1).any()
+    for k in range(10):
+        s = wl.random_spins(k, L ** 3)
+        assert o.energy(L, J_g, (s * tau).astype(np.int8)) == o.energy(L, J_plain, s)
+
+
+def test_local_field_identity():
+    """sum_i s_i h_i counts every edge twice: it equals 2E."""
+    L = 6
+    J3 = wl.random_couplings(3, L, jmax=2)
+    for k in range(5):
+        s = wl.random_spins(50 + k, L ** 3)
+        tot = sum(int(s[i]) * o.local_field(L, J3, s, i) for i in range(L ** 3))
+        assert tot == 2 * o.energy(L, J3, s)
+
+
+def test_single_flip_energy_change():
+    """Flipping spin i changes E by -2 s_i h_i (brute-force energy difference)."""
+    L = 4
+    J3 = wl.random_couplings(8, L, jmax=2)
+    s = wl.random_spins(9, L ** 3)
+    E0 = o.energy(L, J3, s)
+    for i in range(0, L ** 3, 7):
+        t = s.copy()
+        t[i] = -t[i]
+        assert o.energy(L, J3, t) - E0 == -2 * int(s[i]) * o.local_field(L, J3, s, i)
+
+
+def test_random_state_gap_is_one():
+    """A random configuration has mean E = 0, so mean eps = 1 (the paper's ~100%)."""
+    L = 8
+    J3, tau, egs = o.generate(L, 1, wl.UNIFORM)
+    eps = [o.epsilon(o.energy(L, J3, wl.random_spins(1000 + k, L ** 3)), egs) for k in range(400)]
+    # Var E = number of edges (independent +-1 terms) -> sd of mean eps
+    sd = math.sqrt(3 * L ** 3) / abs(egs) / math.sqrt(len(eps))
+    assert abs(np.mean(eps) - 1.0) < 5 * sd
+
+
+def test_epsilon_definition():
+    assert o.epsilon(-100, -100) == 0.0
+    assert o.epsilon(0, -100) == 1.0
+    assert o.epsilon(-97, -100) == pytest.approx(0.03)
+
+
+# --------------------------------------------------------------------------- schedules
+
+def test_schedules():
+    b = o.beta_schedule(1000, 0.1, 3.0)
+    assert b[0] == 0.1 and b[-1] == 3.0
+    assert np.all(np.diff(b) > 0)
+    assert np.allclose(np.diff(b), 2.9 / 999)
+    g = o.beta_schedule(50, 0.2, 3.0, geometric=True)
+    assert g[0] == 0.2 and g[-1] == 3.0
+    assert np.allclose(g[1:] / g[:-1], (3.0 / 0.2) ** (1 / 49))
+    assert list(o.beta_schedule(1, 0.7, 3.0)) == [0.7]
+    lad = o.pt_ladder(32, 0.2, 3.0)
+    assert lad[0] == 0.2 and lad[-1] == 3.0
+    assert np.allclose(lad[1:] / lad[:-1], 15 ** (1 / 31))
+
+
+def _exact_threshold(beta, dE):
+    """floor(2^32 exp(-beta dE)) in 60-digit decimal arithmetic (independent of libm)."""
+    decimal.getcontext().prec = 60
+    v = (decimal.Decimal(-beta) * dE).exp() * (2 ** 32)
+    f = int(v)
+    near = abs(v - f) < decimal.Decimal("1e-6") or abs(v - f - 1) < decimal.Decimal("1e-6")
+    return min(f, 2 ** 32 - 1), near
+
+
+@pytest.mark.parametrize("beta", [0.1, 0.37, 1.0, 2.2, 3.0, 5.0])
+def test_metropolis_thresholds(beta):
+    prev = 2 ** 32
+    for dE in range(1, 25):
+        t = o.metropolis_threshold(beta, dE)
+        exact, near = _exact_threshold(beta, dE)
+        if not near:
+            assert t == exact
+        assert t <= prev
+        prev = t
+    assert o.metropolis_threshold(1e9, 2) == 0
+    assert o.metropolis_threshold(0.0, 2) == 2 ** 32 - 1
+
+
+def test_exchange_thresholds():
+    for dbeta in (0.01, 0.05, 0.3):
+        prev = 2 ** 32
+        for d in range(1, 400, 3):
+            t = o.exchange_threshold(dbeta, d)
+            exact, near = _exact_threshold(dbeta, d)
+            if not near:
+                assert t == exact
+            assert t <= prev
+            prev = t
+    assert o.exchange_threshold(0.0, 1000) == 2 ** 32 - 1
+
+
+# --------------------------------------------------------------------------- Metropolis dynamics
+
+def _boltzmann_l2(J3, beta):
+    E = np.array([o.energy(2, J3, np.array([1 - 2 * ((st >> i) & 1) for i in range(8)], np.int8))
+                  for st in range(256)])
+    w = np.exp(-beta * (E - E.min()))
+    return E, w / w.sum()
+
+
+def _state_index(s):
+    return int(sum(((1 - int(v)) // 2) << i for i, v in enumerate(s)))
+
+
+@pytest.mark.parametrize("beta", [0.25, 0.6])
+def test_metropolis_samples_boltzmann_l2(beta):
+    """Fixed beta (beta0 = beta1): independent replicas after many sweeps follow
+    exp(-beta E)/Z over all 256 states of an L=2 instance (chi-square test)."""
+    J3, tau, egs = o.generate(2, 17, wl.UNIFORM)
+    R = 40000
+    spins, E = o.sa_run(2, J3, 5, 0, 40, beta, beta, R=R)
+    idx = np.array([_state_index(s) for s in spins])
+    obs = np.bincount(idx, minlength=256)
+    _, p = _boltzmann_l2(J3, beta)
+    # pool states with small expected counts
+    exp = p * R
+    big = exp >= 5
+    chi = (((obs[big] - exp[big]) ** 2) / exp[big]).sum()
+    small_o, small_e = obs[~big].sum(), exp[~big].sum()
+    if small_e > 0:
+        chi += (small_o - small_e) ** 2 / small_e
+    dof = big.sum() + (1 if small_e > 0 else 0) - 1
+    assert stats.chi2.sf(chi, dof) > 1e-4
+    # the incremental energy bookkeeping matches a full recompute
+    for n in range(0, R, 997):
+        assert E[n] == o.energy(2, J3, spins[n])
+
+
+def test_sa_energy_bookkeeping_and_bounds():
+    L = 6
+    J3, tau, egs = o.generate(L, 3, wl.UNIFORM)
+    spins, E = o.sa_run(L, J3, 1, 2, 200, 0.1, 3.0, R=6)
+    for n in range(6):
+        assert E[n] == o.energy(L, J3, spins[n])
+        assert E[n] >= egs
+    # annealing lowers the energy far below the random-state mean of 0
+    assert (E < 0.7 * egs).all()
+
+
+def test_zero_temperature_is_monotone():
+    """At beta -> infinity (all thresholds 0) the energy never increases."""
+    L = 6
+    J3, tau, egs = o.generate(L, 4, wl.UNIFORM)
+    prev = None
+    for S in range(0, 12):
+        _, E = o.sa_run(L, J3, 9, 0, S, 1e9, 1e9, reps=[0, 5])
+        if prev is not None:
+            assert (E <= prev).all()
+        prev = E
+
+
+def test_sweep_prefix_property():
+    """The draw at sweep s depends only on s: S sweeps are a prefix of S+k at fixed beta."""
+    L = 4
+    J3, tau, egs = o.generate(L, 8, wl.UNIFORM)
+    a, Ea = o.sa_run(L, J3, 2, 0, 5, 0.8, 0.8, R=4)
+    b, Eb = o.sa_run(L, J3, 2, 0, 5, 0.8, 0.8, R=4)
+    assert np.array_equal(a, b) and np.array_equal(Ea, Eb)
+    c, Ec = o.sa_run(L, J3, 2, 0, 6, 0.8, 0.8, R=4)
+    assert not np.array_equal(a, c)
+
+
+# --------------------------------------------------------------------------- parallel tempering
+
+def test_pt_single_rung_is_fixed_beta_metropolis():
+    L = 4
+    J3, tau, egs = o.generate(L, 21, wl.UNIFORM)
+    pt = o.pt_run(L, J3, 3, 1, 1, 30, 0.9, 2.0)
+    s, E = o.sa_run(L, J3, 3, 1, 30, 0.9, 0.9, reps=[0])
+    assert np.array_equal(pt["spins"][0], s[0])
+    assert pt["E"][0] == E[0]
+
+
+def test_pt_equal_rungs_always_swap():
+    L = 4
+    J3, tau, egs = o.generate(L, 22, wl.UNIFORM)
+    K, S = 5, 40
+    pt = o.pt_run(L, J3, 4, 0, K, S, 1.1, 1.1)
+    # attempts per pair: pair k is tried on sweeps with s % 2 == k % 2
+    attempts = [sum(1 for s in range(S) if s % 2 == k % 2) for k in range(K - 1)]
+    assert list(pt["accepts"]) == attempts
+
+
+def test_pt_bookkeeping():
+    L = 4
+    J3, tau, egs = o.generate(L, 23, wl.UNIFORM)
+    K = 6
+    runs = [o.pt_run(L, J3, 5, 0, K, S, 0.2, 3.0) for S in range(0, 15)]
+    minE = runs[0]["minE"]
+    assert minE == runs[0]["E"].min()
+    for S in range(1, 15):
+        r = runs[S]
+        assert sorted(r["perm"]) == list(range(K))
+        for k in range(K):
+            assert r["E"][k] == o.energy(L, J3, r["spins"][k])
+        minE = min(minE, int(r["E"].min()))
+        assert r["minE"] == minE  # running minimum over every sweep
+        assert r["minE"] >= egs
+
+
+def test_pt_samples_boltzmann_on_each_rung():
+    """PT with 2 rungs at L=2: across independent runs, the state held at each rung
+    follows exp(-beta_k E)/Z (pins the exchange rule's sign and threshold)."""
+    J3, tau, egs = o.generate(2, 31, wl.UNIFORM)
+    bmin, bmax = 0.15, 0.5
+    runs = 3000
+    counts = [np.zeros(256, int), np.zeros(256, int)]
+    for n in range(runs):
+        r = o.pt_run(2, J3, 1000 + n, 0, 2, 25, bmin, bmax)
+        for slot in range(2):
+            counts[r["perm"][slot]][_state_index(r["spins"][slot])] += 1
+    for k, beta in enumerate((bmin, bmax)):
+        _, p = _boltzmann_l2(J3, beta)
+        exp = p * runs
+        big = exp >= 5
+        obs = counts[k]
+        chi = (((obs[big] - exp[big]) ** 2) / exp[big]).sum()
+        se, so = exp[~big].sum(), obs[~big].sum()
+        if se > 0:
+            chi += (so - se) ** 2 / se
+        dof = big.sum() + (1 if se > 0 else 0) - 1
+        assert stats.chi2.sf(chi, dof) > 1e-4
