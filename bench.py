@@ -1,0 +1,323 @@
+"""Benchmark: Metropolis spin-flip attempts/s of parallel tempering on tile-planted
+L=64 cubic-lattice spin glasses (16 instances x 32 temperatures, geometric beta
+0.2 -> 3.0, exchange after every sweep, 10^4 sweeps), through the libsg C ABI.
+
+One step = one full run of the hot path over the batch: initial spins, 10^4
+checkerboard Metropolis sweeps of every slot, an exchange attempt after each
+sweep, the energy recompute and the optimality gap eps of the minimum energy.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  `value` is attempts/s with the instances already
+resident on the device; `e2e` is the same metric with host couplings uploaded
+and results read back inside the timed region; `roofline` covers the sweep kernel;
+`cpu_baseline` times the CPU oracle on a bounded sample on the host cores.
+For N > 1 each rank runs its own 16 instances (weak scaling, no collective on the
+data path); value = all ranks' attempts / max-over-ranks time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2501_17267_gb300 import workloads as wl  # noqa: E402
+
+WORK = wl.PT_L64
+METRIC = "Metropolis spin-flip attempts/s"
+UNIT = "attempts/s"
+BYTES_PER_ATTEMPT = 2.0 + 3.0 / WORK.temps  # spin byte read + written once per sweep, 3 J bytes per site
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+# ---------------------------------------------------------------- CPU oracle leg
+
+def _oracle_job(args):
+    k, sweeps = args
+    from oracle import oracle as o
+    J3, _, _ = o.generate(WORK.L, WORK.instance_seed(k), WORK.class_prob, True)
+    t = time.perf_counter()
+    o.pt_run(WORK.L, J3, WORK.run_seed, k, WORK.temps, sweeps, WORK.beta_min, WORK.beta_max)
+    return time.perf_counter() - t
+
+
+def oracle_sample(sweeps: int, workers: int):
+    """The oracle, as it stands, on all 16 instances for `sweeps` sweeps, one process
+    per instance on `workers` host cores.  Wall time includes each run's initial
+    state and energy evaluation."""
+    ctx = mp.get_context("spawn")
+    t = time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_job, [(k, sweeps) for k in range(WORK.instances)])
+    wall = time.perf_counter() - t
+    attempts = WORK.instances * WORK.temps * WORK.L ** 3 * sweeps
+    return attempts / wall, wall
+
+
+def cpu_baseline(sweeps: int):
+    from oracle import oracle as o
+    o.build()
+    workers = min(WORK.instances, os.cpu_count() or 1)
+    rate, wall = oracle_sample(sweeps, workers)
+    return {"value": rate, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"all {WORK.instances} instances, first {sweeps} sweeps of the {WORK.sweeps} "
+                      f"(L={WORK.L}, {WORK.temps} temperatures), one spawn process per instance; "
+                      f"{wall:.1f} s wall incl. initial state + energy",
+            "cpu": _cpu_model()}
+
+
+def _cpu_model():
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return "unknown"
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    from oracle import oracle as o
+    o.build()
+    workers = min(WORK.instances, os.cpu_count() or 1)
+    for _ in range(args.warmup):
+        oracle_sample(args.ref_sweeps, workers)
+    rates, walls = [], []
+    for _ in range(args.steps):
+        r, w = oracle_sample(args.ref_sweeps, workers)
+        rates.append(r)
+        walls.append(w)
+    attempts = WORK.instances * WORK.temps * WORK.L ** 3 * args.ref_sweeps * args.steps
+    value = attempts / sum(walls)
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000 * sum(walls) / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": _config(),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
+                             "sample": f"each step: all {WORK.instances} instances, first "
+                                       f"{args.ref_sweeps} sweeps, one spawn process per instance",
+                             "cpu": _cpu_model()},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def _config():
+    return {"workload": WORK.name, "L": WORK.L, "instances": WORK.instances, "temps": WORK.temps,
+            "sweeps": WORK.sweeps, "beta": f"geometric {WORK.beta_min}->{WORK.beta_max}",
+            "exchange": "every sweep", "tiles": "uniform F22/F42/F6, gauged",
+            "cache": "inputs larger than L2: 134 MB of spins + 34 MB of couplings per step"}
+
+
+# ---------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        out, _ = self.proc.communicate(timeout=10)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- GPU leg
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--sweeps", type=int, default=WORK.sweeps,
+                    help="sweeps per run (default: the workload's 10^4)")
+    ap.add_argument("--cpu-sweeps", type=int, default=4)
+    ap.add_argument("--ref-sweeps", type=int, default=1)
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, rank)
+        return
+
+    # CPU oracle leg first: its spawn pool starts before this process touches the GPU
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        cpu = cpu_baseline(args.cpu_sweeps)
+
+    import numpy as np
+    import torch
+
+    torch.cuda.set_device(local)
+    torch.cuda.init()
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_2501_17267_gb300 import build as libbuild
+    if rank == 0:
+        libbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    libbuild.build()
+    from paper_2501_17267_gb300 import sg
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    S = args.sweeps
+    base = rank * WORK.instances
+    insts = [sg.Instance.create(WORK.L, WORK.instance_seed(base + k), WORK.class_prob, True)
+             for k in range(WORK.instances)]
+    params = [dict(temps=WORK.temps, sweeps=S, beta_min=WORK.beta_min, beta_max=WORK.beta_max,
+                   seed=WORK.run_seed, instance_id=base + k) for k in range(WORK.instances)]
+    stream = torch.cuda.current_stream()
+
+    def step():
+        return sg.pt_run_batch(insts, params)
+
+    for _ in range(args.warmup):
+        out = step()
+    sg.stats_read(reset=True)
+    sg.stats_enable(True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    barrier()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        out = step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clk = clocks.stop()
+    sg.stats_enable(False)
+    st = sg.stats_read(reset=True)
+    ms = ev0.elapsed_time(ev1)
+    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+    ms_max = float(t.item())
+    attempts_per_step = WORK.instances * WORK.temps * WORK.L ** 3 * S
+    value = attempts_per_step * world * args.steps / (ms_max / 1000.0)
+    launches = sum(v["launches"] for v in st.values())
+
+    # roofline of the sweep kernel: algorithmic bytes per launch / mean launch duration
+    sw = st["sweep"]
+    peak, peak_kind = _peaks()
+    roof = None
+    if sw["launches"] and sw["device_ms"] > 0:
+        per_launch_s = sw["device_ms"] / 1000.0 / sw["launches"]
+        bytes_per_launch = sw["units"] / sw["launches"] * BYTES_PER_ATTEMPT
+        achieved = bytes_per_launch / per_launch_s / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
+                "kernel": "half_sweep_kernel<PT>", "launch_ms": 1000 * per_launch_s,
+                "attempts_per_launch": sw["units"] / sw["launches"],
+                "share_of_step": sw["device_ms"] / ms}
+
+    # end to end: host couplings in, results out, inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        host = [i.get() for i in insts]
+
+        def e2e_step():
+            hi = [sg.Instance.from_couplings(WORK.L, J3, egs) for (J3, _, egs) in host]
+            r = sg.pt_run_batch(hi, params)
+            for x in hi:
+                x.close()
+            return r
+
+        e2e_step()
+        barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            e2e_step()
+        torch.cuda.synchronize()
+        barrier()
+        e_s = time.perf_counter() - t0
+        te = torch.tensor([e_s], dtype=torch.float64, device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        K = WORK.temps
+        e2e = {"value": attempts_per_step * world * args.steps / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": WORK.instances * 3 * WORK.L ** 3,
+               "d2h_bytes_per_step": WORK.instances * (8 * K + 4 * K + 8 * (K - 1) + 8 + 8)}
+
+    if rank == 0:
+        mins = [o["min_eps"] for o in out]
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "int8", "data": "synthetic", "config": _config(),
+                "pct_hbm_roofline": (value * BYTES_PER_ATTEMPT / 1e9) / peak,
+                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
+                "clocks": clk, "min_eps_mean": float(np.mean(mins)),
+                "kernel_stats": st}
+        if S != WORK.sweeps:
+            line["config"]["sweeps"] = S
+            line["note"] = f"reduced sweeps ({S}) -- not the workload's number"
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

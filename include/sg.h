@@ -1,0 +1,224 @@
+/*
+ * sg.h -- C ABI of libsg, the GB300 (sm_103a) Metropolis simulated-annealing and
+ * parallel-tempering library for tile-planted cubic-lattice Ising spin glasses.
+ *
+ * Problem statement (arXiv:2501.17267):
+ *   H = sum over lattice edges <i,j> of J_ij s_i s_j, s_i in {-1,+1}      (Eq. 1)
+ *   on the periodic L x L x L simple-cubic lattice (Sec. II, Fig. 4 caption),
+ *   scored by the optimality gap eps = (E - E_gs) / |E_gs|                   (Eq. 2)
+ *   where E_gs is the planted ground-state energy of a tile-planting instance
+ *   (Sec. II).  The solvers are Metropolis single-spin-flip simulated annealing
+ *   along a beta schedule (App. D.1) and parallel tempering over a geometric beta
+ *   ladder (App. D.2).
+ *
+ * Conventions shared by every entry point:
+ *   - Every call returns int32_t status: SG_OK (0) or a negative SG_E* code.  On
+ *     error, sg_last_error_string() gives a message for the calling thread.  No C++
+ *     exception crosses the ABI.
+ *   - Site index i = x + L*(y + L*z).  Couplings "J3" are int8 [N][3] (N = L^3);
+ *     J3[i][d] couples site i to its +1 neighbour along axis d (0=x, 1=y, 2=z),
+ *     periodic.  |J| <= SG_JMAX.  Spins are int8 in {-1, +1}.
+ *   - Handles (sg_instance) are owned by the library and released with
+ *     sg_instance_destroy.  Caller buffers are borrowed for the duration of the
+ *     call only: host pointers, or device pointers when the matching *_mem field
+ *     is SG_MEM_DEVICE (device memory of the current CUDA device).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *     Work is enqueued on it; every run call returns after its host outputs are
+ *     written (it synchronises the stream before returning).
+ *   - Runs are deterministic: the same instance, parameters and seed give the same
+ *     bytes on every call, batch composition and GPU.  Every random number is word
+ *     w of Philox4x32-10 (Salmon et al., SC'11) with key
+ *     (seed_lo32, seed_hi32 ^ instance_id) at a counter that names its use:
+ *       Metropolis draw of replica r at site i, sweep s: counter (i, s, r/4, 0), w = r%4
+ *       initial spin of replica r at site i:             counter (i, 0xFFFFFFFF, r/4, 0), w = r%4,
+ *                                                         spin = -1 iff bit 31 is set
+ *       PT exchange of rungs (k, k+1) after sweep s:      counter (k, s, 0, 1), w = 0
+ *   - A Metropolis attempt at site i computes x = s_i * sum_j J_ij s_j (flipping
+ *     changes E by dE = -2x) and flips when x >= 0, or when the draw u satisfies
+ *     u < floor(2^32 * exp(-beta * dE)).  Sites are swept in checkerboard order:
+ *     all sites with x+y+z even, then all with x+y+z odd.
+ */
+#ifndef SG_H
+#define SG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define SG_OK 0
+#define SG_EINVAL (-1)    /* invalid argument (odd L, beta <= 0, R = 0, |J| > SG_JMAX, ...) */
+#define SG_ENOMEM (-2)    /* host or device allocation failed, or request exceeds a budget */
+#define SG_ECUDA (-3)     /* a CUDA runtime call failed */
+#define SG_ETIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define SG_EBUSY (-5)     /* a queue or slot pool is full */
+#define SG_EINTERNAL (-6) /* a self-check failed (e.g. incremental energy != recomputed) */
+#define SG_PENDING 1      /* sg_poll: the request has not finished */
+
+#define SG_MEM_HOST 0
+#define SG_MEM_DEVICE 1
+
+#define SG_SCHEDULE_LINEAR 0    /* beta_s = b0 + (b1 - b0) * s / (S - 1)      */
+#define SG_SCHEDULE_GEOMETRIC 1 /* beta_s = b0 * (b1 / b0) ^ (s / (S - 1))    */
+
+#define SG_JMAX 2      /* largest |J| the kernels accept */
+#define SG_LMAX 256    /* largest lattice side */
+
+typedef struct sg_instance sg_instance;
+
+/* ------------------------------------------------------------------------ */
+/* Instances: tile planting (Sec. II).                                       */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sg_instance_desc {
+    int32_t L;             /* even, 2 <= L <= SG_LMAX */
+    int32_t gauge;         /* 1: scramble the planted state with a random gauge (Sec. II) */
+    uint64_t seed;         /* instance seed */
+    double class_prob[3];  /* weights of tile classes F22, F42, F6 (>= 0, sum > 0) */
+} sg_instance_desc;
+
+/* Generate a tile-planted instance (Sec. II).  The lattice is split into the
+ * N/4 unit cubes whose origin has all-even or all-odd coordinates; every edge lies
+ * in exactly one.  Each cube draws a class (F22: two adjacent frustrated faces,
+ * F42: four frustrated faces with the two others opposite, F6: all six frustrated;
+ * |J| = 1) and one of the 48 cube symmetries; E_gs is the sum of the cube minima
+ * and the planted state is all +1, then gauged by a random tau when gauge = 1.
+ * Counters: class and symmetry from words 0 and 1 of Philox at (tile, 0, 0, 2),
+ * gauge from bit 31 of word 0 at (site, 0, 0, 3), key (seed_lo32, seed_hi32).
+ * Errors: SG_EINVAL for bad L or weights; SG_ENOMEM. */
+int32_t sg_instance_create(const sg_instance_desc* desc, sg_instance** out);
+
+/* Wrap caller couplings J3 [N][3] (host or device per mem_kind) with a known
+ * ground-state energy e_gs (used only for eps; pass 0 if unknown, eps is then
+ * not finite).  The planted state is reported as all +1.  The couplings are copied.
+ * Errors: SG_EINVAL for bad L, a NULL pointer or |J| > SG_JMAX. */
+int32_t sg_instance_create_from_couplings(int32_t L, const int8_t* J3, int32_t mem_kind,
+                                          int64_t e_gs, sg_instance** out);
+
+/* Read back an instance.  Any output pointer may be NULL.  J3_out: host int8
+ * [N][3]; planted_out: host int8 [N]. */
+int32_t sg_instance_get(const sg_instance* inst, int32_t* L_out, int8_t* J3_out,
+                        int8_t* planted_out, int64_t* e_gs_out);
+
+/* Release an instance (and its cached device copy).  NULL is a no-op. */
+int32_t sg_instance_destroy(sg_instance* inst);
+
+/* ------------------------------------------------------------------------ */
+/* Simulated annealing (App. D.1).                                           */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sg_sa_params {
+    int32_t replicas;      /* R >= 1: independent chains (num_reads), run side by side */
+    int32_t sweeps;        /* S >= 0: one checkerboard sweep per schedule value */
+    double beta0, beta1;   /* schedule end points, > 0 */
+    int32_t schedule;      /* SG_SCHEDULE_LINEAR or SG_SCHEDULE_GEOMETRIC */
+    uint32_t instance_id;  /* mixed into the RNG key */
+    uint64_t seed;         /* run seed */
+} sg_sa_params;
+
+typedef struct sg_sa_result {
+    int64_t* E;            /* [R] host: final energy of each replica (required) */
+    double* eps;           /* [R] host: final optimality gap (Eq. 2), may be NULL */
+    int8_t* spins;         /* [R][N]: final spins, may be NULL */
+    int32_t spins_mem;     /* SG_MEM_HOST or SG_MEM_DEVICE for `spins` */
+} sg_sa_result;
+
+/* Anneal R replicas of one instance for S sweeps.  The energy of each replica
+ * is tracked incrementally on the device and checked against a full recompute at
+ * the end (mismatch: SG_EINTERNAL).  Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA. */
+int32_t sg_sa_run(const sg_instance* inst, const sg_sa_params* p, sg_sa_result* out,
+                  void* stream);
+
+/* Anneal n instances in one call; instances of equal L and equal (R, S, beta0,
+ * beta1, schedule) share launches.  Results are byte-identical to n separate
+ * sg_sa_run calls. */
+int32_t sg_sa_run_batch(const sg_instance* const* insts, const sg_sa_params* ps, int32_t n,
+                        sg_sa_result* outs, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Parallel tempering (App. D.2).                                            */
+/* ------------------------------------------------------------------------ */
+
+typedef struct sg_pt_params {
+    int32_t temps;         /* K >= 1 rungs (one replica slot per rung) */
+    int32_t sweeps;        /* S >= 0 */
+    double beta_min, beta_max; /* geometric ladder beta_k = bmin (bmax/bmin)^(k/(K-1)), > 0 */
+    uint32_t instance_id;
+    uint64_t seed;
+} sg_pt_params;
+
+typedef struct sg_pt_result {
+    int64_t* E;            /* [K] host, by slot: final energies (may be NULL) */
+    int32_t* perm;         /* [K] host, by slot: rung held at the end (may be NULL) */
+    int64_t* accepts;      /* [K-1] host: accepted swaps of rungs (k, k+1) (may be NULL) */
+    int64_t minE;          /* out: lowest energy seen in any slot, after init and every sweep */
+    double min_eps;        /* out: eps of minE (Eq. 2) */
+    int8_t* spins;         /* [K][N] by slot, may be NULL */
+    int32_t spins_mem;
+} sg_pt_result;
+
+/* Run PT: after every sweep s, rung pairs (k, k+1) with k = s mod 2 attempt a
+ * label swap, accepted when d = E_a - E_b <= 0 (slot a at rung k, b at k+1) or
+ * when the draw u < floor(2^32 exp(-(beta_{k+1} - beta_k) d)).  Errors: SG_EINVAL
+ * (also when the ladder is so fine that an exchange table would exceed 2^22
+ * entries), SG_ENOMEM, SG_ECUDA, SG_EINTERNAL. */
+int32_t sg_pt_run(const sg_instance* inst, const sg_pt_params* p, sg_pt_result* out,
+                  void* stream);
+
+/* n instances in one call; instances of equal L and equal (K, S, beta range)
+ * share launches.  Byte-identical to n separate sg_pt_run calls. */
+int32_t sg_pt_run_batch(const sg_instance* const* insts, const sg_pt_params* ps, int32_t n,
+                        sg_pt_result* outs, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Energy (Eq. 1).                                                           */
+/* ------------------------------------------------------------------------ */
+
+/* E_out[c] = sum_i sum_d J3[i][d] s_c[i] s_c[i + e_d] for n_configs spin
+ * configurations s_c laid out [n_configs][N] (host or device per mem_kind);
+ * E_out is host.  Errors: SG_EINVAL (also for a spin not in {-1,+1}), SG_ECUDA. */
+int32_t sg_energy(const sg_instance* inst, const int8_t* spins, int32_t n_configs,
+                  int32_t mem_kind, int64_t* E_out, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Launch statistics (diagnostics; no counterpart in the paper).             */
+/* ------------------------------------------------------------------------ */
+
+#define SG_KERNEL_INIT 0      /* initial spins */
+#define SG_KERNEL_ENERGY 1    /* full energy recompute */
+#define SG_KERNEL_SWEEP 2     /* Metropolis sweep kernels (the hot path) */
+#define SG_KERNEL_EXCHANGE 3  /* PT exchange */
+#define SG_KERNEL_OTHER 4     /* layout conversion, checks, set-up */
+#define SG_KERNEL_KINDS 5
+
+typedef struct sg_kernel_stats {
+    int64_t launches[SG_KERNEL_KINDS];  /* kernels launched by this library, per kind */
+    double device_ms[SG_KERNEL_KINDS];  /* summed launch durations (only while timing is on) */
+    int64_t units[SG_KERNEL_KINDS];     /* work units processed: spin-flip attempts for
+                                           SG_KERNEL_SWEEP, spin sites x replicas otherwise */
+} sg_kernel_stats;
+
+/* timing = 1: every later launch is bracketed by CUDA events recorded on the
+ * launch's own stream, and its duration is added to device_ms when the run that
+ * issued it completes.  Launch counts and units are always kept.  Process-wide. */
+int32_t sg_stats_enable(int32_t timing);
+
+/* Copy the process-wide counters into *out; reset = 1 zeroes them afterwards. */
+int32_t sg_stats_read(sg_kernel_stats* out, int32_t reset);
+
+/* ------------------------------------------------------------------------ */
+/* Misc.                                                                     */
+/* ------------------------------------------------------------------------ */
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* sg_last_error_string(void);
+
+/* Library version, major*10000 + minor*100 + patch. */
+int32_t sg_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SG_H */

@@ -1,0 +1,639 @@
+// api.cu -- the C ABI entry points: validation, device workspace, launch sequence.
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <algorithm>
+#include <map>
+#include <tuple>
+
+#include "sg_internal.h"
+
+namespace sg {
+
+static thread_local char g_err[512] = "";
+
+void set_error(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_err, sizeof(g_err), fmt, ap);
+    va_end(ap);
+}
+
+void clear_error() { g_err[0] = 0; }
+
+namespace {
+
+// ---- launch statistics: counts always, CUDA-event durations when enabled ----
+struct Stats {
+    std::mutex mu;
+    bool timing = false;
+    sg_kernel_stats totals{};
+    std::vector<cudaEvent_t> pool;
+};
+Stats& stats()
+{
+    static Stats s;
+    return s;
+}
+
+// Per-run recorder.  Each launch is counted; with timing on it is bracketed by two
+// events on its stream, resolved by finish() once the run has synchronised.
+class LaunchLog {
+  public:
+    LaunchLog()
+    {
+        std::lock_guard<std::mutex> g(stats().mu);
+        timing_ = stats().timing;
+    }
+    ~LaunchLog() { release(); }
+    template <class F>
+    int32_t run(int kind, int64_t units, cudaStream_t st, F&& launch)
+    {
+        cudaEvent_t a = nullptr, b = nullptr;
+        if (timing_) {
+            a = take();
+            b = take();
+            if (a && b) cudaEventRecord(a, st);
+        }
+        const int32_t rc = launch();
+        if (timing_ && a && b) {
+            cudaEventRecord(b, st);
+            pending_.push_back({kind, a, b});
+        } else {
+            give(a);
+            give(b);
+        }
+        {
+            std::lock_guard<std::mutex> g(stats().mu);
+            stats().totals.launches[kind] += 1;
+            stats().totals.units[kind] += units;
+        }
+        return rc;
+    }
+    // Call after the stream has been synchronised.
+    void finish()
+    {
+        double ms[SG_KERNEL_KINDS] = {0};
+        for (auto& p : pending_) {
+            float t = 0.f;
+            if (cudaEventElapsedTime(&t, p.a, p.b) == cudaSuccess) ms[p.kind] += t;
+        }
+        {
+            std::lock_guard<std::mutex> g(stats().mu);
+            for (int k = 0; k < SG_KERNEL_KINDS; ++k) stats().totals.device_ms[k] += ms[k];
+        }
+        release();
+    }
+
+  private:
+    struct Pending {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    cudaEvent_t take()
+    {
+        {
+            std::lock_guard<std::mutex> g(stats().mu);
+            if (!stats().pool.empty()) {
+                cudaEvent_t e = stats().pool.back();
+                stats().pool.pop_back();
+                return e;
+            }
+        }
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        return e;
+    }
+    void give(cudaEvent_t e)
+    {
+        if (!e) return;
+        std::lock_guard<std::mutex> g(stats().mu);
+        stats().pool.push_back(e);
+    }
+    void release()
+    {
+        for (auto& p : pending_) {
+            give(p.a);
+            give(p.b);
+        }
+        pending_.clear();
+    }
+    bool timing_ = false;
+    std::vector<Pending> pending_;
+};
+
+// Stream-ordered device allocation released when the owner goes out of scope.
+class DevBuf {
+  public:
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    ~DevBuf()
+    {
+        if (p_) cudaFreeAsync(p_, st_);
+    }
+    int32_t alloc(size_t bytes, cudaStream_t st)
+    {
+        st_ = st;
+        cudaError_t e = cudaMallocAsync(&p_, bytes ? bytes : 16, st);
+        if (e != cudaSuccess) {
+            p_ = nullptr;
+            cudaGetLastError();
+            set_error("device allocation of %zu bytes failed: %s", bytes, cudaGetErrorString(e));
+            return SG_ENOMEM;
+        }
+        return SG_OK;
+    }
+    template <class T>
+    T* as() const
+    {
+        return reinterpret_cast<T*>(p_);
+    }
+
+  private:
+    void* p_ = nullptr;
+    cudaStream_t st_ = nullptr;
+};
+
+#define SG_RET(expr)                    \
+    do {                                \
+        int32_t _rc = (expr);           \
+        if (_rc != SG_OK) return _rc;   \
+    } while (0)
+
+// Instances per launch group: the grid's y extent holds one instance per row.
+constexpr size_t kMaxGroup = 65535;
+
+RunKeys make_key(uint64_t seed, uint32_t instance_id)
+{
+    return RunKeys{(uint32_t)seed, (uint32_t)(seed >> 32) ^ instance_id};
+}
+
+double eps_of(int64_t E, int64_t egs) { return (double)(E - egs) / (double)(-egs); }
+
+bool beta_ok(double b) { return b > 0 && isfinite(b); }
+
+int32_t check_sa(const sg_instance* inst, const sg_sa_params* p, const sg_sa_result* o)
+{
+    if (!inst || !p || !o) {
+        set_error("NULL argument");
+        return SG_EINVAL;
+    }
+    if (p->replicas < 1 || p->replicas > (1 << 20)) {
+        set_error("replicas must be in [1, 2^20] (got %d)", p->replicas);
+        return SG_EINVAL;
+    }
+    if (p->sweeps < 0) {
+        set_error("sweeps must be >= 0");
+        return SG_EINVAL;
+    }
+    if (!beta_ok(p->beta0) || !beta_ok(p->beta1)) {
+        set_error("beta0 and beta1 must be finite and > 0");
+        return SG_EINVAL;
+    }
+    if (p->schedule != SG_SCHEDULE_LINEAR && p->schedule != SG_SCHEDULE_GEOMETRIC) {
+        set_error("unknown schedule %d", p->schedule);
+        return SG_EINVAL;
+    }
+    if (!o->E) {
+        set_error("result E must not be NULL");
+        return SG_EINVAL;
+    }
+    if (o->spins && o->spins_mem != SG_MEM_HOST && o->spins_mem != SG_MEM_DEVICE) {
+        set_error("bad spins_mem");
+        return SG_EINVAL;
+    }
+    return SG_OK;
+}
+
+int32_t check_pt(const sg_instance* inst, const sg_pt_params* p, const sg_pt_result* o)
+{
+    if (!inst || !p || !o) {
+        set_error("NULL argument");
+        return SG_EINVAL;
+    }
+    if (p->temps < 1 || p->temps > 256) {
+        set_error("temps must be in [1, 256] (got %d)", p->temps);
+        return SG_EINVAL;
+    }
+    if (p->sweeps < 0) {
+        set_error("sweeps must be >= 0");
+        return SG_EINVAL;
+    }
+    if (!beta_ok(p->beta_min) || !beta_ok(p->beta_max)) {
+        set_error("beta_min and beta_max must be finite and > 0");
+        return SG_EINVAL;
+    }
+    if (o->spins && o->spins_mem != SG_MEM_HOST && o->spins_mem != SG_MEM_DEVICE) {
+        set_error("bad spins_mem");
+        return SG_EINVAL;
+    }
+    return SG_OK;
+}
+
+// Shared tail of a run: copy the spins of instance `idx` out of the packed layout.
+int32_t emit_spins(const int8_t* packed, int idx, int64_t N, int Rp, int R, int8_t* dst, int mem,
+                   cudaStream_t st, DevBuf* staging, LaunchLog* log)
+{
+    if (!dst) return SG_OK;
+    int8_t* target = mem == SG_MEM_DEVICE ? dst : staging->as<int8_t>();
+    SG_RET(log->run(SG_KERNEL_OTHER, (int64_t)R * N, st, [&] {
+        return launch_unpack_spins(packed, target, N, Rp, R, idx, 0, st);
+    }));
+    if (mem == SG_MEM_DEVICE) return SG_OK;
+    SG_TRY_CUDA(cudaMemcpyAsync(dst, staging->as<int8_t>(), (size_t)R * N, cudaMemcpyDeviceToHost, st));
+    return SG_OK;
+}
+
+// ------------------------------------------------------------------ SA group
+
+// Instances of one group share L, R, S and schedule; keys differ per instance.
+int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* insts,
+                     const sg_sa_params* ps, sg_sa_result* outs, cudaStream_t st)
+{
+    const int I = (int)members.size();
+    const sg_sa_params& p = ps[members[0]];
+    sg_instance* first = const_cast<sg_instance*>(insts[members[0]]);
+    const int L = first->L;
+    const int64_t N = first->N;
+    const int R = p.replicas;
+    const int Wn = (R + 3) / 4, Rp = 4 * Wn;
+    const int S = p.sweeps;
+
+    std::vector<double> beta((size_t)std::max(S, 1));
+    beta_schedule(S, p.beta0, p.beta1, p.schedule == SG_SCHEDULE_GEOMETRIC, beta.data());
+    std::vector<uint32_t> thr((size_t)std::max(S, 1) * kThrRow);
+    for (int s = 0; s < S; ++s) metropolis_row(beta[s], &thr[(size_t)s * kThrRow]);
+
+    std::vector<RunKeys> keys(I);
+    std::vector<const uint2*> j6(I);
+    for (int a = 0; a < I; ++a) {
+        const sg_sa_params& q = ps[members[a]];
+        keys[a] = make_key(q.seed, q.instance_id);
+        SG_RET(instance_device_j6(const_cast<sg_instance*>(insts[members[a]]), st, &j6[a]));
+    }
+
+    DevBuf d_spins, d_E, d_E64, d_thr, d_keys, d_j6, d_flag, d_stage;
+    SG_RET(d_spins.alloc((size_t)I * N * Rp, st));
+    SG_RET(d_E.alloc(sizeof(int32_t) * (size_t)I * Rp, st));
+    SG_RET(d_E64.alloc(sizeof(unsigned long long) * (size_t)I * Rp, st));
+    SG_RET(d_thr.alloc(sizeof(uint32_t) * thr.size(), st));
+    SG_RET(d_keys.alloc(sizeof(RunKeys) * I, st));
+    SG_RET(d_j6.alloc(sizeof(uint2*) * I, st));
+    SG_RET(d_flag.alloc(sizeof(int), st));
+    bool host_spins = false;
+    for (int a = 0; a < I; ++a)
+        host_spins |= outs[members[a]].spins && outs[members[a]].spins_mem == SG_MEM_HOST;
+    if (host_spins) SG_RET(d_stage.alloc((size_t)R * N, st));
+
+    SG_TRY_CUDA(cudaMemcpyAsync(d_thr.as<void>(), thr.data(), sizeof(uint32_t) * thr.size(),
+                                cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(d_keys.as<void>(), keys.data(), sizeof(RunKeys) * I,
+                                cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(d_j6.as<void>(), j6.data(), sizeof(uint2*) * I,
+                                cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * (size_t)I * Rp, st));
+    SG_TRY_CUDA(cudaMemsetAsync(d_flag.as<void>(), 0, sizeof(int), st));
+
+    int8_t* spins = d_spins.as<int8_t>();
+    const uint2* const* j6p = d_j6.as<const uint2*>();
+    const RunKeys* kp = d_keys.as<RunKeys>();
+    LaunchLog log;
+    const int64_t cells = (int64_t)I * N * Rp;
+    unsigned long long* E64d = d_E64.as<unsigned long long>();
+    SG_RET(log.run(SG_KERNEL_INIT, cells, st, [&] { return launch_init_spins(spins, kp, I, N, Wn, R, st); }));
+    SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st); }));
+    SG_RET(log.run(SG_KERNEL_OTHER, (int64_t)I * Rp, st, [&] {
+        return launch_narrow_energy(E64d, d_E.as<int32_t>(), (int64_t)I * Rp, st);
+    }));
+    for (int s = 0; s < S; ++s)
+        for (int c = 0; c < 2; ++c)
+            SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * R, st, [&] {
+                return launch_half_sweep_sa(spins, j6p, kp, d_thr.as<uint32_t>() + (size_t)s * kThrRow,
+                                            d_E.as<int32_t>(), I, L, Wn, R, (uint32_t)s, c, st);
+            }));
+    SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * (size_t)I * Rp, st));
+    SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st); }));
+    SG_RET(log.run(SG_KERNEL_OTHER, (int64_t)I * Rp, st, [&] {
+        return launch_check_energy(E64d, d_E.as<int32_t>(), I, Rp, R, d_flag.as<int>(), st);
+    }));
+
+    std::vector<long long> E64((size_t)I * Rp);
+    int mismatch = 0;
+    SG_TRY_CUDA(cudaMemcpyAsync(E64.data(), d_E64.as<void>(), sizeof(long long) * E64.size(),
+                                cudaMemcpyDeviceToHost, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(&mismatch, d_flag.as<void>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    for (int a = 0; a < I; ++a) {
+        sg_sa_result& o = outs[members[a]];
+        SG_RET(emit_spins(spins, a, N, Rp, R, o.spins, o.spins_mem, st, &d_stage, &log));
+        if (o.spins && o.spins_mem == SG_MEM_HOST) SG_TRY_CUDA(cudaStreamSynchronize(st));
+    }
+    SG_TRY_CUDA(cudaStreamSynchronize(st));
+    log.finish();
+    if (mismatch) {
+        set_error("incremental energies disagree with the recomputed energies (%d slots)", mismatch);
+        return SG_EINTERNAL;
+    }
+    for (int a = 0; a < I; ++a) {
+        const sg_instance* inst = insts[members[a]];
+        sg_sa_result& o = outs[members[a]];
+        for (int r = 0; r < R; ++r) {
+            o.E[r] = E64[(size_t)a * Rp + r];
+            if (o.eps) o.eps[r] = eps_of(o.E[r], inst->e_gs);
+        }
+    }
+    return SG_OK;
+}
+
+// ------------------------------------------------------------------ PT group
+
+int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* insts,
+                     const sg_pt_params* ps, sg_pt_result* outs, cudaStream_t st)
+{
+    const int I = (int)members.size();
+    const sg_pt_params& p = ps[members[0]];
+    const sg_instance* first = insts[members[0]];
+    const int L = first->L;
+    const int64_t N = first->N;
+    const int K = p.temps;
+    const int Wn = (K + 3) / 4, Rp = 4 * Wn;
+    const int S = p.sweeps;
+
+    std::vector<double> ladder(K);
+    beta_schedule(K, p.beta_min, p.beta_max, 1, ladder.data());
+    std::vector<uint32_t> thr((size_t)K * kThrRow);
+    for (int k = 0; k < K; ++k) metropolis_row(ladder[k], &thr[(size_t)k * kThrRow]);
+    int64_t dmax = 0;
+    for (int a = 0; a < I; ++a) dmax = std::max<int64_t>(dmax, 4 * (int64_t)insts[members[a]]->abs_sum);
+    ExchangeTables xt;
+    SG_RET(build_exchange_tables(ladder, dmax, &xt));
+
+    std::vector<RunKeys> keys(I);
+    std::vector<const uint2*> j6(I);
+    for (int a = 0; a < I; ++a) {
+        const sg_pt_params& q = ps[members[a]];
+        keys[a] = make_key(q.seed, q.instance_id);
+        SG_RET(instance_device_j6(const_cast<sg_instance*>(insts[members[a]]), st, &j6[a]));
+    }
+    const int Kp = std::max(K - 1, 1);
+    DevBuf d_spins, d_E, d_E64, d_thr, d_keys, d_j6, d_flag, d_stage, d_perm, d_inv, d_acc, d_min,
+        d_xtab, d_xoff, d_xlen, d_xtail;
+    SG_RET(d_spins.alloc((size_t)I * N * Rp, st));
+    SG_RET(d_E.alloc(sizeof(int32_t) * (size_t)I * Rp, st));
+    SG_RET(d_E64.alloc(sizeof(unsigned long long) * (size_t)I * Rp, st));
+    SG_RET(d_thr.alloc(sizeof(uint32_t) * thr.size(), st));
+    SG_RET(d_keys.alloc(sizeof(RunKeys) * I, st));
+    SG_RET(d_j6.alloc(sizeof(uint2*) * I, st));
+    SG_RET(d_flag.alloc(sizeof(int), st));
+    SG_RET(d_perm.alloc((size_t)I * Rp, st));
+    SG_RET(d_inv.alloc((size_t)I * K, st));
+    SG_RET(d_acc.alloc(sizeof(unsigned long long) * (size_t)I * Kp, st));
+    SG_RET(d_min.alloc(sizeof(int32_t) * I, st));
+    SG_RET(d_xtab.alloc(sizeof(uint32_t) * xt.tab.size(), st));
+    SG_RET(d_xoff.alloc(sizeof(uint32_t) * xt.off.size(), st));
+    SG_RET(d_xlen.alloc(sizeof(uint32_t) * xt.len.size(), st));
+    SG_RET(d_xtail.alloc(sizeof(uint32_t) * xt.tail.size(), st));
+    bool host_spins = false;
+    for (int a = 0; a < I; ++a)
+        host_spins |= outs[members[a]].spins && outs[members[a]].spins_mem == SG_MEM_HOST;
+    if (host_spins) SG_RET(d_stage.alloc((size_t)K * N, st));
+
+    auto h2d = [&](DevBuf& b, const void* src, size_t n) {
+        return cudaMemcpyAsync(b.as<void>(), src, n, cudaMemcpyHostToDevice, st);
+    };
+    SG_TRY_CUDA(h2d(d_thr, thr.data(), sizeof(uint32_t) * thr.size()));
+    SG_TRY_CUDA(h2d(d_keys, keys.data(), sizeof(RunKeys) * I));
+    SG_TRY_CUDA(h2d(d_j6, j6.data(), sizeof(uint2*) * I));
+    SG_TRY_CUDA(h2d(d_xtab, xt.tab.data(), sizeof(uint32_t) * xt.tab.size()));
+    SG_TRY_CUDA(h2d(d_xoff, xt.off.data(), sizeof(uint32_t) * xt.off.size()));
+    SG_TRY_CUDA(h2d(d_xlen, xt.len.data(), sizeof(uint32_t) * xt.len.size()));
+    SG_TRY_CUDA(h2d(d_xtail, xt.tail.data(), sizeof(uint32_t) * xt.tail.size()));
+    SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * (size_t)I * Rp, st));
+    SG_TRY_CUDA(cudaMemsetAsync(d_flag.as<void>(), 0, sizeof(int), st));
+
+    int8_t* spins = d_spins.as<int8_t>();
+    const uint2* const* j6p = d_j6.as<const uint2*>();
+    const RunKeys* kp = d_keys.as<RunKeys>();
+    int32_t* E = d_E.as<int32_t>();
+    uint8_t* perm = d_perm.as<uint8_t>();
+    uint8_t* inv = d_inv.as<uint8_t>();
+    unsigned long long* acc = d_acc.as<unsigned long long>();
+    int32_t* minE = d_min.as<int32_t>();
+    LaunchLog log;
+    const int64_t cells = (int64_t)I * N * Rp;
+    unsigned long long* E64d = d_E64.as<unsigned long long>();
+    SG_RET(log.run(SG_KERNEL_INIT, cells, st, [&] { return launch_init_spins(spins, kp, I, N, Wn, K, st); }));
+    SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st); }));
+    SG_RET(log.run(SG_KERNEL_OTHER, (int64_t)I * Rp, st, [&] {
+        return launch_pt_setup(E64d, E, perm, inv, acc, minE, I, Rp, K, st);
+    }));
+    for (int s = 0; s < S; ++s) {
+        for (int c = 0; c < 2; ++c)
+            SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * K, st, [&] {
+                return launch_half_sweep_pt(spins, j6p, kp, d_thr.as<uint32_t>(), perm, E, I, L, Wn, K,
+                                            (uint32_t)s, c, st);
+            }));
+        SG_RET(log.run(SG_KERNEL_EXCHANGE, (int64_t)I * (K / 2), st, [&] {
+            return launch_pt_exchange(kp, E, perm, inv, acc, minE, d_xtab.as<uint32_t>(),
+                                      d_xoff.as<uint32_t>(), d_xlen.as<uint32_t>(),
+                                      d_xtail.as<uint32_t>(), I, Rp, K, (uint32_t)s, st);
+        }));
+    }
+    SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * (size_t)I * Rp, st));
+    SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st); }));
+    SG_RET(log.run(SG_KERNEL_OTHER, (int64_t)I * Rp, st, [&] {
+        return launch_check_energy(E64d, E, I, Rp, K, d_flag.as<int>(), st);
+    }));
+
+    std::vector<long long> E64((size_t)I * Rp);
+    std::vector<uint8_t> hperm((size_t)I * Rp);
+    std::vector<unsigned long long> hacc((size_t)I * Kp);
+    std::vector<int32_t> hmin(I);
+    int mismatch = 0;
+    SG_TRY_CUDA(cudaMemcpyAsync(E64.data(), d_E64.as<void>(), sizeof(long long) * E64.size(),
+                                cudaMemcpyDeviceToHost, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(hperm.data(), perm, hperm.size(), cudaMemcpyDeviceToHost, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(hacc.data(), acc, sizeof(unsigned long long) * hacc.size(),
+                                cudaMemcpyDeviceToHost, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(hmin.data(), minE, sizeof(int32_t) * I, cudaMemcpyDeviceToHost, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(&mismatch, d_flag.as<void>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    for (int a = 0; a < I; ++a) {
+        sg_pt_result& o = outs[members[a]];
+        SG_RET(emit_spins(spins, a, N, Rp, K, o.spins, o.spins_mem, st, &d_stage, &log));
+        if (o.spins && o.spins_mem == SG_MEM_HOST) SG_TRY_CUDA(cudaStreamSynchronize(st));
+    }
+    SG_TRY_CUDA(cudaStreamSynchronize(st));
+    log.finish();
+    if (mismatch) {
+        set_error("incremental energies disagree with the recomputed energies (%d slots)", mismatch);
+        return SG_EINTERNAL;
+    }
+    for (int a = 0; a < I; ++a) {
+        const sg_instance* inst = insts[members[a]];
+        sg_pt_result& o = outs[members[a]];
+        for (int r = 0; r < K; ++r) {
+            if (o.E) o.E[r] = E64[(size_t)a * Rp + r];
+            if (o.perm) o.perm[r] = hperm[(size_t)a * Rp + r];
+        }
+        if (o.accepts)
+            for (int k = 0; k + 1 < K; ++k) o.accepts[k] = (int64_t)hacc[(size_t)a * Kp + k];
+        o.minE = hmin[a];
+        o.min_eps = eps_of(o.minE, inst->e_gs);
+    }
+    return SG_OK;
+}
+
+}  // namespace
+}  // namespace sg
+
+using namespace sg;
+
+extern "C" const char* sg_last_error_string(void) { return g_err; }
+
+extern "C" int32_t sg_version(void) { return 100; }
+
+extern "C" int32_t sg_stats_enable(int32_t timing)
+{
+    clear_error();
+    std::lock_guard<std::mutex> g(stats().mu);
+    stats().timing = timing != 0;
+    return SG_OK;
+}
+
+extern "C" int32_t sg_stats_read(sg_kernel_stats* out, int32_t reset)
+{
+    clear_error();
+    if (!out) {
+        set_error("NULL argument");
+        return SG_EINVAL;
+    }
+    std::lock_guard<std::mutex> g(stats().mu);
+    *out = stats().totals;
+    if (reset) stats().totals = sg_kernel_stats{};
+    return SG_OK;
+}
+
+extern "C" int32_t sg_sa_run_batch(const sg_instance* const* insts, const sg_sa_params* ps, int32_t n,
+                                   sg_sa_result* outs, void* stream)
+{
+    clear_error();
+    if (n < 0 || (n > 0 && (!insts || !ps || !outs))) {
+        set_error("bad batch arguments");
+        return SG_EINVAL;
+    }
+    for (int a = 0; a < n; ++a) SG_RET(check_sa(insts[a], &ps[a], &outs[a]));
+    cudaStream_t st = (cudaStream_t)stream;
+    // group instances that can share launches
+    std::map<std::tuple<int, int, int, double, double, int>, std::vector<int>> groups;
+    for (int a = 0; a < n; ++a) {
+        const sg_sa_params& p = ps[a];
+        groups[std::make_tuple(insts[a]->L, p.replicas, p.sweeps, p.beta0, p.beta1, p.schedule)]
+            .push_back(a);
+    }
+    for (auto& g : groups)
+        for (size_t at = 0; at < g.second.size(); at += kMaxGroup) {
+            std::vector<int> part(g.second.begin() + at,
+                                  g.second.begin() + std::min(g.second.size(), at + kMaxGroup));
+            SG_RET(run_sa_group(part, insts, ps, outs, st));
+        }
+    return SG_OK;
+}
+
+extern "C" int32_t sg_sa_run(const sg_instance* inst, const sg_sa_params* p, sg_sa_result* out,
+                             void* stream)
+{
+    return sg_sa_run_batch(&inst, p, 1, out, stream);
+}
+
+extern "C" int32_t sg_pt_run_batch(const sg_instance* const* insts, const sg_pt_params* ps, int32_t n,
+                                   sg_pt_result* outs, void* stream)
+{
+    clear_error();
+    if (n < 0 || (n > 0 && (!insts || !ps || !outs))) {
+        set_error("bad batch arguments");
+        return SG_EINVAL;
+    }
+    for (int a = 0; a < n; ++a) SG_RET(check_pt(insts[a], &ps[a], &outs[a]));
+    cudaStream_t st = (cudaStream_t)stream;
+    std::map<std::tuple<int, int, int, double, double>, std::vector<int>> groups;
+    for (int a = 0; a < n; ++a) {
+        const sg_pt_params& p = ps[a];
+        groups[std::make_tuple(insts[a]->L, p.temps, p.sweeps, p.beta_min, p.beta_max)].push_back(a);
+    }
+    for (auto& g : groups)
+        for (size_t at = 0; at < g.second.size(); at += kMaxGroup) {
+            std::vector<int> part(g.second.begin() + at,
+                                  g.second.begin() + std::min(g.second.size(), at + kMaxGroup));
+            SG_RET(run_pt_group(part, insts, ps, outs, st));
+        }
+    return SG_OK;
+}
+
+extern "C" int32_t sg_pt_run(const sg_instance* inst, const sg_pt_params* p, sg_pt_result* out,
+                             void* stream)
+{
+    return sg_pt_run_batch(&inst, p, 1, out, stream);
+}
+
+extern "C" int32_t sg_energy(const sg_instance* inst_c, const int8_t* spins, int32_t n_configs,
+                             int32_t mem_kind, int64_t* E_out, void* stream)
+{
+    clear_error();
+    if (!inst_c || !E_out || n_configs < 0 || (n_configs > 0 && !spins) ||
+        (mem_kind != SG_MEM_HOST && mem_kind != SG_MEM_DEVICE)) {
+        set_error("bad sg_energy arguments");
+        return SG_EINVAL;
+    }
+    if (n_configs == 0) return SG_OK;
+    if (n_configs > (1 << 20)) {
+        set_error("n_configs must be <= 2^20");
+        return SG_EINVAL;
+    }
+    sg_instance* inst = const_cast<sg_instance*>(inst_c);
+    cudaStream_t st = (cudaStream_t)stream;
+    const int64_t N = inst->N;
+    const int R = n_configs, Wn = (R + 3) / 4, Rp = 4 * Wn;
+    const uint2* j6 = nullptr;
+    SG_RET(instance_device_j6(inst, st, &j6));
+    DevBuf d_in, d_packed, d_E64, d_j6, d_bad;
+    const int8_t* src = spins;
+    if (mem_kind == SG_MEM_HOST) {
+        SG_RET(d_in.alloc((size_t)R * N, st));
+        SG_TRY_CUDA(cudaMemcpyAsync(d_in.as<void>(), spins, (size_t)R * N, cudaMemcpyHostToDevice, st));
+        src = d_in.as<int8_t>();
+    }
+    SG_RET(d_packed.alloc((size_t)Rp * N, st));
+    SG_RET(d_E64.alloc(sizeof(unsigned long long) * Rp, st));
+    SG_RET(d_j6.alloc(sizeof(uint2*), st));
+    SG_RET(d_bad.alloc(sizeof(int), st));
+    SG_TRY_CUDA(cudaMemcpyAsync(d_j6.as<void>(), &j6, sizeof(uint2*), cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * Rp, st));
+    SG_TRY_CUDA(cudaMemsetAsync(d_bad.as<void>(), 0, sizeof(int), st));
+    LaunchLog log;
+    SG_RET(log.run(SG_KERNEL_OTHER, (int64_t)Rp * N, st, [&] {
+        return launch_pack_spins(src, d_packed.as<int8_t>(), N, Rp, R, d_bad.as<int>(), st);
+    }));
+    SG_RET(log.run(SG_KERNEL_ENERGY, (int64_t)Rp * N, st, [&] {
+        return launch_energy(d_packed.as<int8_t>(), d_j6.as<const uint2*>(), 1, inst->L, Wn,
+                             d_E64.as<unsigned long long>(), st);
+    }));
+    std::vector<long long> E((size_t)Rp);
+    int bad = 0;
+    SG_TRY_CUDA(cudaMemcpyAsync(E.data(), d_E64.as<void>(), sizeof(long long) * Rp,
+                                cudaMemcpyDeviceToHost, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(&bad, d_bad.as<void>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    SG_TRY_CUDA(cudaStreamSynchronize(st));
+    log.finish();
+    if (bad) {
+        set_error("%d spin values are not -1 or +1", bad);
+        return SG_EINVAL;
+    }
+    for (int r = 0; r < R; ++r) E_out[r] = E[r];
+    return SG_OK;
+}

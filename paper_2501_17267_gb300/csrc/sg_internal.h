@@ -1,0 +1,114 @@
+// sg_internal.h -- internal declarations shared by the libsg translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/sg.h"
+
+namespace sg {
+
+// ---- error reporting (thread-local message behind sg_last_error_string) ----
+void set_error(const char* fmt, ...);
+void clear_error();
+
+struct Status {
+    int32_t code = SG_OK;
+    bool ok() const { return code == SG_OK; }
+};
+
+#define SG_TRY_CUDA(expr)                                                          \
+    do {                                                                           \
+        cudaError_t _e = (expr);                                                   \
+        if (_e != cudaSuccess) {                                                   \
+            ::sg::set_error("%s failed: %s (%s:%d)", #expr, cudaGetErrorString(_e), \
+                            __FILE__, __LINE__);                                   \
+            return SG_ECUDA;                                                       \
+        }                                                                          \
+    } while (0)
+
+// ---- instances ----
+struct DeviceCopy {
+    int device = -1;
+    uint2* j6 = nullptr;  // [N] per-site record of the six couplings (see kernels.cu)
+};
+
+}  // namespace sg
+
+struct sg_instance {
+    int32_t L = 0;
+    int64_t N = 0;
+    int64_t e_gs = 0;
+    std::vector<int8_t> J3;      // [N][3]
+    std::vector<int8_t> planted; // [N]
+    int32_t abs_sum = 0;         // sum over edges of |J| (bounds energy gaps)
+    std::mutex mu;               // guards dev
+    std::vector<sg::DeviceCopy> dev;
+};
+
+namespace sg {
+
+// Host tile-planting generator (Sec. II).  Returns SG_OK or SG_EINVAL.
+int32_t generate_instance(int L, uint64_t seed, const double class_prob[3], int gauge,
+                          int8_t* J3, int8_t* planted, int64_t* e_gs);
+
+// ---- schedules and acceptance tables (host) ----
+// Metropolis thresholds for one beta: thr[k] = min(floor(2^32 exp(-beta*2k)), 2^32-1),
+// k = 0..kMaxK (the accepted energy increase is dE = 2k; entry 0 is unused).
+constexpr int kMaxK = 6 * SG_JMAX;  // largest |x| = sum of |J| over six neighbours
+constexpr int kThrRow = 16;         // padded row length of a threshold table
+void beta_schedule(int S, double b0, double b1, int geometric, double* beta);
+void metropolis_row(double beta, uint32_t* row /* kThrRow */);
+uint32_t exchange_threshold(double dbeta, int64_t d);
+
+// PT exchange tables: per rung pair k, T_k(d) for d >= 1 is tab[off[k] + d - 1] when
+// d <= len[k], else tail[k].
+struct ExchangeTables {
+    std::vector<uint32_t> tab;
+    std::vector<uint32_t> off, len, tail;
+};
+int32_t build_exchange_tables(const std::vector<double>& ladder, int64_t dmax,
+                              ExchangeTables* out);
+
+// Per-instance device copy of the six-coupling records, uploaded on first use.
+int32_t instance_device_j6(sg_instance* inst, cudaStream_t stream, const uint2** out);
+
+// ---- kernels (kernels.cu) ----
+struct RunKeys {
+    uint32_t k0, k1;
+};
+
+int32_t launch_prepare_j6(const int8_t* J3_dev, uint2* j6_dev, int L, cudaStream_t st);
+int32_t launch_init_spins(int8_t* spins, const RunKeys* keys_dev, int I, int64_t N, int Wn,
+                          int R, cudaStream_t st);
+int32_t launch_energy(const int8_t* spins, const uint2* const* j6_ptrs, int I, int L, int Wn,
+                      unsigned long long* E_out /* [I][Wn*4] */, cudaStream_t st);
+int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
+                             const uint32_t* thr_row /* kThrRow */, int32_t* E, int I, int L,
+                             int Wn, int R, uint32_t sweep, int colour, cudaStream_t st);
+int32_t launch_half_sweep_pt(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
+                             const uint32_t* thr_rungs /* [K][kThrRow] */,
+                             const uint8_t* rung_of_slot /* [I][Wn*4] */, int32_t* E, int I,
+                             int L, int Wn, int K, uint32_t sweep, int colour, cudaStream_t st);
+int32_t launch_pt_exchange(const RunKeys* keys, const int32_t* E, uint8_t* rung_of_slot,
+                           uint8_t* slot_of_rung, unsigned long long* accepts,
+                           int32_t* minE, const uint32_t* xtab, const uint32_t* xoff,
+                           const uint32_t* xlen, const uint32_t* xtail, int I, int Rp, int K,
+                           uint32_t sweep, cudaStream_t st);
+int32_t launch_pt_setup(const unsigned long long* E64, int32_t* E, uint8_t* rung_of_slot,
+                        uint8_t* slot_of_rung, unsigned long long* accepts, int32_t* minE,
+                        int I, int Rp, int K, cudaStream_t st);
+int32_t launch_check_energy(const unsigned long long* E64, const int32_t* E, int I, int Rp,
+                            int R, int* mismatch, cudaStream_t st);
+int32_t launch_narrow_energy(const unsigned long long* E64, int32_t* E, int64_t n, cudaStream_t st);
+int32_t launch_unpack_spins(const int8_t* spins, int8_t* out, int64_t N, int Rp, int R,
+                            int I_index, int I, cudaStream_t st);
+int32_t launch_pack_spins(const int8_t* in, int8_t* spins, int64_t N, int Rp, int R,
+                          int* bad, cudaStream_t st);
+
+}  // namespace sg

@@ -1,0 +1,306 @@
+"""Thin ctypes binding of libsg (C ABI in include/sg.h).
+
+Argument marshalling only: every step of the path runs in the CUDA library.
+Host arrays are numpy; device arrays are torch CUDA tensors (PyTorch supplies
+device memory and the current stream, nothing else).  Importing this module
+loads ``libsg.so`` and raises if it has not been built -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsg.so")
+
+SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_ETIMEOUT, SG_EBUSY, SG_EINTERNAL = 0, -1, -2, -3, -4, -5, -6
+SG_PENDING = 1
+SG_MEM_HOST, SG_MEM_DEVICE = 0, 1
+SG_SCHEDULE_LINEAR, SG_SCHEDULE_GEOMETRIC = 0, 1
+SG_JMAX = 2
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(
+        f"{LIB_PATH} is missing: build the CUDA library first "
+        "(python -c 'import __graft_entry__ as g; g.build()')")
+_lib = ctypes.CDLL(LIB_PATH)
+
+_P = ctypes.c_void_p
+
+
+class InstanceDesc(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("gauge", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("class_prob", ctypes.c_double * 3)]
+
+
+class SAParams(ctypes.Structure):
+    _fields_ = [("replicas", ctypes.c_int32), ("sweeps", ctypes.c_int32),
+                ("beta0", ctypes.c_double), ("beta1", ctypes.c_double),
+                ("schedule", ctypes.c_int32), ("instance_id", ctypes.c_uint32),
+                ("seed", ctypes.c_uint64)]
+
+
+class SAResult(ctypes.Structure):
+    _fields_ = [("E", _P), ("eps", _P), ("spins", _P), ("spins_mem", ctypes.c_int32)]
+
+
+class PTParams(ctypes.Structure):
+    _fields_ = [("temps", ctypes.c_int32), ("sweeps", ctypes.c_int32),
+                ("beta_min", ctypes.c_double), ("beta_max", ctypes.c_double),
+                ("instance_id", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+class PTResult(ctypes.Structure):
+    _fields_ = [("E", _P), ("perm", _P), ("accepts", _P), ("minE", ctypes.c_int64),
+                ("min_eps", ctypes.c_double), ("spins", _P), ("spins_mem", ctypes.c_int32)]
+
+
+KERNEL_KINDS = ("init", "energy", "sweep", "exchange", "other")
+
+
+class KernelStats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 5), ("device_ms", ctypes.c_double * 5),
+                ("units", ctypes.c_int64 * 5)]
+
+
+_SIGS = {
+    "sg_instance_create": [ctypes.POINTER(InstanceDesc), ctypes.POINTER(_P)],
+    "sg_instance_create_from_couplings": [ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int64,
+                                          ctypes.POINTER(_P)],
+    "sg_instance_get": [_P, _P, _P, _P, _P],
+    "sg_instance_destroy": [_P],
+    "sg_sa_run": [_P, ctypes.POINTER(SAParams), ctypes.POINTER(SAResult), _P],
+    "sg_sa_run_batch": [_P, _P, ctypes.c_int32, _P, _P],
+    "sg_pt_run": [_P, ctypes.POINTER(PTParams), ctypes.POINTER(PTResult), _P],
+    "sg_pt_run_batch": [_P, _P, ctypes.c_int32, _P, _P],
+    "sg_energy": [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P],
+    "sg_version": [],
+    "sg_stats_enable": [ctypes.c_int32],
+    "sg_stats_read": [ctypes.POINTER(KernelStats), ctypes.c_int32],
+}
+for _name, _args in _SIGS.items():
+    _fn = getattr(_lib, _name)
+    _fn.argtypes = _args
+    _fn.restype = ctypes.c_int32
+_lib.sg_last_error_string.argtypes = []
+_lib.sg_last_error_string.restype = ctypes.c_char_p
+
+EXPORTED = list(_SIGS) + ["sg_last_error_string"]
+
+
+class SGError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libsg error {code}: {msg}")
+        self.code = code
+
+
+def _check(rc: int):
+    if rc != SG_OK:
+        raise SGError(rc, _lib.sg_last_error_string().decode())
+
+
+def last_error_string() -> str:
+    return _lib.sg_last_error_string().decode()
+
+
+def version() -> int:
+    return int(_lib.sg_version())
+
+
+def _np_ptr(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    return a.ctypes.data_as(_P)
+
+
+def _stream_handle(stream):
+    """cudaStream_t of `stream` (a torch.cuda.Stream), else torch's current stream."""
+    if stream is not None:
+        return _P(stream.cuda_stream)
+    try:
+        import torch
+        if torch.cuda.is_available() and torch.cuda.is_initialized():
+            return _P(torch.cuda.current_stream().cuda_stream)
+    except ImportError:
+        pass
+    return _P(0)
+
+
+def _is_torch_cuda(x) -> bool:
+    return hasattr(x, "is_cuda") and bool(x.is_cuda)
+
+
+class Instance:
+    """Owned sg_instance handle (tile-planted, or wrapped couplings)."""
+
+    def __init__(self, handle: int):
+        self._h = _P(handle)
+        L = ctypes.c_int32()
+        egs = ctypes.c_int64()
+        _check(_lib.sg_instance_get(self._h, ctypes.byref(L), None, None, ctypes.byref(egs)))
+        self.L = int(L.value)
+        self.N = self.L ** 3
+        self.e_gs = int(egs.value)
+
+    @classmethod
+    def create(cls, L: int, seed: int, class_prob=(1 / 3, 1 / 3, 1 / 3), gauge: bool = True):
+        d = InstanceDesc(L, int(bool(gauge)), seed, (ctypes.c_double * 3)(*class_prob))
+        h = _P()
+        _check(_lib.sg_instance_create(ctypes.byref(d), ctypes.byref(h)))
+        return cls(h.value)
+
+    @classmethod
+    def from_couplings(cls, L: int, J3, e_gs: int = 0):
+        """J3: int8 (L^3, 3), numpy (host) or torch CUDA tensor (device)."""
+        h = _P()
+        if _is_torch_cuda(J3):
+            assert J3.is_contiguous() and J3.numel() == 3 * L ** 3
+            _check(_lib.sg_instance_create_from_couplings(L, _P(J3.data_ptr()), SG_MEM_DEVICE,
+                                                          e_gs, ctypes.byref(h)))
+        else:
+            J3 = np.ascontiguousarray(J3, dtype=np.int8)
+            assert J3.size == 3 * L ** 3
+            _check(_lib.sg_instance_create_from_couplings(L, _np_ptr(J3), SG_MEM_HOST, e_gs,
+                                                          ctypes.byref(h)))
+        return cls(h.value)
+
+    def get(self):
+        """-> (J3 int8 (N,3), planted int8 (N,), e_gs)."""
+        J3 = np.zeros((self.N, 3), dtype=np.int8)
+        planted = np.zeros(self.N, dtype=np.int8)
+        egs = ctypes.c_int64()
+        _check(_lib.sg_instance_get(self._h, None, _np_ptr(J3), _np_ptr(planted), ctypes.byref(egs)))
+        return J3, planted, int(egs.value)
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            _lib.sg_instance_destroy(self._h)
+            self._h = _P()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _spins_target(spins, n_rows: int, N: int):
+    """spins: None | 'host' | 'device' | numpy array | torch CUDA tensor -> (obj, ptr, mem)."""
+    if spins is None:
+        return None, None, SG_MEM_HOST
+    if isinstance(spins, str):
+        if spins == "host":
+            spins = np.zeros((n_rows, N), dtype=np.int8)
+        elif spins == "device":
+            import torch
+            spins = torch.empty((n_rows, N), dtype=torch.int8, device="cuda")
+        else:
+            raise ValueError(spins)
+    if _is_torch_cuda(spins):
+        assert spins.is_contiguous() and spins.numel() == n_rows * N
+        return spins, _P(spins.data_ptr()), SG_MEM_DEVICE
+    assert spins.dtype == np.int8 and spins.flags["C_CONTIGUOUS"] and spins.size == n_rows * N
+    return spins, _np_ptr(spins), SG_MEM_HOST
+
+
+def _sa_params(replicas, sweeps, beta0, beta1, schedule, seed, instance_id):
+    sch = {"linear": SG_SCHEDULE_LINEAR, "geometric": SG_SCHEDULE_GEOMETRIC}.get(schedule, schedule)
+    return SAParams(replicas, sweeps, beta0, beta1, sch, instance_id, seed)
+
+
+def sa_run_batch(insts, params, spins=None, stream=None):
+    """Anneal several instances in one call.
+
+    params: list of dicts with keys replicas, sweeps, beta0, beta1, schedule, seed,
+    instance_id.  spins: None, 'host', 'device', or a list of per-instance targets.
+    Returns a list of dicts {E, eps, spins}.
+    """
+    n = len(insts)
+    HandleArr = _P * n
+    handles = HandleArr(*[i.handle.value for i in insts])
+    ps = (SAParams * n)(*[_sa_params(**p) for p in params])
+    outs = (SAResult * n)()
+    keep = []
+    for a, (inst, p) in enumerate(zip(insts, params)):
+        E = np.zeros(p["replicas"], dtype=np.int64)
+        eps = np.zeros(p["replicas"], dtype=np.float64)
+        tgt = spins[a] if isinstance(spins, (list, tuple)) else spins
+        obj, ptr, mem = _spins_target(tgt, p["replicas"], inst.N)
+        outs[a] = SAResult(_np_ptr(E), _np_ptr(eps), ptr, mem)
+        keep.append({"E": E, "eps": eps, "spins": obj})
+    _check(_lib.sg_sa_run_batch(handles, ps, n, outs, _stream_handle(stream)))
+    return keep
+
+
+def sa_run(inst: Instance, replicas: int, sweeps: int, beta0: float, beta1: float,
+           schedule="linear", seed: int = 0, instance_id: int = 0, spins=None, stream=None):
+    p = dict(replicas=replicas, sweeps=sweeps, beta0=beta0, beta1=beta1, schedule=schedule,
+             seed=seed, instance_id=instance_id)
+    return sa_run_batch([inst], [p], spins=[spins], stream=stream)[0]
+
+
+def pt_run_batch(insts, params, spins=None, stream=None):
+    """Parallel tempering of several instances.  params: dicts with temps, sweeps,
+    beta_min, beta_max, seed, instance_id.  Returns dicts {E, perm, accepts, minE,
+    min_eps, spins} (E, perm, spins by slot)."""
+    n = len(insts)
+    handles = (_P * n)(*[i.handle.value for i in insts])
+    ps = (PTParams * n)(*[PTParams(p["temps"], p["sweeps"], p["beta_min"], p["beta_max"],
+                                   p.get("instance_id", 0), p.get("seed", 0)) for p in params])
+    outs = (PTResult * n)()
+    keep = []
+    for a, (inst, p) in enumerate(zip(insts, params)):
+        K = p["temps"]
+        E = np.zeros(K, dtype=np.int64)
+        perm = np.zeros(K, dtype=np.int32)
+        acc = np.zeros(max(K - 1, 1), dtype=np.int64)
+        tgt = spins[a] if isinstance(spins, (list, tuple)) else spins
+        obj, ptr, mem = _spins_target(tgt, K, inst.N)
+        outs[a] = PTResult(_np_ptr(E), _np_ptr(perm), _np_ptr(acc), 0, 0.0, ptr, mem)
+        keep.append({"E": E, "perm": perm, "accepts": acc[: max(K - 1, 0)], "spins": obj})
+    _check(_lib.sg_pt_run_batch(handles, ps, n, outs, _stream_handle(stream)))
+    for a in range(n):
+        keep[a]["minE"] = int(outs[a].minE)
+        keep[a]["min_eps"] = float(outs[a].min_eps)
+    return keep
+
+
+def pt_run(inst: Instance, temps: int, sweeps: int, beta_min: float, beta_max: float,
+           seed: int = 0, instance_id: int = 0, spins=None, stream=None):
+    p = dict(temps=temps, sweeps=sweeps, beta_min=beta_min, beta_max=beta_max, seed=seed,
+             instance_id=instance_id)
+    return pt_run_batch([inst], [p], spins=[spins], stream=stream)[0]
+
+
+def energy(inst: Instance, spins, stream=None) -> np.ndarray:
+    """Energies (Eq. 1) of configurations spins (n, N): numpy host or torch CUDA."""
+    if _is_torch_cuda(spins):
+        assert spins.is_contiguous() and spins.numel() % inst.N == 0
+        n = spins.numel() // inst.N
+        ptr, mem = _P(spins.data_ptr()), SG_MEM_DEVICE
+    else:
+        spins = np.ascontiguousarray(spins, dtype=np.int8)
+        n = spins.size // inst.N
+        ptr, mem = _np_ptr(spins), SG_MEM_HOST
+    E = np.zeros(n, dtype=np.int64)
+    _check(_lib.sg_energy(inst.handle, ptr, n, mem, _np_ptr(E), _stream_handle(stream)))
+    return E
+
+
+def stats_enable(timing: bool):
+    """Time every later launch with CUDA events on its own stream (process-wide)."""
+    _check(_lib.sg_stats_enable(int(bool(timing))))
+
+
+def stats_read(reset: bool = False) -> dict:
+    """Launch counts, summed device milliseconds and work units per kernel kind."""
+    st = KernelStats()
+    _check(_lib.sg_stats_read(ctypes.byref(st), int(bool(reset))))
+    return {k: {"launches": int(st.launches[i]), "device_ms": float(st.device_ms[i]),
+                "units": int(st.units[i])} for i, k in enumerate(KERNEL_KINDS)}

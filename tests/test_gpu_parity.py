@@ -1,0 +1,182 @@
+"""GPU parity: the CUDA path through the C ABI against the CPU oracle.
+
+All couplings and spins are integers and every accept decision is an integer
+compare of the same Philox word against the same threshold, so the bar is
+bit-exact: spins, energies, eps, PT permutations, swap counts and minimum
+energies must be identical.
+"""
+import numpy as np
+import pytest
+
+from oracle import oracle as o
+from paper_2501_17267_gb300 import workloads as wl
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def sg():
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    from paper_2501_17267_gb300 import build
+    build.build()
+    from paper_2501_17267_gb300 import sg as mod
+    return mod
+
+
+def _sa_compare(sg, inst, J3, egs, R, S, b0, b1, geometric=False, seed=0, iid=0, reps=None):
+    res = sg.sa_run(inst, R, S, b0, b1, "geometric" if geometric else "linear", seed, iid,
+                    spins="host")
+    reps = list(range(R)) if reps is None else reps
+    ospins, oE = o.sa_run(inst.L, J3, seed, iid, S, b0, b1, geometric, reps=reps)
+    assert np.array_equal(res["spins"][reps], ospins)
+    assert np.array_equal(res["E"][reps], oE)
+    for n, r in enumerate(reps):
+        assert res["eps"][r] == o.epsilon(int(oE[n]), egs)
+    return res
+
+
+def test_sa_L4_R8_S1000_full(sg):
+    """Workload: L=4, 8 replicas, 1000 sweeps, beta linear 0.1 -> 3.0, seed 0 -- all outputs."""
+    w = wl.SA_L4
+    inst = sg.Instance.create(w.L, w.instance_seed(0), w.class_prob, True)
+    J3, _, egs = inst.get()
+    res = _sa_compare(sg, inst, J3, egs, w.replicas, w.sweeps, w.beta0, w.beta1, seed=w.run_seed)
+    assert (res["E"] >= egs).all()
+
+
+def test_sa_L16_R1024_S1000_sampled(sg):
+    """Workload: L=16, 1024 replicas, 1000 sweeps -- full run on the GPU, replicas sampled
+    across every 4-replica word position and both ends checked against the oracle."""
+    w = wl.SA_L16
+    inst = sg.Instance.create(w.L, w.instance_seed(0), w.class_prob, True)
+    J3, _, egs = inst.get()
+    reps = [0, 1, 2, 3, 257, 514, 771, 1020, 1021, 1022, 1023]
+    res = _sa_compare(sg, inst, J3, egs, w.replicas, w.sweeps, w.beta0, w.beta1, reps=reps)
+    assert (res["E"] >= egs).all()
+    # every replica's reported energy equals a recompute of its spins
+    assert np.array_equal(sg.energy(inst, res["spins"]), res["E"])
+
+
+@pytest.mark.parametrize("L,R,S,geo", [(2, 5, 40, False), (6, 13, 30, True), (10, 7, 25, False),
+                                       (12, 4, 20, True), (8, 1, 60, False)])
+def test_sa_ragged_shapes(sg, L, R, S, geo):
+    """Ragged replica counts (R not a multiple of 4), L=2 multi-edges, several tiles."""
+    inst = sg.Instance.create(L, 1000 + L, wl.UNIFORM, True)
+    J3, _, egs = inst.get()
+    _sa_compare(sg, inst, J3, egs, R, S, 0.2, 2.5, geometric=geo, seed=77 + L, iid=L)
+
+
+def test_sa_zero_sweeps_is_initial_state(sg):
+    inst = sg.Instance.create(6, 5)
+    J3, _, egs = inst.get()
+    _sa_compare(sg, inst, J3, egs, 9, 0, 0.5, 1.0, seed=3)
+
+
+@pytest.mark.parametrize("cls", [(1, 0, 0), (0, 1, 0), (0, 0, 1)])
+def test_sa_single_class_instances(sg, cls):
+    inst = sg.Instance.create(8, 42, cls, True)
+    J3, _, egs = inst.get()
+    _sa_compare(sg, inst, J3, egs, 8, 40, 0.3, 3.0, geometric=True, seed=9)
+
+
+def test_sa_general_couplings(sg):
+    """|J| in {0, 1, 2}: exercises the magnitude path of the kernel."""
+    L = 6
+    J3 = wl.random_couplings(21, L, jmax=2, allow_zero=True)
+    inst = sg.Instance.from_couplings(L, J3, e_gs=-1)
+    _sa_compare(sg, inst, J3, -1, 12, 30, 0.1, 2.0, seed=5)
+
+
+def test_sa_batch_equals_separate(sg):
+    insts = [sg.Instance.create(L, 70 + L) for L in (4, 6, 4)]
+    params = [dict(replicas=8, sweeps=30, beta0=0.1, beta1=3.0, schedule="linear", seed=1,
+                   instance_id=k) for k in range(3)]
+    batch = sg.sa_run_batch(insts, params, spins="host")
+    for inst, p, b in zip(insts, params, batch):
+        single = sg.sa_run(inst, spins="host", **p)
+        assert np.array_equal(single["spins"], b["spins"])
+        assert np.array_equal(single["E"], b["E"])
+
+
+def test_sa_device_spins_output(sg):
+    import torch
+    inst = sg.Instance.create(8, 3)
+    a = sg.sa_run(inst, 12, 20, 0.2, 2.0, spins="host", seed=4)
+    b = sg.sa_run(inst, 12, 20, 0.2, 2.0, spins="device", seed=4)
+    assert isinstance(b["spins"], torch.Tensor)
+    assert np.array_equal(a["spins"], b["spins"].cpu().numpy())
+
+
+def _pt_compare(sg, inst, J3, egs, K, S, bmin, bmax, seed=0, iid=0, res=None):
+    if res is None:
+        res = sg.pt_run(inst, K, S, bmin, bmax, seed, iid, spins="host")
+    ref = o.pt_run(inst.L, J3, seed, iid, K, S, bmin, bmax)
+    assert np.array_equal(res["spins"], ref["spins"])
+    assert np.array_equal(res["E"], ref["E"])
+    assert np.array_equal(res["perm"], ref["perm"])
+    assert np.array_equal(res["accepts"], ref["accepts"])
+    assert res["minE"] == ref["minE"]
+    assert res["min_eps"] == o.epsilon(ref["minE"], egs)
+    return res
+
+
+@pytest.mark.parametrize("L,K,S", [(4, 5, 60), (8, 8, 40), (6, 1, 20), (2, 3, 30), (10, 11, 15)])
+def test_pt_small(sg, L, K, S):
+    inst = sg.Instance.create(L, 500 + L, wl.UNIFORM, True)
+    J3, _, egs = inst.get()
+    _pt_compare(sg, inst, J3, egs, K, S, 0.2, 3.0, seed=11, iid=L)
+
+
+def test_pt_equal_rungs(sg):
+    inst = sg.Instance.create(4, 9)
+    J3, _, egs = inst.get()
+    res = _pt_compare(sg, inst, J3, egs, 4, 30, 1.3, 1.3, seed=2)
+    assert list(res["accepts"]) == [15, 15, 15]
+
+
+def test_pt_L64_K32_truncated(sg):
+    """Workload geometry (L=64, 32 temperatures, beta 0.2 -> 3.0), first 3 sweeps, one
+    instance, checked in full against the oracle."""
+    w = wl.PT_L64
+    inst = sg.Instance.create(w.L, w.instance_seed(0), w.class_prob, True)
+    J3, _, egs = inst.get()
+    _pt_compare(sg, inst, J3, egs, w.temps, 3, w.beta_min, w.beta_max, seed=w.run_seed, iid=0)
+
+
+def test_pt_batch_equals_separate_and_oracle(sg):
+    """16 instances at L=16 in one batch: identical to separate runs; two checked
+    against the oracle."""
+    insts = [sg.Instance.create(16, 2 ** 33 + k) for k in range(16)]
+    params = [dict(temps=12, sweeps=8, beta_min=0.2, beta_max=3.0, seed=3, instance_id=k)
+              for k in range(16)]
+    batch = sg.pt_run_batch(insts, params, spins="host")
+    for k in (0, 11):
+        J3, _, egs = insts[k].get()
+        _pt_compare(sg, insts[k], J3, egs, 12, 8, 0.2, 3.0, seed=3, iid=k, res=batch[k])
+    for k in (5, 15):
+        single = sg.pt_run(insts[k], spins="host", **params[k])
+        assert np.array_equal(single["spins"], batch[k]["spins"])
+        assert single["minE"] == batch[k]["minE"]
+
+
+def test_energy_parity(sg):
+    for L, jmax in [(2, 2), (4, 1), (6, 2), (10, 2)]:
+        J3 = wl.random_couplings(L, L, jmax=jmax)
+        inst = sg.Instance.from_couplings(L, J3)
+        spins = wl.random_spins(L + 1, (7, L ** 3))
+        E = sg.energy(inst, spins)
+        assert [o.energy(L, J3, s) for s in spins] == list(E)
+
+
+def test_energy_device_input_and_validation(sg):
+    import torch
+    inst = sg.Instance.create(6, 1)
+    J3, tau, egs = inst.get()
+    s = torch.from_numpy(np.stack([tau, -tau, np.ones_like(tau)])).cuda()
+    E = sg.energy(inst, s)
+    assert E[0] == egs and E[1] == egs  # global flip leaves E unchanged
+    bad = np.zeros((1, 216), dtype=np.int8)
+    with pytest.raises(sg.SGError) as e:
+        sg.energy(inst, bad)
+    assert e.value.code == sg.SG_EINVAL

@@ -1,0 +1,93 @@
+"""Host-side tests of libsg (no GPU): the C ABI loads and exports every declared
+symbol, the host tile-planting generator agrees byte for byte with the oracle's
+independent generator, and invalid arguments are rejected before any device work."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from oracle import oracle as o
+from paper_2501_17267_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def sg():
+    from paper_2501_17267_gb300 import build
+    build.build()
+    from paper_2501_17267_gb300 import sg as mod
+    return mod
+
+
+def test_exports_every_declared_symbol(sg):
+    declared = set()
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        text = open(os.path.join(ROOT, "include", hdr)).read()
+        declared |= set(re.findall(r"^\s*(?:int32_t|const char\*)\s+(sg_\w+)\s*\(", text, re.M))
+    assert {"sg_instance_create", "sg_sa_run", "sg_pt_run", "sg_energy"} <= declared
+    lib = ctypes.CDLL(sg.LIB_PATH)
+    for name in sorted(declared):
+        assert hasattr(lib, name), name
+
+
+@pytest.mark.parametrize("L", [2, 4, 6, 12, 16])
+@pytest.mark.parametrize("cp,gauge", [(wl.UNIFORM, True), ((0, 0, 1), True), ((0.3, 0.7, 0), False),
+                                      ((0.5, 0, 0.5), True)])
+def test_generator_matches_oracle(sg, L, cp, gauge):
+    seed = 2 ** 32 * 3 + 17 * L
+    inst = sg.Instance.create(L, seed, cp, gauge)
+    J3, planted, egs = inst.get()
+    J3o, tauo, egso = o.generate(L, seed, cp, gauge)
+    assert egs == egso == inst.e_gs
+    assert np.array_equal(J3, J3o)
+    assert np.array_equal(planted, tauo)
+
+
+def test_workload_instances_match_oracle(sg):
+    for w in (wl.SA_L4, wl.SA_L16):
+        inst = sg.Instance.create(w.L, w.instance_seed(0), w.class_prob, True)
+        J3, planted, egs = inst.get()
+        J3o, tauo, egso = o.generate(w.L, w.instance_seed(0), w.class_prob, True)
+        assert np.array_equal(J3, J3o) and egs == egso
+
+
+def test_from_couplings_roundtrip(sg):
+    L = 6
+    J3 = wl.random_couplings(5, L, jmax=2)
+    inst = sg.Instance.from_couplings(L, J3, e_gs=-123)
+    J3b, planted, egs = inst.get()
+    assert np.array_equal(J3, J3b) and egs == -123 and (planted == 1).all()
+
+
+def test_invalid_arguments(sg):
+    with pytest.raises(sg.SGError) as e:
+        sg.Instance.create(5, 0)
+    assert e.value.code == sg.SG_EINVAL
+    assert "even" in sg.last_error_string()
+    with pytest.raises(sg.SGError):
+        sg.Instance.create(0, 0)
+    with pytest.raises(sg.SGError):
+        sg.Instance.create(4, 0, (-1, 1, 1))
+    with pytest.raises(sg.SGError):
+        sg.Instance.create(4, 0, (0, 0, 0))
+    bad = np.full((64, 3), 3, dtype=np.int8)
+    with pytest.raises(sg.SGError) as e:
+        sg.Instance.from_couplings(4, bad)
+    assert e.value.code == sg.SG_EINVAL
+    inst = sg.Instance.create(4, 1)
+    for kw in [dict(replicas=0), dict(sweeps=-1), dict(beta0=0.0), dict(beta1=-1.0),
+               dict(beta0=float("nan")), dict(schedule=7)]:
+        args = dict(replicas=4, sweeps=1, beta0=0.1, beta1=1.0)
+        args.update(kw)
+        with pytest.raises(sg.SGError) as e:
+            sg.sa_run(inst, **args)
+        assert e.value.code == sg.SG_EINVAL
+    for kw in [dict(temps=0), dict(temps=300), dict(beta_min=0.0), dict(sweeps=-2)]:
+        args = dict(temps=4, sweeps=1, beta_min=0.2, beta_max=3.0)
+        args.update(kw)
+        with pytest.raises(sg.SGError) as e:
+            sg.pt_run(inst, **args)
+        assert e.value.code == sg.SG_EINVAL
