@@ -125,9 +125,8 @@ typedef struct sg_sa_result {
     int32_t spins_mem;     /* SG_MEM_HOST or SG_MEM_DEVICE for `spins` */
 } sg_sa_result;
 
-/* Anneal R replicas of one instance for S sweeps.  The energy of each replica
- * is tracked incrementally on the device and checked against a full recompute at
- * the end (mismatch: SG_EINTERNAL).  Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA. */
+/* Anneal R replicas of one instance for S sweeps.  The energy of each replica is
+ * computed (Eq. 1) from its final spins.  Errors: SG_EINVAL, SG_ENOMEM, SG_ECUDA. */
 int32_t sg_sa_run(const sg_instance* inst, const sg_sa_params* p, sg_sa_result* out,
                   void* stream);
 
@@ -159,7 +158,9 @@ typedef struct sg_pt_result {
     int32_t spins_mem;
 } sg_pt_result;
 
-/* Run PT: after every sweep s, rung pairs (k, k+1) with k = s mod 2 attempt a
+/* Run PT: slot energies are tracked incrementally on the device (the exchange needs
+ * them after every sweep) and checked against a full recompute at the end
+ * (mismatch: SG_EINTERNAL).  After every sweep s, rung pairs (k, k+1) with k = s mod 2 attempt a
  * label swap, accepted when d = E_a - E_b <= 0 (slot a at rung k, b at k+1) or
  * when the draw u < floor(2^32 exp(-(beta_{k+1} - beta_k) d)).  Errors: SG_EINVAL
  * (also when the ladder is so fine that an exchange table would exceed 2^22

@@ -279,6 +279,8 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
         SG_RET(instance_device_j6(const_cast<sg_instance*>(insts[members[a]]), st, &j6[a]));
     }
 
+    bool unit_j = true;  // every coupling of the group has |J| = 1
+    for (int a = 0; a < I; ++a) unit_j &= insts[members[a]]->unit_couplings;
     DevBuf d_spins, d_E, d_E64, d_thr, d_keys, d_j6, d_flag, d_stage;
     SG_RET(d_spins.alloc((size_t)I * N * Rp, st));
     SG_RET(d_E.alloc(sizeof(int32_t) * (size_t)I * Rp, st));
@@ -307,22 +309,18 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
     LaunchLog log;
     const int64_t cells = (int64_t)I * N * Rp;
     unsigned long long* E64d = d_E64.as<unsigned long long>();
+    // SA keeps no per-sweep energies: the energy of every replica is computed once,
+    // from the final spins.
     SG_RET(log.run(SG_KERNEL_INIT, cells, st, [&] { return launch_init_spins(spins, kp, I, N, Wn, R, st); }));
-    SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st); }));
-    SG_RET(log.run(SG_KERNEL_OTHER, (int64_t)I * Rp, st, [&] {
-        return launch_narrow_energy(E64d, d_E.as<int32_t>(), (int64_t)I * Rp, st);
-    }));
     for (int s = 0; s < S; ++s)
         for (int c = 0; c < 2; ++c)
             SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * R, st, [&] {
                 return launch_half_sweep_sa(spins, j6p, kp, d_thr.as<uint32_t>() + (size_t)s * kThrRow,
-                                            d_E.as<int32_t>(), I, L, Wn, R, (uint32_t)s, c, st);
+                                            d_E.as<int32_t>(), unit_j, I, L, Wn, R, (uint32_t)s, c,
+                                            st);
             }));
     SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * (size_t)I * Rp, st));
     SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st); }));
-    SG_RET(log.run(SG_KERNEL_OTHER, (int64_t)I * Rp, st, [&] {
-        return launch_check_energy(E64d, d_E.as<int32_t>(), I, Rp, R, d_flag.as<int>(), st);
-    }));
 
     std::vector<long long> E64((size_t)I * Rp);
     int mismatch = 0;
@@ -382,6 +380,8 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
         SG_RET(instance_device_j6(const_cast<sg_instance*>(insts[members[a]]), st, &j6[a]));
     }
     const int Kp = std::max(K - 1, 1);
+    bool unit_j = true;
+    for (int a = 0; a < I; ++a) unit_j &= insts[members[a]]->unit_couplings;
     DevBuf d_spins, d_E, d_E64, d_thr, d_keys, d_j6, d_flag, d_stage, d_perm, d_inv, d_acc, d_min,
         d_xtab, d_xoff, d_xlen, d_xtail;
     SG_RET(d_spins.alloc((size_t)I * N * Rp, st));
@@ -436,8 +436,8 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     for (int s = 0; s < S; ++s) {
         for (int c = 0; c < 2; ++c)
             SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * K, st, [&] {
-                return launch_half_sweep_pt(spins, j6p, kp, d_thr.as<uint32_t>(), perm, E, I, L, Wn, K,
-                                            (uint32_t)s, c, st);
+                return launch_half_sweep_pt(spins, j6p, kp, d_thr.as<uint32_t>(), perm, E, unit_j, I,
+                                            L, Wn, K, (uint32_t)s, c, st);
             }));
         SG_RET(log.run(SG_KERNEL_EXCHANGE, (int64_t)I * (K / 2), st, [&] {
             return launch_pt_exchange(kp, E, perm, inv, acc, minE, d_xtab.as<uint32_t>(),

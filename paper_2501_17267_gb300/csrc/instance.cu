@@ -234,8 +234,13 @@ using namespace sg;
 static int32_t finish_instance(sg_instance* inst)
 {
     int64_t s = 0;
-    for (int8_t j : inst->J3) s += j < 0 ? -j : j;
+    bool unit = true;
+    for (int8_t j : inst->J3) {
+        s += j < 0 ? -j : j;
+        unit &= (j == 1 || j == -1);
+    }
     inst->abs_sum = (int32_t)s;
+    inst->unit_couplings = unit;
     return SG_OK;
 }
 

@@ -474,9 +474,12 @@ int32_t launch_energy(const int8_t* spins, const uint2* const* j6_ptrs, int I, i
 }
 
 int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
-                             const uint32_t* thr_row, int32_t* E, int I, int L, int Wn, int R,
-                             uint32_t sweep, int colour, cudaStream_t st)
+                             const uint32_t* thr_row, int32_t* E, bool unit_j, int I, int L, int Wn,
+                             int R, uint32_t sweep, int colour, cudaStream_t st)
 {
+    if (rows_kernel_supports(Wn))
+        return launch_sweep_rows_sa(spins, j6_ptrs, keys, thr_row, unit_j, I, L, Wn, R, sweep,
+                                    colour, st);
     const int64_t N = (int64_t)L * L * L;
     dim3 grid(sweep_grid_x((N / 2) * Wn, Wn), I);
     half_sweep_kernel<false><<<grid, kBlock, 0, st>>>((uint32_t*)spins, j6_ptrs, keys, thr_row,
@@ -486,9 +489,12 @@ int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs, const R
 
 int32_t launch_half_sweep_pt(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
-                             int I, int L, int Wn, int K, uint32_t sweep, int colour,
+                             bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
                              cudaStream_t st)
 {
+    if (rows_kernel_supports(Wn))
+        return launch_sweep_rows_pt(spins, j6_ptrs, keys, thr_rungs, rung_of_slot, E, unit_j, I, L,
+                                    Wn, K, sweep, colour, st);
     const int64_t N = (int64_t)L * L * L;
     dim3 grid(sweep_grid_x((N / 2) * Wn, Wn), I);
     half_sweep_kernel<true><<<grid, kBlock, 0, st>>>((uint32_t*)spins, j6_ptrs, keys, thr_rungs,

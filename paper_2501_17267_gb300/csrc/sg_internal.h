@@ -47,6 +47,7 @@ struct sg_instance {
     std::vector<int8_t> J3;      // [N][3]
     std::vector<int8_t> planted; // [N]
     int32_t abs_sum = 0;         // sum over edges of |J| (bounds energy gaps)
+    bool unit_couplings = false; // every coupling is +1 or -1
     std::mutex mu;               // guards dev
     std::vector<sg::DeviceCopy> dev;
 };
@@ -89,12 +90,24 @@ int32_t launch_init_spins(int8_t* spins, const RunKeys* keys_dev, int I, int64_t
 int32_t launch_energy(const int8_t* spins, const uint2* const* j6_ptrs, int I, int L, int Wn,
                       unsigned long long* E_out /* [I][Wn*4] */, cudaStream_t st);
 int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
-                             const uint32_t* thr_row /* kThrRow */, int32_t* E, int I, int L,
-                             int Wn, int R, uint32_t sweep, int colour, cudaStream_t st);
+                             const uint32_t* thr_row /* kThrRow */, int32_t* E, bool unit_j, int I,
+                             int L, int Wn, int R, uint32_t sweep, int colour, cudaStream_t st);
 int32_t launch_half_sweep_pt(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs /* [K][kThrRow] */,
-                             const uint8_t* rung_of_slot /* [I][Wn*4] */, int32_t* E, int I,
-                             int L, int Wn, int K, uint32_t sweep, int colour, cudaStream_t st);
+                             const uint8_t* rung_of_slot /* [I][Wn*4] */, int32_t* E, bool unit_j,
+                             int I, int L, int Wn, int K, uint32_t sweep, int colour,
+                             cudaStream_t st);
+// sweep.cu: row-mapped sweep kernel (used whenever it supports the word count)
+bool rows_kernel_supports(int Wn);
+// SA variant keeps no incremental energies (the run recomputes them at the end);
+// unit_j: every coupling of the group has |J| = 1.
+int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
+                             const uint32_t* thr_row, bool unit_j, int I, int L, int Wn, int R,
+                             uint32_t sweep, int colour, cudaStream_t st);
+int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
+                             const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
+                             bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
+                             cudaStream_t st);
 int32_t launch_pt_exchange(const RunKeys* keys, const int32_t* E, uint8_t* rung_of_slot,
                            uint8_t* slot_of_rung, unsigned long long* accepts,
                            int32_t* minE, const uint32_t* xtab, const uint32_t* xoff,
