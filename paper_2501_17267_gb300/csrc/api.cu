@@ -272,11 +272,15 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
     for (int s = 0; s < S; ++s) metropolis_row(beta[s], &thr[(size_t)s * kThrRow]);
 
     std::vector<RunKeys> keys(I);
-    std::vector<const uint2*> j6(I);
+    std::vector<const void*> jp(2 * (size_t)I);  // [I] six-coupling records, then [I] sign bytes
     for (int a = 0; a < I; ++a) {
         const sg_sa_params& q = ps[members[a]];
         keys[a] = make_key(q.seed, q.instance_id);
-        SG_RET(instance_device_j6(const_cast<sg_instance*>(insts[members[a]]), st, &j6[a]));
+        const uint2* j6 = nullptr;
+        const uint8_t* j1 = nullptr;
+        SG_RET(instance_device_j6(const_cast<sg_instance*>(insts[members[a]]), st, &j6, &j1));
+        jp[a] = j6;
+        jp[I + a] = j1;
     }
 
     bool unit_j = true;  // every coupling of the group has |J| = 1
@@ -287,8 +291,8 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
     SG_RET(d_E64.alloc(sizeof(unsigned long long) * (size_t)I * Rp, st));
     SG_RET(d_thr.alloc(sizeof(uint32_t) * thr.size(), st));
     SG_RET(d_keys.alloc(sizeof(RunKeys) * I, st));
-    SG_RET(d_j6.alloc(sizeof(uint2*) * I, st));
-    SG_RET(d_flag.alloc(sizeof(int), st));
+    SG_RET(d_j6.alloc(sizeof(void*) * 2 * I, st));
+    SG_RET(d_flag.alloc(2 * sizeof(int), st));  // [0] energy mismatches, [1] device status
     bool host_spins = false;
     for (int a = 0; a < I; ++a)
         host_spins |= outs[members[a]].spins && outs[members[a]].spins_mem == SG_MEM_HOST;
@@ -298,13 +302,14 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
                                 cudaMemcpyHostToDevice, st));
     SG_TRY_CUDA(cudaMemcpyAsync(d_keys.as<void>(), keys.data(), sizeof(RunKeys) * I,
                                 cudaMemcpyHostToDevice, st));
-    SG_TRY_CUDA(cudaMemcpyAsync(d_j6.as<void>(), j6.data(), sizeof(uint2*) * I,
+    SG_TRY_CUDA(cudaMemcpyAsync(d_j6.as<void>(), jp.data(), sizeof(void*) * 2 * I,
                                 cudaMemcpyHostToDevice, st));
     SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * (size_t)I * Rp, st));
-    SG_TRY_CUDA(cudaMemsetAsync(d_flag.as<void>(), 0, sizeof(int), st));
+    SG_TRY_CUDA(cudaMemsetAsync(d_flag.as<void>(), 0, 2 * sizeof(int), st));
 
     int8_t* spins = d_spins.as<int8_t>();
     const uint2* const* j6p = d_j6.as<const uint2*>();
+    const uint8_t* const* j1p = reinterpret_cast<const uint8_t* const*>(d_j6.as<const void*>() + I);
     const RunKeys* kp = d_keys.as<RunKeys>();
     LaunchLog log;
     const int64_t cells = (int64_t)I * N * Rp;
@@ -315,18 +320,19 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
     for (int s = 0; s < S; ++s)
         for (int c = 0; c < 2; ++c)
             SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * R, st, [&] {
-                return launch_half_sweep_sa(spins, j6p, kp, d_thr.as<uint32_t>() + (size_t)s * kThrRow,
-                                            d_E.as<int32_t>(), unit_j, I, L, Wn, R, (uint32_t)s, c,
+                return launch_half_sweep_sa(spins, j6p, j1p, kp, d_thr.as<uint32_t>() + (size_t)s * kThrRow,
+                                            d_E.as<int32_t>(), d_flag.as<int>() + 1, unit_j, I, L, Wn, R, (uint32_t)s, c,
                                             st);
             }));
     SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * (size_t)I * Rp, st));
     SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st); }));
 
     std::vector<long long> E64((size_t)I * Rp);
-    int mismatch = 0;
+    int flags[2] = {0, 0};
+    int& mismatch = flags[0];
     SG_TRY_CUDA(cudaMemcpyAsync(E64.data(), d_E64.as<void>(), sizeof(long long) * E64.size(),
                                 cudaMemcpyDeviceToHost, st));
-    SG_TRY_CUDA(cudaMemcpyAsync(&mismatch, d_flag.as<void>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(flags, d_flag.as<void>(), 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     for (int a = 0; a < I; ++a) {
         sg_sa_result& o = outs[members[a]];
         SG_RET(emit_spins(spins, a, N, Rp, R, o.spins, o.spins_mem, st, &d_stage, &log));
@@ -334,6 +340,10 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
     }
     SG_TRY_CUDA(cudaStreamSynchronize(st));
     log.finish();
+    if (flags[1] != 0) {
+        set_error("a bounded device-side wait gave up (status %d)", flags[1]);
+        return SG_ETIMEOUT;
+    }
     if (mismatch) {
         set_error("incremental energies disagree with the recomputed energies (%d slots)", mismatch);
         return SG_EINTERNAL;
@@ -373,11 +383,15 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     SG_RET(build_exchange_tables(ladder, dmax, &xt));
 
     std::vector<RunKeys> keys(I);
-    std::vector<const uint2*> j6(I);
+    std::vector<const void*> jp(2 * (size_t)I);  // [I] six-coupling records, then [I] sign bytes
     for (int a = 0; a < I; ++a) {
         const sg_pt_params& q = ps[members[a]];
         keys[a] = make_key(q.seed, q.instance_id);
-        SG_RET(instance_device_j6(const_cast<sg_instance*>(insts[members[a]]), st, &j6[a]));
+        const uint2* j6 = nullptr;
+        const uint8_t* j1 = nullptr;
+        SG_RET(instance_device_j6(const_cast<sg_instance*>(insts[members[a]]), st, &j6, &j1));
+        jp[a] = j6;
+        jp[I + a] = j1;
     }
     const int Kp = std::max(K - 1, 1);
     bool unit_j = true;
@@ -389,8 +403,8 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     SG_RET(d_E64.alloc(sizeof(unsigned long long) * (size_t)I * Rp, st));
     SG_RET(d_thr.alloc(sizeof(uint32_t) * thr.size(), st));
     SG_RET(d_keys.alloc(sizeof(RunKeys) * I, st));
-    SG_RET(d_j6.alloc(sizeof(uint2*) * I, st));
-    SG_RET(d_flag.alloc(sizeof(int), st));
+    SG_RET(d_j6.alloc(sizeof(void*) * 2 * I, st));
+    SG_RET(d_flag.alloc(2 * sizeof(int), st));  // [0] energy mismatches, [1] device status
     SG_RET(d_perm.alloc((size_t)I * Rp, st));
     SG_RET(d_inv.alloc((size_t)I * K, st));
     SG_RET(d_acc.alloc(sizeof(unsigned long long) * (size_t)I * Kp, st));
@@ -409,16 +423,17 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     };
     SG_TRY_CUDA(h2d(d_thr, thr.data(), sizeof(uint32_t) * thr.size()));
     SG_TRY_CUDA(h2d(d_keys, keys.data(), sizeof(RunKeys) * I));
-    SG_TRY_CUDA(h2d(d_j6, j6.data(), sizeof(uint2*) * I));
+    SG_TRY_CUDA(h2d(d_j6, jp.data(), sizeof(void*) * 2 * I));
     SG_TRY_CUDA(h2d(d_xtab, xt.tab.data(), sizeof(uint32_t) * xt.tab.size()));
     SG_TRY_CUDA(h2d(d_xoff, xt.off.data(), sizeof(uint32_t) * xt.off.size()));
     SG_TRY_CUDA(h2d(d_xlen, xt.len.data(), sizeof(uint32_t) * xt.len.size()));
     SG_TRY_CUDA(h2d(d_xtail, xt.tail.data(), sizeof(uint32_t) * xt.tail.size()));
     SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * (size_t)I * Rp, st));
-    SG_TRY_CUDA(cudaMemsetAsync(d_flag.as<void>(), 0, sizeof(int), st));
+    SG_TRY_CUDA(cudaMemsetAsync(d_flag.as<void>(), 0, 2 * sizeof(int), st));
 
     int8_t* spins = d_spins.as<int8_t>();
     const uint2* const* j6p = d_j6.as<const uint2*>();
+    const uint8_t* const* j1p = reinterpret_cast<const uint8_t* const*>(d_j6.as<const void*>() + I);
     const RunKeys* kp = d_keys.as<RunKeys>();
     int32_t* E = d_E.as<int32_t>();
     uint8_t* perm = d_perm.as<uint8_t>();
@@ -436,7 +451,8 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     for (int s = 0; s < S; ++s) {
         for (int c = 0; c < 2; ++c)
             SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * K, st, [&] {
-                return launch_half_sweep_pt(spins, j6p, kp, d_thr.as<uint32_t>(), perm, E, unit_j, I,
+                return launch_half_sweep_pt(spins, j6p, j1p, kp, d_thr.as<uint32_t>(), perm, E,
+                                            d_flag.as<int>() + 1, unit_j, I,
                                             L, Wn, K, (uint32_t)s, c, st);
             }));
         SG_RET(log.run(SG_KERNEL_EXCHANGE, (int64_t)I * (K / 2), st, [&] {
@@ -455,14 +471,15 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     std::vector<uint8_t> hperm((size_t)I * Rp);
     std::vector<unsigned long long> hacc((size_t)I * Kp);
     std::vector<int32_t> hmin(I);
-    int mismatch = 0;
+    int flags[2] = {0, 0};
+    int& mismatch = flags[0];
     SG_TRY_CUDA(cudaMemcpyAsync(E64.data(), d_E64.as<void>(), sizeof(long long) * E64.size(),
                                 cudaMemcpyDeviceToHost, st));
     SG_TRY_CUDA(cudaMemcpyAsync(hperm.data(), perm, hperm.size(), cudaMemcpyDeviceToHost, st));
     SG_TRY_CUDA(cudaMemcpyAsync(hacc.data(), acc, sizeof(unsigned long long) * hacc.size(),
                                 cudaMemcpyDeviceToHost, st));
     SG_TRY_CUDA(cudaMemcpyAsync(hmin.data(), minE, sizeof(int32_t) * I, cudaMemcpyDeviceToHost, st));
-    SG_TRY_CUDA(cudaMemcpyAsync(&mismatch, d_flag.as<void>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(flags, d_flag.as<void>(), 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     for (int a = 0; a < I; ++a) {
         sg_pt_result& o = outs[members[a]];
         SG_RET(emit_spins(spins, a, N, Rp, K, o.spins, o.spins_mem, st, &d_stage, &log));
@@ -470,6 +487,10 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     }
     SG_TRY_CUDA(cudaStreamSynchronize(st));
     log.finish();
+    if (flags[1] != 0) {
+        set_error("a bounded device-side wait gave up (status %d)", flags[1]);
+        return SG_ETIMEOUT;
+    }
     if (mismatch) {
         set_error("incremental energies disagree with the recomputed energies (%d slots)", mismatch);
         return SG_EINTERNAL;
@@ -600,7 +621,7 @@ extern "C" int32_t sg_energy(const sg_instance* inst_c, const int8_t* spins, int
     const int64_t N = inst->N;
     const int R = n_configs, Wn = (R + 3) / 4, Rp = 4 * Wn;
     const uint2* j6 = nullptr;
-    SG_RET(instance_device_j6(inst, st, &j6));
+    SG_RET(instance_device_j6(inst, st, &j6, nullptr));
     DevBuf d_in, d_packed, d_E64, d_j6, d_bad;
     const int8_t* src = spins;
     if (mem_kind == SG_MEM_HOST) {

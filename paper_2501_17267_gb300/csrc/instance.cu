@@ -190,28 +190,39 @@ int32_t generate_instance(int L, uint64_t seed, const double class_prob[3], int 
 
 // Upload J3 and build the per-site six-coupling records on the current device
 // (once per device; later calls reuse the copy).
-int32_t instance_device_j6(sg_instance* inst, cudaStream_t stream, const uint2** out)
+int32_t instance_device_j6(sg_instance* inst, cudaStream_t stream, const uint2** j6,
+                           const uint8_t** j1)
 {
     int dev = 0;
     SG_TRY_CUDA(cudaGetDevice(&dev));
     std::lock_guard<std::mutex> lock(inst->mu);
     for (auto& d : inst->dev)
         if (d.device == dev) {
-            *out = d.j6;
+            *j6 = d.j6;
+            if (j1) *j1 = d.j1;
             return SG_OK;
         }
     DeviceCopy dc;
     dc.device = dev;
     int8_t* J3d = nullptr;
-    SG_TRY_CUDA(cudaMalloc(&dc.j6, sizeof(uint2) * (size_t)inst->N));
-    cudaError_t e = cudaMalloc(&J3d, (size_t)(3 * inst->N));
+    const size_t N = (size_t)inst->N;
+    // one allocation: [N] uint2 records, then [N] sign bytes
+    cudaError_t e = cudaMalloc(&dc.j6, sizeof(uint2) * N + N);
     if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("cudaMalloc: %s", cudaGetErrorString(e));
+        return SG_ENOMEM;
+    }
+    dc.j1 = reinterpret_cast<uint8_t*>(dc.j6 + N);
+    e = cudaMalloc(&J3d, 3 * N);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
         cudaFree(dc.j6);
         set_error("cudaMalloc: %s", cudaGetErrorString(e));
         return SG_ENOMEM;
     }
-    e = cudaMemcpyAsync(J3d, inst->J3.data(), (size_t)(3 * inst->N), cudaMemcpyHostToDevice, stream);
-    int32_t rc = e == cudaSuccess ? launch_prepare_j6(J3d, dc.j6, inst->L, stream) : SG_ECUDA;
+    e = cudaMemcpyAsync(J3d, inst->J3.data(), 3 * N, cudaMemcpyHostToDevice, stream);
+    int32_t rc = e == cudaSuccess ? launch_prepare_j6(J3d, dc.j6, dc.j1, inst->L, stream) : SG_ECUDA;
     if (rc == SG_OK) {
         e = cudaStreamSynchronize(stream);
         if (e != cudaSuccess) rc = SG_ECUDA;
@@ -223,7 +234,8 @@ int32_t instance_device_j6(sg_instance* inst, cudaStream_t stream, const uint2**
         return rc;
     }
     inst->dev.push_back(dc);
-    *out = dc.j6;
+    *j6 = dc.j6;
+    if (j1) *j1 = dc.j1;
     return SG_OK;
 }
 

@@ -91,7 +91,8 @@ __device__ __forceinline__ SiteGeom colour_site(int64_t h, int L, int colour)
 
 // ---------------------------------------------------------------- couplings
 
-__global__ void prepare_j6_kernel(const int8_t* __restrict__ J3, uint2* __restrict__ j6, int L)
+__global__ void prepare_j6_kernel(const int8_t* __restrict__ J3, uint2* __restrict__ j6,
+                                  uint8_t* __restrict__ j1, int L)
 {
     const int64_t N = (int64_t)L * L * L;
     for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < N;
@@ -105,6 +106,9 @@ __global__ void prepare_j6_kernel(const int8_t* __restrict__ J3, uint2* __restri
         const uint32_t b2 = (uint8_t)J3[3 * i + 1], b3 = (uint8_t)J3[3 * by + 1];
         const uint32_t b4 = (uint8_t)J3[3 * i + 2], b5 = (uint8_t)J3[3 * bz + 2];
         j6[i] = make_uint2(b0 | (b1 << 8) | (b2 << 16) | (b3 << 24), b4 | (b5 << 8));
+        // bit q: coupling q is negative (used only when every coupling is +-1)
+        j1[i] = (uint8_t)((b0 >> 7) | ((b1 >> 7) << 1) | ((b2 >> 7) << 2) | ((b3 >> 7) << 3) |
+                          ((b4 >> 7) << 4) | ((b5 >> 7) << 5));
     }
 }
 
@@ -449,10 +453,11 @@ int sweep_grid_x(int64_t items, int Wn)
 
 }  // namespace
 
-int32_t launch_prepare_j6(const int8_t* J3_dev, uint2* j6_dev, int L, cudaStream_t st)
+int32_t launch_prepare_j6(const int8_t* J3_dev, uint2* j6_dev, uint8_t* j1_dev, int L,
+                          cudaStream_t st)
 {
     const int64_t N = (int64_t)L * L * L;
-    prepare_j6_kernel<<<grid_for(N, 1, 4096), kBlock, 0, st>>>(J3_dev, j6_dev, L);
+    prepare_j6_kernel<<<grid_for(N, 1, 4096), kBlock, 0, st>>>(J3_dev, j6_dev, j1_dev, L);
     return check_launch("prepare_j6");
 }
 
@@ -473,12 +478,16 @@ int32_t launch_energy(const int8_t* spins, const uint2* const* j6_ptrs, int I, i
     return check_launch("energy");
 }
 
-int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
-                             const uint32_t* thr_row, int32_t* E, bool unit_j, int I, int L, int Wn,
-                             int R, uint32_t sweep, int colour, cudaStream_t st)
+int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs,
+                             const uint8_t* const* j1_ptrs, const RunKeys* keys,
+                             const uint32_t* thr_row, int32_t* E, int* status, bool unit_j, int I,
+                             int L, int Wn, int R, uint32_t sweep, int colour, cudaStream_t st)
 {
+    if (tile_kernel_supports(I, L, Wn))
+        return launch_sweep_tile(spins, j6_ptrs, j1_ptrs, keys, thr_row, nullptr, E, status, false,
+                                 unit_j, I, L, Wn, R, sweep, colour, st);
     if (rows_kernel_supports(Wn))
-        return launch_sweep_rows_sa(spins, j6_ptrs, keys, thr_row, unit_j, I, L, Wn, R, sweep,
+        return launch_sweep_rows_sa(spins, j6_ptrs, j1_ptrs, keys, thr_row, unit_j, I, L, Wn, R, sweep,
                                     colour, st);
     const int64_t N = (int64_t)L * L * L;
     dim3 grid(sweep_grid_x((N / 2) * Wn, Wn), I);
@@ -487,13 +496,18 @@ int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs, const R
     return check_launch("half_sweep_sa");
 }
 
-int32_t launch_half_sweep_pt(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
+int32_t launch_half_sweep_pt(int8_t* spins, const uint2* const* j6_ptrs,
+                             const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
-                             bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
-                             cudaStream_t st)
+                             int* status, bool unit_j, int I, int L, int Wn, int K, uint32_t sweep,
+                             int colour, cudaStream_t st)
 {
+    if (tile_kernel_supports(I, L, Wn))
+        return launch_sweep_tile(spins, j6_ptrs, j1_ptrs, keys, thr_rungs, rung_of_slot, E, status,
+                                 true, unit_j, I, L, Wn, K, sweep, colour, st);
     if (rows_kernel_supports(Wn))
-        return launch_sweep_rows_pt(spins, j6_ptrs, keys, thr_rungs, rung_of_slot, E, unit_j, I, L,
+        return launch_sweep_rows_pt(spins, j6_ptrs, j1_ptrs, keys, thr_rungs, rung_of_slot, E, unit_j,
+                                    I, L,
                                     Wn, K, sweep, colour, st);
     const int64_t N = (int64_t)L * L * L;
     dim3 grid(sweep_grid_x((N / 2) * Wn, Wn), I);

@@ -35,7 +35,8 @@ struct Status {
 // ---- instances ----
 struct DeviceCopy {
     int device = -1;
-    uint2* j6 = nullptr;  // [N] per-site record of the six couplings (see kernels.cu)
+    uint2* j6 = nullptr;    // [N] per-site record of the six couplings (see kernels.cu)
+    uint8_t* j1 = nullptr;  // [N] per-site sign bits of the six couplings (unit couplings)
 };
 
 }  // namespace sg
@@ -76,38 +77,51 @@ struct ExchangeTables {
 int32_t build_exchange_tables(const std::vector<double>& ladder, int64_t dmax,
                               ExchangeTables* out);
 
-// Per-instance device copy of the six-coupling records, uploaded on first use.
-int32_t instance_device_j6(sg_instance* inst, cudaStream_t stream, const uint2** out);
+// Per-instance device copy of the coupling records, uploaded on first use.
+int32_t instance_device_j6(sg_instance* inst, cudaStream_t stream, const uint2** j6,
+                           const uint8_t** j1);
 
 // ---- kernels (kernels.cu) ----
 struct RunKeys {
     uint32_t k0, k1;
 };
 
-int32_t launch_prepare_j6(const int8_t* J3_dev, uint2* j6_dev, int L, cudaStream_t st);
+int32_t launch_prepare_j6(const int8_t* J3_dev, uint2* j6_dev, uint8_t* j1_dev, int L,
+                          cudaStream_t st);
 int32_t launch_init_spins(int8_t* spins, const RunKeys* keys_dev, int I, int64_t N, int Wn,
                           int R, cudaStream_t st);
 int32_t launch_energy(const int8_t* spins, const uint2* const* j6_ptrs, int I, int L, int Wn,
                       unsigned long long* E_out /* [I][Wn*4] */, cudaStream_t st);
-int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
-                             const uint32_t* thr_row /* kThrRow */, int32_t* E, bool unit_j, int I,
-                             int L, int Wn, int R, uint32_t sweep, int colour, cudaStream_t st);
-int32_t launch_half_sweep_pt(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
+int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs,
+                             const uint8_t* const* j1_ptrs, const RunKeys* keys,
+                             const uint32_t* thr_row /* kThrRow */, int32_t* E, int* status,
+                             bool unit_j, int I, int L, int Wn, int R, uint32_t sweep, int colour,
+                             cudaStream_t st);
+int32_t launch_half_sweep_pt(int8_t* spins, const uint2* const* j6_ptrs,
+                             const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs /* [K][kThrRow] */,
-                             const uint8_t* rung_of_slot /* [I][Wn*4] */, int32_t* E, bool unit_j,
-                             int I, int L, int Wn, int K, uint32_t sweep, int colour,
+                             const uint8_t* rung_of_slot /* [I][Wn*4] */, int32_t* E, int* status,
+                             bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
                              cudaStream_t st);
 // sweep.cu: row-mapped sweep kernel (used whenever it supports the word count)
 bool rows_kernel_supports(int Wn);
 // SA variant keeps no incremental energies (the run recomputes them at the end);
 // unit_j: every coupling of the group has |J| = 1.
-int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
+int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
+                             const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_row, bool unit_j, int I, int L, int Wn, int R,
                              uint32_t sweep, int colour, cudaStream_t st);
-int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys,
+int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
+                             const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
                              cudaStream_t st);
+// tile.cu: shared-memory streaming sweep (used when it supports the shape)
+bool tile_kernel_supports(int I, int L, int Wn);
+int32_t launch_sweep_tile(int8_t* spins, const uint2* const* j6_ptrs, const uint8_t* const* j1_ptrs,
+                          const RunKeys* keys, const uint32_t* thr, const uint8_t* rung_of_slot,
+                          int32_t* E, int* status, bool pt, bool unit_j, int I, int L, int Wn,
+                          int Rvalid, uint32_t sweep, int colour, cudaStream_t st);
 int32_t launch_pt_exchange(const RunKeys* keys, const int32_t* E, uint8_t* rung_of_slot,
                            uint8_t* slot_of_rung, unsigned long long* accepts,
                            int32_t* minE, const uint32_t* xtab, const uint32_t* xoff,

@@ -180,3 +180,43 @@ def test_energy_device_input_and_validation(sg):
     with pytest.raises(sg.SGError) as e:
         sg.energy(inst, bad)
     assert e.value.code == sg.SG_EINVAL
+
+
+@pytest.mark.parametrize("zc", ["1", "16", "32"])
+def test_pt_tile_kernel_zranges(sg, monkeypatch, zc):
+    """Shared-memory streaming kernel with slab ranges of 1, 16 and 32 (longer than the
+    8-bit energy lanes hold, so the periodic fold is exercised)."""
+    monkeypatch.setenv("SG_SWEEP_KERNEL", "2")
+    monkeypatch.setenv("SG_TILE_ZC", zc)
+    inst = sg.Instance.create(32, 77)
+    J3, _, egs = inst.get()
+    _pt_compare(sg, inst, J3, egs, 8, 6, 0.2, 3.0, seed=4, iid=2)
+
+
+def test_sweep_kernels_agree(sg, monkeypatch):
+    """The row kernel and the shared-memory kernel give the same bytes."""
+    insts = [sg.Instance.create(32, 900 + k) for k in range(3)]
+    params = [dict(temps=32, sweeps=12, beta_min=0.2, beta_max=3.0, seed=8, instance_id=k)
+              for k in range(3)]
+    monkeypatch.setenv("SG_SWEEP_KERNEL", "1")
+    rows = sg.pt_run_batch(insts, params, spins="host")
+    monkeypatch.setenv("SG_SWEEP_KERNEL", "2")
+    tile = sg.pt_run_batch(insts, params, spins="host")
+    for a, b in zip(rows, tile):
+        assert np.array_equal(a["spins"], b["spins"]) and np.array_equal(a["E"], b["E"])
+        assert a["minE"] == b["minE"] and np.array_equal(a["perm"], b["perm"])
+    sa_rows = None
+    monkeypatch.setenv("SG_SWEEP_KERNEL", "1")
+    sa_rows = sg.sa_run(insts[0], 36, 15, 0.1, 3.0, seed=2, spins="host")
+    monkeypatch.setenv("SG_SWEEP_KERNEL", "2")
+    sa_tile = sg.sa_run(insts[0], 36, 15, 0.1, 3.0, seed=2, spins="host")
+    assert np.array_equal(sa_rows["spins"], sa_tile["spins"])
+
+
+@pytest.mark.parametrize("kernel", ["1", "2"])
+@pytest.mark.parametrize("L,R", [(16, 32), (32, 64), (48, 8)])
+def test_sa_kernel_shapes(sg, monkeypatch, kernel, L, R):
+    monkeypatch.setenv("SG_SWEEP_KERNEL", kernel)
+    inst = sg.Instance.create(L, 40 + L)
+    J3, _, egs = inst.get()
+    _sa_compare(sg, inst, J3, egs, R, 12, 0.1, 3.0, seed=6, reps=[0, 5, R - 1])
