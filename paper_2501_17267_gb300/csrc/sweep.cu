@@ -3,7 +3,8 @@
 // One launch updates every site of one checkerboard colour, for every replica of a
 // group of instances.  Thread mapping (no division except one multiply-high per row):
 //   blockIdx.y        instance
-//   blockIdx.x, ty    rows (y, z) of the lattice; each thread walks `rows_per_thread` rows
+//   blockIdx.x, ty    rows (y, z) of the lattice, dealt out grid-stride: thread (bx, ty)
+//                     takes rows (c * gridDim.x + bx) * blockDim.y + ty, c < rows_per_thread
 //   tx = j * G + g    site j of the colour inside the row, word group g
 // A word holds four replicas (one byte each).  Thread g of a site owns CH chunks of
 // WG consecutive words, so it updates 4*WG*CH replicas with one decode of the site's
@@ -125,9 +126,10 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
     };
     int items = 0;  // site updates folded into the 8-bit lanes since the last flush
 
-    const int row_base = blockIdx.x * blockDim.y * a.rows_per_thread + threadIdx.y;
+    // rows are dealt out grid-stride, so the blocks of an instance advance together
+    // through the lattice and the +-z neighbour rows they read are still in L2
     for (int c = 0; c < a.rows_per_thread; ++c) {
-        const int row = row_base + c * blockDim.y;
+        const int row = (c * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y;
         if (row >= LL) break;
         const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
         const int y = row - z * L;
