@@ -38,12 +38,37 @@ BYTES_PER_ATTEMPT = 2.0 + 3.0 / WORK.temps  # spin byte read + written once per 
 
 
 def _peaks():
+    """(HBM GB/s, its source, max SM MHz)."""
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
             p = json.load(f)
-        return float(p["hbm_gbs"]), "measured"
+        return float(p["hbm_gbs"]), "measured", float(p.get("sm_max_mhz", 2070.0))
     except Exception:
-        return 6800.0, "fallback"
+        return 6800.0, "fallback", 2070.0
+
+
+# Integer roof of one attempt: every attempt consumes one 32-bit Philox4x32-10 word, and
+# a Philox call (4 words) makes 20 32x32->64-bit multiplies, i.e. 5 per attempt.  The SM
+# executes 32 such multiplies per clock (64 IMAD lanes, two IMADs -- high and low half --
+# per product), so the multiply pipe alone caps a GB300 at SMs * 32 / 5 attempts per clock.
+MULS_PER_ATTEMPT = 5
+WIDE_MULS_PER_SM_CLOCK = 32
+
+
+def _traffic_record():
+    """DRAM bytes per sweep launch from the committed ncu capture, if the sweep kernel's
+    sources are unchanged since it was taken (else None)."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "sweep_rows_pt_L64_I16_K32.traffic.json")) as f:
+            rec = json.load(f)
+        h = hashlib.sha256()
+        for src in rec["sources"]:
+            with open(os.path.join(ROOT, src), "rb") as f:
+                h.update(f.read())
+        return rec if h.hexdigest() == rec["sources_sha256"] else None
+    except Exception:
+        return None
 
 
 # ---------------------------------------------------------------- CPU oracle leg
@@ -258,18 +283,32 @@ def main():
     value = attempts_per_step * world * args.steps / (ms_max / 1000.0)
     launches = sum(v["launches"] for v in st.values())
 
-    # roofline of the sweep kernel: algorithmic bytes per launch / mean launch duration
+    # roofline of the sweep kernel, from its launches' CUDA-event durations in the timed
+    # region: attempts per launch / mean launch duration against the integer roof, with
+    # the HBM view (algorithmic bytes per launch / duration) beside it
     sw = st["sweep"]
-    peak, peak_kind = _peaks()
+    peak, peak_kind, sm_mhz = _peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = sms * WIDE_MULS_PER_SM_CLOCK / MULS_PER_ATTEMPT * sm_mhz * 1e6
     roof = None
     if sw["launches"] and sw["device_ms"] > 0:
         per_launch_s = sw["device_ms"] / 1000.0 / sw["launches"]
-        bytes_per_launch = sw["units"] / sw["launches"] * BYTES_PER_ATTEMPT
-        achieved = bytes_per_launch / per_launch_s / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None, "peak_source": peak_kind,
-                "kernel": "half_sweep_kernel<PT>", "launch_ms": 1000 * per_launch_s,
-                "attempts_per_launch": sw["units"] / sw["launches"],
+        attempts_per_launch = sw["units"] / sw["launches"]
+        bytes_per_launch = attempts_per_launch * BYTES_PER_ATTEMPT
+        gbs = bytes_per_launch / per_launch_s / 1e9
+        rate = attempts_per_launch / per_launch_s
+        rec = _traffic_record()
+        roof = {"bound": "alu", "achieved": rate, "peak": alu_peak, "unit": "attempts/s",
+                "frac": rate / alu_peak,
+                "traffic": rec["traffic_bytes_per_launch"] if rec else None,
+                "traffic_unit": "DRAM bytes per launch (ncu)",
+                "algorithmic_bytes_per_launch": bytes_per_launch,
+                "peak_source": f"derived: {sms} SMs x {WIDE_MULS_PER_SM_CLOCK} 32x32->64 multiplies "
+                               f"per clock / {MULS_PER_ATTEMPT} per attempt at {sm_mhz:.0f} MHz",
+                "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+                        "peak_source": peak_kind},
+                "kernel": "sweep_rows_kernel<PT>", "launch_ms": 1000 * per_launch_s,
+                "attempts_per_launch": attempts_per_launch,
                 "share_of_step": sw["device_ms"] / ms}
 
     # end to end: host couplings in, results out, inside the timed region
