@@ -184,6 +184,35 @@ int32_t sg_energy(const sg_instance* inst, const int8_t* spins, int32_t n_config
                   int32_t mem_kind, int64_t* E_out, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Energy without device allocation (no counterpart in the paper).           */
+/* ------------------------------------------------------------------------ */
+
+/* Size of the fixed device scratch array behind sg_energy_noalloc (16 MiB).  Every
+ * GPU that loads the library holds this array until the process exits. */
+#define SG_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+
+/* Same energies as sg_energy (Eq. 1), for callers that must not let a library
+ * allocate device memory -- for example a server that owns the device-memory budget
+ * through its own pool, or a latency-critical loop where cudaMalloc/cudaFree (which
+ * can synchronise the device and can fail under fragmentation) is not allowed.
+ *   L          lattice side (even, 2 <= L <= SG_LMAX)
+ *   J3_dev     device int8 [L^3][3] couplings (|J| <= SG_JMAX), read only
+ *   spins_dev  device int8 [n_configs][L^3] configurations in {-1, +1}, read only
+ *   E_dev      device int64 [n_configs], written
+ * No cudaMalloc, cudaFree or allocating library routine is called.  All scratch lives
+ * in one fixed array of SG_NOALLOC_SCRATCH_BYTES per device; a request that needs more
+ * (about 8*L^3 + L^3 * 4*ceil(n_configs/4) bytes) fails with SG_EINVAL and a message.
+ * The first call on a device looks up the array's device address (with that device
+ * current); make that first call before any stream capture.  Every call shares the
+ * array and it keeps the last call's contents (the call clears what must start at
+ * zero): calls that overlap on the GPU -- on different streams or from different host
+ * threads -- race on it, so serialise them.  The call enqueues on `stream` and
+ * returns after it has completed.  Errors: SG_EINVAL (bad arguments, too large, a
+ * spin not in {-1,+1}), SG_ECUDA. */
+int32_t sg_energy_noalloc(int32_t L, const int8_t* J3_dev, const int8_t* spins_dev,
+                          int32_t n_configs, int64_t* E_dev, void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Launch statistics (diagnostics; no counterpart in the paper).             */
 /* ------------------------------------------------------------------------ */
 

@@ -543,6 +543,21 @@ int32_t launch_check_energy(const unsigned long long* E64, const int32_t* E, int
     return check_launch("check_energy");
 }
 
+namespace {
+__global__ void copy_energies_kernel(const unsigned long long* __restrict__ E64,
+                                     int64_t* __restrict__ E, int n)
+{
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < n; q += gridDim.x * blockDim.x)
+        E[q] = (int64_t)(long long)E64[q];
+}
+}  // namespace
+
+int32_t launch_copy_energies(const unsigned long long* E64, int64_t* E, int n, cudaStream_t st)
+{
+    copy_energies_kernel<<<grid_for(n, 1, 1024), kBlock, 0, st>>>(E64, E, n);
+    return check_launch("copy_energies");
+}
+
 int32_t launch_narrow_energy(const unsigned long long* E64, int32_t* E, int64_t n, cudaStream_t st)
 {
     narrow_energy_kernel<<<grid_for(n, 1, 1024), kBlock, 0, st>>>(E64, E, n);

@@ -132,6 +132,7 @@ int32_t launch_pt_setup(const unsigned long long* E64, int32_t* E, uint8_t* rung
                         int I, int Rp, int K, cudaStream_t st);
 int32_t launch_check_energy(const unsigned long long* E64, const int32_t* E, int I, int Rp,
                             int R, int* mismatch, cudaStream_t st);
+int32_t launch_copy_energies(const unsigned long long* E64, int64_t* E, int n, cudaStream_t st);
 int32_t launch_narrow_energy(const unsigned long long* E64, int32_t* E, int64_t n, cudaStream_t st);
 int32_t launch_unpack_spins(const int8_t* spins, int8_t* out, int64_t N, int Rp, int R,
                             int I_index, int I, cudaStream_t st);

@@ -21,6 +21,7 @@ SG_PENDING = 1
 SG_MEM_HOST, SG_MEM_DEVICE = 0, 1
 SG_SCHEDULE_LINEAR, SG_SCHEDULE_GEOMETRIC = 0, 1
 SG_JMAX = 2
+SG_NOALLOC_SCRATCH_BYTES = 16 * 1024 * 1024
 
 if not os.path.exists(LIB_PATH):
     raise ImportError(
@@ -77,6 +78,7 @@ _SIGS = {
     "sg_pt_run": [_P, ctypes.POINTER(PTParams), ctypes.POINTER(PTResult), _P],
     "sg_pt_run_batch": [_P, _P, ctypes.c_int32, _P, _P],
     "sg_energy": [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P],
+    "sg_energy_noalloc": [ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P],
     "sg_version": [],
     "sg_stats_enable": [ctypes.c_int32],
     "sg_stats_read": [ctypes.POINTER(KernelStats), ctypes.c_int32],
@@ -304,3 +306,14 @@ def stats_read(reset: bool = False) -> dict:
     _check(_lib.sg_stats_read(ctypes.byref(st), int(bool(reset))))
     return {k: {"launches": int(st.launches[i]), "device_ms": float(st.device_ms[i]),
                 "units": int(st.units[i])} for i, k in enumerate(KERNEL_KINDS)}
+
+
+def energy_noalloc(L: int, J3_dev, spins_dev, E_dev, stream=None):
+    """Energies of spins_dev (n, L^3) into E_dev (n,) int64, all torch CUDA tensors,
+    through the entry point that allocates no device memory (fixed scratch)."""
+    assert _is_torch_cuda(J3_dev) and _is_torch_cuda(spins_dev) and _is_torch_cuda(E_dev)
+    assert J3_dev.is_contiguous() and spins_dev.is_contiguous() and E_dev.is_contiguous()
+    n = spins_dev.numel() // (L ** 3)
+    assert E_dev.numel() == n
+    _check(_lib.sg_energy_noalloc(L, _P(J3_dev.data_ptr()), _P(spins_dev.data_ptr()), n,
+                                  _P(E_dev.data_ptr()), _stream_handle(stream)))
