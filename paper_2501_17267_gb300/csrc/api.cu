@@ -8,6 +8,7 @@
 #include <map>
 #include <tuple>
 
+#include "exchange.cuh"
 #include "sg_internal.h"
 
 namespace sg {
@@ -238,13 +239,14 @@ int32_t check_pt(const sg_instance* inst, const sg_pt_params* p, const sg_pt_res
 }
 
 // Shared tail of a run: copy the spins of instance `idx` out of the packed layout.
-int32_t emit_spins(const int8_t* packed, int idx, int64_t N, int Rp, int R, int8_t* dst, int mem,
+int32_t emit_spins(const int8_t* packed, int idx, int L, int Rp, int R, int8_t* dst, int mem,
                    cudaStream_t st, DevBuf* staging, LaunchLog* log)
 {
     if (!dst) return SG_OK;
+    const int64_t N = (int64_t)L * L * L;
     int8_t* target = mem == SG_MEM_DEVICE ? dst : staging->as<int8_t>();
     SG_RET(log->run(SG_KERNEL_OTHER, (int64_t)R * N, st, [&] {
-        return launch_unpack_spins(packed, target, N, Rp, R, idx, 0, st);
+        return launch_unpack_spins(packed, target, L, Rp, R, idx, st);
     }));
     if (mem == SG_MEM_DEVICE) return SG_OK;
     SG_TRY_CUDA(cudaMemcpyAsync(dst, staging->as<int8_t>(), (size_t)R * N, cudaMemcpyDeviceToHost, st));
@@ -316,7 +318,7 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
     unsigned long long* E64d = d_E64.as<unsigned long long>();
     // SA keeps no per-sweep energies: the energy of every replica is computed once,
     // from the final spins.
-    SG_RET(log.run(SG_KERNEL_INIT, cells, st, [&] { return launch_init_spins(spins, kp, I, N, Wn, R, st); }));
+    SG_RET(log.run(SG_KERNEL_INIT, cells, st, [&] { return launch_init_spins(spins, kp, I, L, Wn, R, st); }));
     for (int s = 0; s < S; ++s)
         for (int c = 0; c < 2; ++c)
             SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * R, st, [&] {
@@ -335,7 +337,7 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
     SG_TRY_CUDA(cudaMemcpyAsync(flags, d_flag.as<void>(), 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     for (int a = 0; a < I; ++a) {
         sg_sa_result& o = outs[members[a]];
-        SG_RET(emit_spins(spins, a, N, Rp, R, o.spins, o.spins_mem, st, &d_stage, &log));
+        SG_RET(emit_spins(spins, a, L, Rp, R, o.spins, o.spins_mem, st, &d_stage, &log));
         if (o.spins && o.spins_mem == SG_MEM_HOST) SG_TRY_CUDA(cudaStreamSynchronize(st));
     }
     SG_TRY_CUDA(cudaStreamSynchronize(st));
@@ -397,7 +399,7 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     bool unit_j = true;
     for (int a = 0; a < I; ++a) unit_j &= insts[members[a]]->unit_couplings;
     DevBuf d_spins, d_E, d_E64, d_thr, d_keys, d_j6, d_flag, d_stage, d_perm, d_inv, d_acc, d_min,
-        d_xtab, d_xoff, d_xlen, d_xtail;
+        d_xtab, d_xoff, d_xlen, d_xtail, d_done;
     SG_RET(d_spins.alloc((size_t)I * N * Rp, st));
     SG_RET(d_E.alloc(sizeof(int32_t) * (size_t)I * Rp, st));
     SG_RET(d_E64.alloc(sizeof(unsigned long long) * (size_t)I * Rp, st));
@@ -409,6 +411,7 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     SG_RET(d_inv.alloc((size_t)I * K, st));
     SG_RET(d_acc.alloc(sizeof(unsigned long long) * (size_t)I * Kp, st));
     SG_RET(d_min.alloc(sizeof(int32_t) * I, st));
+    SG_RET(d_done.alloc(sizeof(unsigned) * I, st));
     SG_RET(d_xtab.alloc(sizeof(uint32_t) * xt.tab.size(), st));
     SG_RET(d_xoff.alloc(sizeof(uint32_t) * xt.off.size(), st));
     SG_RET(d_xlen.alloc(sizeof(uint32_t) * xt.len.size(), st));
@@ -430,6 +433,7 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     SG_TRY_CUDA(h2d(d_xtail, xt.tail.data(), sizeof(uint32_t) * xt.tail.size()));
     SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * (size_t)I * Rp, st));
     SG_TRY_CUDA(cudaMemsetAsync(d_flag.as<void>(), 0, 2 * sizeof(int), st));
+    SG_TRY_CUDA(cudaMemsetAsync(d_done.as<void>(), 0, sizeof(unsigned) * I, st));
 
     int8_t* spins = d_spins.as<int8_t>();
     const uint2* const* j6p = d_j6.as<const uint2*>();
@@ -443,23 +447,38 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     LaunchLog log;
     const int64_t cells = (int64_t)I * N * Rp;
     unsigned long long* E64d = d_E64.as<unsigned long long>();
-    SG_RET(log.run(SG_KERNEL_INIT, cells, st, [&] { return launch_init_spins(spins, kp, I, N, Wn, K, st); }));
+    SG_RET(log.run(SG_KERNEL_INIT, cells, st, [&] { return launch_init_spins(spins, kp, I, L, Wn, K, st); }));
     SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st); }));
     SG_RET(log.run(SG_KERNEL_OTHER, (int64_t)I * Rp, st, [&] {
         return launch_pt_setup(E64d, E, perm, inv, acc, minE, I, Rp, K, st);
     }));
+    ExchangeArgs xa;
+    xa.keys = kp;
+    xa.E = E;
+    xa.rung_of_slot = perm;
+    xa.slot_of_rung = inv;
+    xa.accepts = acc;
+    xa.minE = minE;
+    xa.xtab = d_xtab.as<uint32_t>();
+    xa.xoff = d_xoff.as<uint32_t>();
+    xa.xlen = d_xlen.as<uint32_t>();
+    xa.xtail = d_xtail.as<uint32_t>();
+    xa.Rp = Rp;
+    xa.K = K;
+    unsigned* done = d_done.as<unsigned>();
     for (int s = 0; s < S; ++s) {
+        bool fused = false;
         for (int c = 0; c < 2; ++c)
             SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * K, st, [&] {
+                // the colour-1 launch may perform the exchange in its last blocks
                 return launch_half_sweep_pt(spins, j6p, j1p, kp, d_thr.as<uint32_t>(), perm, E,
-                                            d_flag.as<int>() + 1, unit_j, I,
-                                            L, Wn, K, (uint32_t)s, c, st);
+                                            d_flag.as<int>() + 1, unit_j, I, L, Wn, K,
+                                            (uint32_t)s, c, c == 1 ? &xa : nullptr, done,
+                                            c == 1 ? &fused : nullptr, st);
             }));
-        SG_RET(log.run(SG_KERNEL_EXCHANGE, (int64_t)I * (K / 2), st, [&] {
-            return launch_pt_exchange(kp, E, perm, inv, acc, minE, d_xtab.as<uint32_t>(),
-                                      d_xoff.as<uint32_t>(), d_xlen.as<uint32_t>(),
-                                      d_xtail.as<uint32_t>(), I, Rp, K, (uint32_t)s, st);
-        }));
+        if (!fused)
+            SG_RET(log.run(SG_KERNEL_EXCHANGE, (int64_t)I * (K / 2), st,
+                           [&] { return launch_pt_exchange(xa, I, (uint32_t)s, st); }));
     }
     SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * (size_t)I * Rp, st));
     SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st); }));
@@ -482,7 +501,7 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     SG_TRY_CUDA(cudaMemcpyAsync(flags, d_flag.as<void>(), 2 * sizeof(int), cudaMemcpyDeviceToHost, st));
     for (int a = 0; a < I; ++a) {
         sg_pt_result& o = outs[members[a]];
-        SG_RET(emit_spins(spins, a, N, Rp, K, o.spins, o.spins_mem, st, &d_stage, &log));
+        SG_RET(emit_spins(spins, a, L, Rp, K, o.spins, o.spins_mem, st, &d_stage, &log));
         if (o.spins && o.spins_mem == SG_MEM_HOST) SG_TRY_CUDA(cudaStreamSynchronize(st));
     }
     SG_TRY_CUDA(cudaStreamSynchronize(st));
@@ -638,7 +657,7 @@ extern "C" int32_t sg_energy(const sg_instance* inst_c, const int8_t* spins, int
     SG_TRY_CUDA(cudaMemsetAsync(d_bad.as<void>(), 0, sizeof(int), st));
     LaunchLog log;
     SG_RET(log.run(SG_KERNEL_OTHER, (int64_t)Rp * N, st, [&] {
-        return launch_pack_spins(src, d_packed.as<int8_t>(), N, Rp, R, d_bad.as<int>(), st);
+        return launch_pack_spins(src, d_packed.as<int8_t>(), inst->L, Rp, R, d_bad.as<int>(), st);
     }));
     SG_RET(log.run(SG_KERNEL_ENERGY, (int64_t)Rp * N, st, [&] {
         return launch_energy(d_packed.as<int8_t>(), d_j6.as<const uint2*>(), 1, inst->L, Wn,

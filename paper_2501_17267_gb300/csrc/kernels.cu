@@ -1,7 +1,7 @@
 // kernels.cu -- device kernels of the Metropolis path (sm_103a).
 //
-// Device layout.  Spins of a run live as int8 [I][N][Rp]: instance, site
-// i = x + L*(y + L*z), replica (fastest), Rp = R rounded up to a multiple of 4 so
+// Device layout.  Spins of a run live as int8 [I][N][Rp]: instance, site in storage
+// order (see storage_of: colour-split rows), replica (fastest), Rp = R rounded up to 4 so
 // that one 32-bit word holds four replicas of one site (padding replicas stay +1 and
 // never flip).  A thread owns one such word and updates its four replicas with
 // SIMD-within-a-register arithmetic; one Philox4x32-10 call supplies the four
@@ -20,6 +20,7 @@
 // 2 sum|J| - P.  With W the selected count, x = sum|J| - W per byte.
 #include <stdio.h>
 
+#include "exchange.cuh"
 #include "philox.cuh"
 #include "sg_internal.h"
 
@@ -115,16 +116,17 @@ __global__ void prepare_j6_kernel(const int8_t* __restrict__ J3, uint2* __restri
 // ---------------------------------------------------------------- initial state
 
 __global__ void init_spins_kernel(uint32_t* __restrict__ spins, const RunKeys* __restrict__ keys,
-                                  int64_t N, int Wn, int R)
+                                  int L, int Wn, int R)
 {
     const int inst = blockIdx.y;
     const RunKeys key = keys[inst];
+    const int64_t N = (int64_t)L * L * L;
     const int64_t items = N * Wn;
     uint32_t* s = spins + (int64_t)inst * items;
     for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < items;
          t += (int64_t)gridDim.x * blockDim.x) {
         const int w = (int)(t % Wn);
-        const int64_t i = t / Wn;
+        const int64_t i = logical_of(L, t / Wn);
         const Philox4 r = philox4x32_10((uint32_t)i, kSweepInit, (uint32_t)w, kDomainMetropolis,
                                         key.k0, key.k1);
         uint32_t word = 0;
@@ -187,10 +189,11 @@ half_sweep_kernel(uint32_t* __restrict__ spins, const uint2* const* __restrict__
         const int64_t h = t / Wn;
         const SiteGeom g = colour_site(h, L, colour);
         const SiteCouplings c = decode_site(j6[g.i]);
-        const uint32_t self = s[g.i * Wn + w];
+        const int64_t is = storage_of(L, g.i);
+        const uint32_t self = s[is * Wn + w];
         uint32_t P = 0;
 #pragma unroll
-        for (int q = 0; q < 6; ++q) P += (s[g.nb[q] * Wn + w] ^ c.S[q]) & c.M[q];
+        for (int q = 0; q < 6; ++q) P += (s[storage_of(L, g.nb[q]) * Wn + w] ^ c.S[q]) & c.M[q];
         const uint32_t W = (P & ~self) | ((c.C2 - P) & self);
 
         uint32_t flip = 0;
@@ -220,7 +223,7 @@ half_sweep_kernel(uint32_t* __restrict__ spins, const uint2* const* __restrict__
                 }
             }
         }
-        if (flip) s[g.i * Wn + w] = self ^ flip;
+        if (flip) s[is * Wn + w] = self ^ flip;
     }
 
     int32_t* Ei = E + (int64_t)inst * Rp;
@@ -259,16 +262,17 @@ energy_kernel(const uint32_t* __restrict__ spins, const uint2* const* __restrict
     long long acc[4] = {0, 0, 0, 0};
     const int64_t items = N * Wn;
     for (int64_t t = t0; t < items; t += stride) {
-        const int64_t i = t / Wn;
+        const int64_t is = t / Wn;                // storage position
+        const int64_t i = logical_of(L, is);      // logical site
         const int x = (int)(i % L), y = (int)((i / L) % L), z = (int)(i / ((int64_t)L * L));
         const int64_t LL = (int64_t)L * L;
-        const int64_t fx = (x + 1 == L ? 0 : x + 1) + (int64_t)L * y + LL * z;
-        const int64_t fy = x + (int64_t)L * (y + 1 == L ? 0 : y + 1) + LL * z;
-        const int64_t fz = x + (int64_t)L * y + LL * (z + 1 == L ? 0 : z + 1);
+        const int64_t fx = storage_of(L, (x + 1 == L ? 0 : x + 1) + (int64_t)L * y + LL * z);
+        const int64_t fy = storage_of(L, x + (int64_t)L * (y + 1 == L ? 0 : y + 1) + LL * z);
+        const int64_t fz = storage_of(L, x + (int64_t)L * y + LL * (z + 1 == L ? 0 : z + 1));
         const uint2 r = j6[i];
         const int J[3] = {(int)(int8_t)(r.x & 0xFF), (int)(int8_t)((r.x >> 16) & 0xFF),
                           (int)(int8_t)(r.y & 0xFF)};
-        const uint32_t me = s[i * Wn + w];
+        const uint32_t me = s[is * Wn + w];
         const uint32_t nb[3] = {s[fx * Wn + w], s[fy * Wn + w], s[fz * Wn + w]};
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
@@ -317,48 +321,11 @@ __global__ void pt_setup_kernel(const unsigned long long* __restrict__ E64, int3
     if (threadIdx.x == 0) minE[inst] = s_min;
 }
 
-// Exchange attempts after sweep `sweep` between rungs (k, k+1), k = sweep mod 2,
-// sweep mod 2 + 2, ...: these pairs are disjoint, so each runs in its own thread.
-__global__ void pt_exchange_kernel(const RunKeys* __restrict__ keys, const int32_t* __restrict__ E,
-                                   uint8_t* __restrict__ rung_of_slot,
-                                   uint8_t* __restrict__ slot_of_rung,
-                                   unsigned long long* __restrict__ accepts,
-                                   int32_t* __restrict__ minE, const uint32_t* __restrict__ xtab,
-                                   const uint32_t* __restrict__ xoff,
-                                   const uint32_t* __restrict__ xlen,
-                                   const uint32_t* __restrict__ xtail, int Rp, int K, uint32_t sweep)
+// Exchange attempts after sweep `sweep` (see exchange.cuh), one block per instance.
+__global__ void pt_exchange_kernel(const ExchangeArgs x, uint32_t sweep)
 {
-    const int inst = blockIdx.x;
-    const RunKeys key = keys[inst];
-    const int32_t* Ei = E + (int64_t)inst * Rp;
-    uint8_t* perm = rung_of_slot + (int64_t)inst * Rp;
-    uint8_t* inv = slot_of_rung + (int64_t)inst * K;
     __shared__ int32_t s_min;
-    if (threadIdx.x == 0) s_min = 0x7FFFFFFF;
-    __syncthreads();
-    for (int j = threadIdx.x;; j += blockDim.x) {
-        const int k = 2 * j + (int)(sweep & 1u);
-        if (k + 1 >= K) break;
-        const int a = inv[k], b = inv[k + 1];
-        const int64_t d = (int64_t)Ei[a] - (int64_t)Ei[b];
-        bool accept = d <= 0;
-        if (!accept) {
-            const uint32_t u = philox4x32_10((uint32_t)k, sweep, 0u, kDomainExchange, key.k0,
-                                             key.k1).v[0];
-            const uint32_t T = d <= (int64_t)xlen[k] ? xtab[xoff[k] + (uint32_t)(d - 1)] : xtail[k];
-            accept = u < T;
-        }
-        if (accept) {
-            perm[a] = (uint8_t)(k + 1);
-            perm[b] = (uint8_t)k;
-            inv[k] = (uint8_t)b;
-            inv[k + 1] = (uint8_t)a;
-            accepts[(int64_t)inst * (K - 1) + k] += 1ull;
-        }
-    }
-    for (int r = threadIdx.x; r < K; r += blockDim.x) atomicMin(&s_min, Ei[r]);
-    __syncthreads();
-    if (threadIdx.x == 0 && s_min < minE[inst]) minE[inst] = s_min;
+    pt_exchange_block(x, blockIdx.x, sweep, threadIdx.x, blockDim.x, &s_min);
 }
 
 // ---------------------------------------------------------------- checks and layout
@@ -384,24 +351,26 @@ __global__ void check_energy_kernel(const unsigned long long* __restrict__ E64,
 }
 
 __global__ void unpack_spins_kernel(const int8_t* __restrict__ spins, int8_t* __restrict__ out,
-                                    int64_t N, int Rp, int R)
+                                    int L, int Rp, int R)
 {
+    const int64_t N = (int64_t)L * L * L;
     const int64_t n = (int64_t)R * N;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int r = (int)(q / N);
         const int64_t i = q % N;
-        out[q] = spins[i * Rp + r];
+        out[q] = spins[storage_of(L, i) * Rp + r];
     }
 }
 
 __global__ void pack_spins_kernel(const int8_t* __restrict__ in, int8_t* __restrict__ spins,
-                                  int64_t N, int Rp, int R, int* __restrict__ bad)
+                                  int L, int Rp, int R, int* __restrict__ bad)
 {
+    const int64_t N = (int64_t)L * L * L;
     const int64_t n = (int64_t)Rp * N;
     for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < n;
          q += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = q / Rp;
+        const int64_t i = logical_of(L, q / Rp);
         const int r = (int)(q % Rp);
         int8_t v = 1;
         if (r < R) {
@@ -461,11 +430,12 @@ int32_t launch_prepare_j6(const int8_t* J3_dev, uint2* j6_dev, uint8_t* j1_dev, 
     return check_launch("prepare_j6");
 }
 
-int32_t launch_init_spins(int8_t* spins, const RunKeys* keys_dev, int I, int64_t N, int Wn, int R,
+int32_t launch_init_spins(int8_t* spins, const RunKeys* keys_dev, int I, int L, int Wn, int R,
                           cudaStream_t st)
 {
+    const int64_t N = (int64_t)L * L * L;
     dim3 grid(grid_for(N * Wn, 1, 8192), I);
-    init_spins_kernel<<<grid, kBlock, 0, st>>>((uint32_t*)spins, keys_dev, N, Wn, R);
+    init_spins_kernel<<<grid, kBlock, 0, st>>>((uint32_t*)spins, keys_dev, L, Wn, R);
     return check_launch("init_spins");
 }
 
@@ -500,15 +470,16 @@ int32_t launch_half_sweep_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
                              int* status, bool unit_j, int I, int L, int Wn, int K, uint32_t sweep,
-                             int colour, cudaStream_t st)
+                             int colour, const ExchangeArgs* xch, unsigned* done, bool* fused,
+                             cudaStream_t st)
 {
+    if (fused) *fused = false;
     if (tile_kernel_supports(I, L, Wn))
         return launch_sweep_tile(spins, j6_ptrs, j1_ptrs, keys, thr_rungs, rung_of_slot, E, status,
                                  true, unit_j, I, L, Wn, K, sweep, colour, st);
     if (rows_kernel_supports(Wn))
         return launch_sweep_rows_pt(spins, j6_ptrs, j1_ptrs, keys, thr_rungs, rung_of_slot, E, unit_j,
-                                    I, L,
-                                    Wn, K, sweep, colour, st);
+                                    I, L, Wn, K, sweep, colour, xch, done, fused, st);
     const int64_t N = (int64_t)L * L * L;
     dim3 grid(sweep_grid_x((N / 2) * Wn, Wn), I);
     half_sweep_kernel<true><<<grid, kBlock, 0, st>>>((uint32_t*)spins, j6_ptrs, keys, thr_rungs,
@@ -524,14 +495,9 @@ int32_t launch_pt_setup(const unsigned long long* E64, int32_t* E, uint8_t* rung
     return check_launch("pt_setup");
 }
 
-int32_t launch_pt_exchange(const RunKeys* keys, const int32_t* E, uint8_t* rung_of_slot,
-                           uint8_t* slot_of_rung, unsigned long long* accepts, int32_t* minE,
-                           const uint32_t* xtab, const uint32_t* xoff, const uint32_t* xlen,
-                           const uint32_t* xtail, int I, int Rp, int K, uint32_t sweep,
-                           cudaStream_t st)
+int32_t launch_pt_exchange(const ExchangeArgs& x, int I, uint32_t sweep, cudaStream_t st)
 {
-    pt_exchange_kernel<<<I, 128, 0, st>>>(keys, E, rung_of_slot, slot_of_rung, accepts, minE, xtab,
-                                          xoff, xlen, xtail, Rp, K, sweep);
+    pt_exchange_kernel<<<I, 128, 0, st>>>(x, sweep);
     return check_launch("pt_exchange");
 }
 
@@ -564,19 +530,20 @@ int32_t launch_narrow_energy(const unsigned long long* E64, int32_t* E, int64_t 
     return check_launch("narrow_energy");
 }
 
-int32_t launch_unpack_spins(const int8_t* spins, int8_t* out, int64_t N, int Rp, int R, int I_index,
-                            int I, cudaStream_t st)
+int32_t launch_unpack_spins(const int8_t* spins, int8_t* out, int L, int Rp, int R, int I_index,
+                            cudaStream_t st)
 {
-    (void)I;
+    const int64_t N = (int64_t)L * L * L;
     unpack_spins_kernel<<<grid_for((int64_t)R * N, 1, 8192), kBlock, 0, st>>>(
-        spins + (int64_t)I_index * N * Rp, out, N, Rp, R);
+        spins + (int64_t)I_index * N * Rp, out, L, Rp, R);
     return check_launch("unpack_spins");
 }
 
-int32_t launch_pack_spins(const int8_t* in, int8_t* spins, int64_t N, int Rp, int R, int* bad,
+int32_t launch_pack_spins(const int8_t* in, int8_t* spins, int L, int Rp, int R, int* bad,
                           cudaStream_t st)
 {
-    pack_spins_kernel<<<grid_for((int64_t)Rp * N, 1, 8192), kBlock, 0, st>>>(in, spins, N, Rp, R, bad);
+    const int64_t N = (int64_t)L * L * L;
+    pack_spins_kernel<<<grid_for((int64_t)Rp * N, 1, 8192), kBlock, 0, st>>>(in, spins, L, Rp, R, bad);
     return check_launch("pack_spins");
 }
 

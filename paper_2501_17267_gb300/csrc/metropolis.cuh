@@ -95,47 +95,63 @@ __device__ __forceinline__ uint32_t bond_term(uint32_t n, const Couplings& c, in
     return (n ^ c.S[q]) & c.M[q];
 }
 
+// Energy lanes.  For parallel tempering each thread sums, per replica byte, the k of
+// every flip it makes (the energy rises by 2k).  The four sums share one word: bytes are
+// added modulo 256 without carries between them, which is exact while |sum| <= 127,
+// i.e. for kLaneCapacity<KMAX> flips of |k| <= KMAX between folds.
+template <int KMAX>
+constexpr int kLaneCapacity = 127 / KMAX;
+
+// Byte-wise a + b modulo 256 (no carry from one byte into the next).
+__device__ __forceinline__ uint32_t add_bytes(uint32_t a, uint32_t b)
+{
+    return ((a & 0x7F7F7F7Fu) + (b & 0x7F7F7F7Fu)) ^ ((a ^ b) & 0x80808080u);
+}
+
+// Sum of byte b of a lane word, as a signed value.
+__device__ __forceinline__ int lane_sum(uint32_t acc, int b)
+{
+    return (int)(int8_t)((acc >> (8 * b)) & 0xFFu);
+}
+
 // Metropolis step for WG words (4*WG replicas) of one site.
 //   self     spins of the site, updated in place
 //   P        negative-term counts from the six neighbours
 //   vmask    bit 7 of every byte that is a real replica
-//   thr      PT: row of slot 4*w0 (rows kThrStride apart); SA: the sweep's row
-//   acc/cnt  PT energy lanes: per byte, sum of (k + 12) and number of flips
+//   thr      PT: row of slot 4*w0 (rows THR_STRIDE apart); SA: the sweep's row
+//   acc      PT energy lanes (see add_bytes)
 // Returns true when some byte flipped.
-// Per-byte energy lanes: each flip adds k + BIAS (BIAS = 12 in general, 6 when all
-// |J| = 1 so that k + 6 <= 12) and one count; kLaneCapacity<BIAS> flips fit 8 bits.
-template <int BIAS>
-constexpr int kLaneCapacity = 255 / (BIAS == 6 ? 12 : 24);
-
-template <bool PT, int WG, int THR_STRIDE, int BIAS = 12>
+// DRAW_ALWAYS: compute the draws whether or not a byte needs one.  They depend only on
+// (site, sweep, word), so the compiler can then overlap them with the loads of the
+// neighbour words; otherwise they sit behind a warp-uniform "any draw needed" branch.
+template <bool PT, int WG, int THR_STRIDE, bool DRAW_ALWAYS = false>
 __device__ __forceinline__ bool update_words(uint32_t (&self)[WG], const uint32_t (&P)[WG],
                                              const uint32_t (&vmask)[WG], int msum, uint32_t site,
                                              uint32_t sweep, uint32_t w0, const RunKeys& key,
-                                             const uint32_t* __restrict__ thr,
-                                             uint32_t (&acc)[WG], uint32_t (&cnt)[WG])
+                                             const uint32_t* __restrict__ thr, uint32_t (&acc)[WG])
 {
     const uint32_t ones = 0x01010101u;
     const uint32_t C2 = (uint32_t)(2 * msum) * ones;
     const uint32_t T1 = (uint32_t)(msum + 1) * ones;
     const uint32_t Km = (uint32_t)msum * ones;
-    const uint32_t Bias = (uint32_t)(BIAS - msum) * ones;
-    uint32_t W[WG], Wg[WG], need[WG], ff[WG];
+    uint32_t W[WG], Kg[WG], need[WG], ff[WG];
     uint32_t anyneed = 0;
 #pragma unroll
     for (int wi = 0; wi < WG; ++wi) {
         W[wi] = (P[wi] & ~self[wi]) | ((C2 - P[wi]) & self[wi]);
-        Wg[wi] = W[wi] | 0x80808080u;  // guard bits: byte-wise subtraction without borrows
-        need[wi] = (Wg[wi] - T1) & vmask[wi];                 // bit 7: k > 0, needs a draw
-        ff[wi] = prmt(vmask[wi] & ~need[wi], 0u, 0xBA98u);     // 0xFF: flips for free
+        const uint32_t Wg = W[wi] | 0x80808080u;  // guard bits: byte-wise subtraction, no borrows
+        Kg[wi] = Wg - Km;                           // per byte 128 + k
+        need[wi] = (Wg - T1) & vmask[wi];           // bit 7: k > 0, needs a draw
+        ff[wi] = prmt(vmask[wi] & ~need[wi], 0u, 0xBA98u);  // 0xFF: flips for free
         anyneed |= need[wi];
     }
-    if (__any_sync(__activemask(), anyneed != 0)) {
+    if (DRAW_ALWAYS || __any_sync(__activemask(), anyneed != 0)) {
 #pragma unroll
         for (int wi = 0; wi < WG; ++wi) {
             const Philox4 u = philox4x32_10(site, sweep, w0 + (uint32_t)wi, kDomainMetropolis,
                                             key.k0, key.k1);
-            const uint32_t nf = prmt(need[wi], 0u, 0xBA98u);            // 0xFF: needs a draw
-            const uint32_t kidx = (Wg[wi] - Km) & 0x7F7F7F7Fu & nf;     // k, or 0
+            const uint32_t nf = prmt(need[wi], 0u, 0xBA98u);    // 0xFF: needs a draw
+            const uint32_t kidx = Kg[wi] & 0x7F7F7F7Fu & nf;     // k, or 0
             const uint32_t* row = PT ? thr + 4 * wi * THR_STRIDE : thr;
             uint32_t ok = 0;
 #pragma unroll
@@ -152,19 +168,9 @@ __device__ __forceinline__ bool update_words(uint32_t (&self)[WG], const uint32_
     for (int wi = 0; wi < WG; ++wi) {
         self[wi] ^= ff[wi] & 0xFEFEFEFEu;
         any |= ff[wi] != 0;
-        if (PT) {
-            acc[wi] += (W[wi] + Bias) & ff[wi];  // k + BIAS on flipped bytes
-            cnt[wi] += ff[wi] & ones;
-        }
+        if (PT) acc[wi] = add_bytes(acc[wi], (Kg[wi] ^ 0x80808080u) & ff[wi]);  // k mod 256
     }
     return any;
-}
-
-// Energy change per slot from the 8-bit lanes: 2 * (sum (k + BIAS) - BIAS * flips).
-template <int BIAS = 12>
-__device__ __forceinline__ int lane_energy(uint32_t acc, uint32_t cnt, int b)
-{
-    return 2 * ((int)((acc >> (8 * b)) & 0xFFu) - BIAS * (int)((cnt >> (8 * b)) & 0xFFu));
 }
 
 }  // namespace mp

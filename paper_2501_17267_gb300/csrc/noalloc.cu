@@ -96,7 +96,7 @@ extern "C" int32_t sg_energy_noalloc(int32_t L, const int8_t* J3_dev, const int8
     SG_TRY_CUDA(cudaMemcpyAsync(j6_ptr, &j6c, sizeof(j6c), cudaMemcpyHostToDevice, st));
     rc = launch_prepare_j6(J3_dev, j6, j1, L, st);
     if (rc != SG_OK) return rc;
-    rc = launch_pack_spins(spins_dev, packed, (int64_t)N, Rp, n_configs, bad, st);
+    rc = launch_pack_spins(spins_dev, packed, L, Rp, n_configs, bad, st);
     if (rc != SG_OK) return rc;
     rc = launch_energy(packed, j6_ptr, 1, L, Wn, E64, st);
     if (rc != SG_OK) return rc;

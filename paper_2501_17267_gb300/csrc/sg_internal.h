@@ -81,15 +81,39 @@ int32_t build_exchange_tables(const std::vector<double>& ladder, int64_t dmax,
 int32_t instance_device_j6(sg_instance* inst, cudaStream_t stream, const uint2** j6,
                            const uint8_t** j1);
 
+// ---- spin storage order ----
+// Within every row (y, z) of the lattice the L/2 sites with even x are stored first,
+// then the L/2 sites with odd x, so that the sites of one checkerboard colour in a row
+// are contiguous.  Logical site i = x + L*(y + L*z) keeps naming a site everywhere else
+// (random-number counters, couplings, inputs and outputs).
+#if defined(__CUDACC__)
+#define SG_HDI __host__ __device__ __forceinline__
+#else
+#define SG_HDI inline
+#endif
+SG_HDI int64_t storage_of(int L, int64_t logical)
+{
+    const int64_t row = logical / L;
+    const int x = (int)(logical - row * L);
+    return row * L + (x & 1) * (L >> 1) + (x >> 1);
+}
+SG_HDI int64_t logical_of(int L, int64_t storage)
+{
+    const int64_t row = storage / L;
+    const int pos = (int)(storage - row * L), H = L >> 1;
+    return row * L + (pos < H ? 2 * pos : 2 * (pos - H) + 1);
+}
+
 // ---- kernels (kernels.cu) ----
 struct RunKeys {
     uint32_t k0, k1;
 };
+struct ExchangeArgs;  // exchange.cuh
 
 int32_t launch_prepare_j6(const int8_t* J3_dev, uint2* j6_dev, uint8_t* j1_dev, int L,
                           cudaStream_t st);
-int32_t launch_init_spins(int8_t* spins, const RunKeys* keys_dev, int I, int64_t N, int Wn,
-                          int R, cudaStream_t st);
+int32_t launch_init_spins(int8_t* spins, const RunKeys* keys_dev, int I, int L, int Wn, int R,
+                          cudaStream_t st);
 int32_t launch_energy(const int8_t* spins, const uint2* const* j6_ptrs, int I, int L, int Wn,
                       unsigned long long* E_out /* [I][Wn*4] */, cudaStream_t st);
 int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs,
@@ -102,6 +126,7 @@ int32_t launch_half_sweep_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint32_t* thr_rungs /* [K][kThrRow] */,
                              const uint8_t* rung_of_slot /* [I][Wn*4] */, int32_t* E, int* status,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
+                             const ExchangeArgs* xch, unsigned* done, bool* fused,
                              cudaStream_t st);
 // sweep.cu: row-mapped sweep kernel (used whenever it supports the word count)
 bool rows_kernel_supports(int Wn);
@@ -111,22 +136,20 @@ int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_row, bool unit_j, int I, int L, int Wn, int R,
                              uint32_t sweep, int colour, cudaStream_t st);
+// xch != nullptr: the launch may also perform the PT exchange (last block per instance);
+// *fused reports whether it did.  done: [I] zeroed counters.
 int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
-                             cudaStream_t st);
+                             const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st);
 // tile.cu: shared-memory streaming sweep (used when it supports the shape)
 bool tile_kernel_supports(int I, int L, int Wn);
 int32_t launch_sweep_tile(int8_t* spins, const uint2* const* j6_ptrs, const uint8_t* const* j1_ptrs,
                           const RunKeys* keys, const uint32_t* thr, const uint8_t* rung_of_slot,
                           int32_t* E, int* status, bool pt, bool unit_j, int I, int L, int Wn,
                           int Rvalid, uint32_t sweep, int colour, cudaStream_t st);
-int32_t launch_pt_exchange(const RunKeys* keys, const int32_t* E, uint8_t* rung_of_slot,
-                           uint8_t* slot_of_rung, unsigned long long* accepts,
-                           int32_t* minE, const uint32_t* xtab, const uint32_t* xoff,
-                           const uint32_t* xlen, const uint32_t* xtail, int I, int Rp, int K,
-                           uint32_t sweep, cudaStream_t st);
+int32_t launch_pt_exchange(const ExchangeArgs& x, int I, uint32_t sweep, cudaStream_t st);
 int32_t launch_pt_setup(const unsigned long long* E64, int32_t* E, uint8_t* rung_of_slot,
                         uint8_t* slot_of_rung, unsigned long long* accepts, int32_t* minE,
                         int I, int Rp, int K, cudaStream_t st);
@@ -134,9 +157,9 @@ int32_t launch_check_energy(const unsigned long long* E64, const int32_t* E, int
                             int R, int* mismatch, cudaStream_t st);
 int32_t launch_copy_energies(const unsigned long long* E64, int64_t* E, int n, cudaStream_t st);
 int32_t launch_narrow_energy(const unsigned long long* E64, int32_t* E, int64_t n, cudaStream_t st);
-int32_t launch_unpack_spins(const int8_t* spins, int8_t* out, int64_t N, int Rp, int R,
-                            int I_index, int I, cudaStream_t st);
-int32_t launch_pack_spins(const int8_t* in, int8_t* spins, int64_t N, int Rp, int R,
-                          int* bad, cudaStream_t st);
+int32_t launch_unpack_spins(const int8_t* spins, int8_t* out, int L, int Rp, int R,
+                            int I_index, cudaStream_t st);
+int32_t launch_pack_spins(const int8_t* in, int8_t* spins, int L, int Rp, int R, int* bad,
+                          cudaStream_t st);
 
 }  // namespace sg

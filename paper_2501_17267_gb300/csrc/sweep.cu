@@ -24,6 +24,7 @@
 // thread with warp reductions.
 #include <stdlib.h>
 
+#include "exchange.cuh"
 #include "metropolis.cuh"
 #include "philox.cuh"
 #include "sg_internal.h"
@@ -45,9 +46,12 @@ struct SweepArgs {
     uint32_t Lmagic;              // ceil(2^32 / L): row / L by multiply-high
     uint32_t sweep;
     int colour;
+    ExchangeArgs x;               // PT exchange performed by the last block of each instance
+    unsigned* done;               // [I] blocks finished in this launch (reset by the last one)
 };
 
-template <bool PT, bool UNITJ, int WG, int CH, int MINB>
+template <bool PT, bool UNITJ, int WG, int CH, bool PAD, int MINB = 2, bool DRAW = false,
+          bool XCH = false>
 __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a)
 {
     __shared__ uint32_t s_thr[PT ? 256 * kThrStride : kThrRow];
@@ -80,7 +84,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
     const int wbase = g * CH * WG;  // first word owned by this thread
 
     uint32_t vmask[CH][WG];  // bit 7 of each byte that is a real replica (not padding)
-    uint32_t acc[CH][WG], cnt[CH][WG];
+    uint32_t acc[CH][WG];
 #pragma unroll
     for (int ch = 0; ch < CH; ++ch)
 #pragma unroll
@@ -89,12 +93,11 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
 #pragma unroll
             for (int b = 0; b < 4; ++b)
                 if (4 * (wbase + ch * WG + wi) + b < a.Rvalid) m |= 0x80u << (8 * b);
-            vmask[ch][wi] = m;
+            vmask[ch][wi] = PAD ? m : 0x80808080u;
             acc[ch][wi] = 0;
-            cnt[ch][wi] = 0;
         }
 
-    constexpr int BIAS = UNITJ ? 6 : 12;
+    constexpr int KMAX = UNITJ ? 6 : 12;  // largest |k| of one flip
     // Folds the 8-bit energy lanes into the block's per-slot sums.  Called by whole
     // warps at the same point of the row loop.
     auto flush = [&]() {
@@ -109,7 +112,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
                     const int slot = 4 * (wbase + ch * WG + wi) + b;
-                    int d = mp::lane_energy<BIAS>(acc[ch][wi], cnt[ch][wi], b);
+                    int d = 2 * mp::lane_sum(acc[ch][wi], b);
                     if (full_warp_same) {
                         d = __reduce_add_sync(0xFFFFFFFFu, d);
                         if (lane == 0 && d) atomicAdd(&s_dE[slot], d);
@@ -121,7 +124,6 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
                     }
                 }
                 acc[ch][wi] = 0;
-                cnt[ch][wi] = 0;
             }
     };
     int items = 0;  // site updates folded into the 8-bit lanes since the last flush
@@ -139,16 +141,20 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
         const int rowoff = row * L;
         for (int j = j0; j < H; j += JX) {
             const int x = 2 * j + par;
-            const int i = rowoff + x;
-            const int nb[6] = {x + 1 == L ? i + 1 - L : i + 1, x == 0 ? i + L - 1 : i - 1,
-                               i + dyp, i + dym, i + dzp, i + dzm};
+            const int i = rowoff + x;  // logical site (counters, couplings)
+            // storage positions (colour-split rows): this site is entry j of half `par`;
+            // its x neighbours are entries j + par and j + par - 1 of the other half
+            const int is = rowoff + par * H + j;
+            const int ho = rowoff + (1 - par) * H;
+            const int jp = j + par == H ? 0 : j + par, jm = j + par == 0 ? H - 1 : j + par - 1;
+            const int nb[6] = {ho + jp, ho + jm, is + dyp, is + dym, is + dzp, is + dzm};
             const mp::Couplings cp = UNITJ ? mp::decode_unit(a.j1_ptrs[inst][i])
                                            : mp::decode_general(a.j6_ptrs[inst][i]);
 #pragma unroll
             for (int ch = 0; ch < CH; ++ch) {
                 const int w0 = wbase + ch * WG;
                 uint32_t self[WG], P[WG];
-                mp::load_words<WG>(s + (size_t)i * Wn + w0, self);
+                mp::load_words<WG>(s + (size_t)is * Wn + w0, self);
 #pragma unroll
                 for (int wi = 0; wi < WG; ++wi) P[wi] = 0;
 #pragma unroll
@@ -159,12 +165,11 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
                     for (int wi = 0; wi < WG; ++wi) P[wi] += mp::bond_term(n[wi], cp, q);
                 }
                 const uint32_t* thr = PT ? s_thr + 4 * w0 * kThrStride : s_thr;
-                if (mp::update_words<PT, WG, kThrStride, BIAS>(self, P, vmask[ch], cp.msum, (uint32_t)i,
-                                                         a.sweep, (uint32_t)w0, key, thr, acc[ch],
-                                                         cnt[ch]))
-                    mp::store_words<WG>(s + (size_t)i * Wn + w0, self);
+                if (mp::update_words<PT, WG, kThrStride, DRAW>(self, P, vmask[ch], cp.msum, (uint32_t)i,
+                                                         a.sweep, (uint32_t)w0, key, thr, acc[ch]))
+                    mp::store_words<WG>(s + (size_t)is * Wn + w0, self);
             }
-            if (PT && ++items == mp::kLaneCapacity<BIAS>) {
+            if (PT && ++items == mp::kLaneCapacity<KMAX>) {
                 flush();
                 items = 0;
             }
@@ -177,6 +182,21 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
         int32_t* Ei = a.E + (size_t)inst * Rp;
         for (int q = tid; q < Rp; q += nthreads)
             if (s_dE[q]) atomicAdd(&Ei[q], s_dE[q]);
+        if (XCH) {
+            // The block that finishes last for this instance performs the exchange: every
+            // block publishes its energy sums, then counts itself done; no block waits.
+            __shared__ int s_last;
+            __shared__ int32_t s_min;
+            __threadfence();
+            __syncthreads();
+            if (tid == 0) s_last = atomicAdd(&a.done[inst], 1u) == gridDim.x - 1;
+            __syncthreads();
+            if (s_last) {
+                __threadfence();
+                pt_exchange_block(a.x, inst, a.sweep, tid, nthreads, &s_min);
+                if (tid == 0) a.done[inst] = 0;
+            }
+        }
     }
 }
 
@@ -192,6 +212,18 @@ int max_chunks()
     static const int v = [] {
         const char* e = getenv("SG_SWEEP_MAX_CH");
         return (e && atoi(e) == 1) ? 1 : 2;
+    }();
+    return v;
+}
+
+// Tuning knob SG_ROWS_MINB (2, 3 or 4): resident blocks per SM the register budget is
+// cut for, for the padding-free four-word variants.
+int rows_min_blocks()
+{
+    static const int v = [] {
+        const char* e = getenv("SG_ROWS_MINB");
+        const int m = e ? atoi(e) : 0;
+        return (m == 3 || m == 4) ? m : 2;
     }();
     return v;
 }
@@ -216,7 +248,8 @@ SweepShape sweep_shape(int I, int L, int Wn)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     // rows per thread: enough blocks for about two per SM, so that each block fills
     // its threshold table and reduces its energies once for many rows
-    long long rpt = ((long long)LL * I + (long long)TY * 2 * sms - 1) / ((long long)TY * 2 * sms);
+    const long long bps = rows_min_blocks();
+    long long rpt = ((long long)LL * I + (long long)TY * bps * sms - 1) / ((long long)TY * bps * sms);
     if (rpt < 1) rpt = 1;
     const char* e = getenv("SG_ROWS_RPT");  // tuning knob: rows per thread
     if (e && atoi(e) >= 1) rpt = atoi(e);
@@ -226,42 +259,73 @@ SweepShape sweep_shape(int I, int L, int Wn)
     return sh;
 }
 
-template <bool PT, bool UNITJ>
-void launch_variant(const SweepShape& sh, const SweepArgs& a, int I, cudaStream_t st)
+// Tuning knob SG_DRAW_ALWAYS (default 1): compute the draws unconditionally in the
+// padding-free variants (0: only when some lane of the warp needs one).
+bool draw_always()
 {
-    (void)I;
-    static const int minb = [] {
-        const char* e = getenv("SG_ROWS_MINB");  // tuning knob: blocks per SM the registers allow
-        return (e && atoi(e) == 3) ? 3 : 2;
+    static const bool v = [] {
+        const char* e = getenv("SG_DRAW_ALWAYS");
+        return !(e && atoi(e) == 0);
     }();
-    if (sh.WG == 4 && sh.CH == 2) {
-        if (minb == 3)
-            sweep_rows_kernel<PT, UNITJ, 4, 2, 3><<<sh.grid, sh.block, 0, st>>>(a);
+    return v;
+}
+
+template <bool PT, bool UNITJ, int CH>
+void launch_nopad(const SweepShape& sh, const SweepArgs& a, bool xch, cudaStream_t st)
+{
+    if (draw_always() && rows_min_blocks() == 2) {
+        if (PT && xch)
+            sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2, true, true><<<sh.grid, sh.block, 0, st>>>(a);
         else
-            sweep_rows_kernel<PT, UNITJ, 4, 2, 2><<<sh.grid, sh.block, 0, st>>>(a);
-    } else if (sh.WG == 4) {
-        if (minb == 3)
-            sweep_rows_kernel<PT, UNITJ, 4, 1, 3><<<sh.grid, sh.block, 0, st>>>(a);
-        else
-            sweep_rows_kernel<PT, UNITJ, 4, 1, 2><<<sh.grid, sh.block, 0, st>>>(a);
-    } else if (sh.WG == 2) {
-        sweep_rows_kernel<PT, UNITJ, 2, 1, 2><<<sh.grid, sh.block, 0, st>>>(a);
-    } else {
-        sweep_rows_kernel<PT, UNITJ, 1, 1, 2><<<sh.grid, sh.block, 0, st>>>(a);
+            sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2, true><<<sh.grid, sh.block, 0, st>>>(a);
+        return;
+    }
+    switch (rows_min_blocks()) {
+    case 4:
+        sweep_rows_kernel<PT, UNITJ, 4, CH, false, 4><<<sh.grid, sh.block, 0, st>>>(a);
+        break;
+    case 3:
+        sweep_rows_kernel<PT, UNITJ, 4, CH, false, 3><<<sh.grid, sh.block, 0, st>>>(a);
+        break;
+    default:
+        sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2><<<sh.grid, sh.block, 0, st>>>(a);
     }
 }
 
+// Launches the variant for the shape; returns true when it also performed the exchange.
+template <bool PT, bool UNITJ>
+bool launch_variant(const SweepShape& sh, const SweepArgs& a, bool pad, bool xch, cudaStream_t st)
+{
+    const bool fused = xch && !pad && draw_always() && rows_min_blocks() == 2 && sh.WG == 4;
+    if (sh.WG == 4 && sh.CH == 2) {
+        if (pad)
+            sweep_rows_kernel<PT, UNITJ, 4, 2, true><<<sh.grid, sh.block, 0, st>>>(a);
+        else
+            launch_nopad<PT, UNITJ, 2>(sh, a, fused, st);
+    } else if (sh.WG == 4) {
+        if (pad)
+            sweep_rows_kernel<PT, UNITJ, 4, 1, true><<<sh.grid, sh.block, 0, st>>>(a);
+        else
+            launch_nopad<PT, UNITJ, 1>(sh, a, fused, st);
+    } else if (sh.WG == 2) {
+        sweep_rows_kernel<PT, UNITJ, 2, 1, true><<<sh.grid, sh.block, 0, st>>>(a);
+    } else {
+        sweep_rows_kernel<PT, UNITJ, 1, 1, true><<<sh.grid, sh.block, 0, st>>>(a);
+    }
+    return fused;
+}
+
 template <bool PT>
-int32_t launch_rows(SweepArgs a, int I, bool unit_j, cudaStream_t st)
+int32_t launch_rows(SweepArgs a, int I, bool unit_j, bool xch, bool* fused, cudaStream_t st)
 {
     const SweepShape sh = sweep_shape(I, a.L, a.Wn);
     a.G = sh.G;
     a.rows_per_thread = sh.rows_per_thread;
     a.Lmagic = (uint32_t)((0x100000000ull + (uint64_t)a.L - 1) / (uint64_t)a.L);
-    if (unit_j)
-        launch_variant<PT, true>(sh, a, I, st);
-    else
-        launch_variant<PT, false>(sh, a, I, st);
+    const bool pad = a.Rvalid != 4 * a.Wn;  // padding replicas in the last word
+    const bool f = unit_j ? launch_variant<PT, true>(sh, a, pad, xch, st)
+                          : launch_variant<PT, false>(sh, a, pad, xch, st);
+    if (fused) *fused = f;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("sweep launch failed: %s", cudaGetErrorString(e));
@@ -295,14 +359,14 @@ int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
     a.Rvalid = R;
     a.sweep = sweep;
     a.colour = colour;
-    return launch_rows<false>(a, I, unit_j, st);
+    return launch_rows<false>(a, I, unit_j, false, nullptr, st);
 }
 
 int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
-                             cudaStream_t st)
+                             const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st)
 {
     SweepArgs a{};
     a.spins = reinterpret_cast<uint32_t*>(spins);
@@ -317,7 +381,9 @@ int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
     a.Rvalid = K;
     a.sweep = sweep;
     a.colour = colour;
-    return launch_rows<true>(a, I, unit_j, st);
+    if (xch) a.x = *xch;
+    a.done = done;
+    return launch_rows<true>(a, I, unit_j, xch != nullptr, fused, st);
 }
 
 }  // namespace sg

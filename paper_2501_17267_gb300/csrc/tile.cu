@@ -26,7 +26,7 @@ namespace {
 
 constexpr int kThrStrideT = 17;
 constexpr int kRing = 4;
-constexpr int kMaxLaneSteps = 10;  // site updates a thread may fold into its 8-bit energy lanes
+constexpr int kMaxLaneSteps = 10;  // site updates a thread may add to its 8-bit energy lanes
 constexpr uint32_t kSpinLimit = 1u << 24;  // try_wait rounds before a wait gives up
 
 __device__ __forceinline__ uint32_t smem_addr(const void* p)
@@ -87,7 +87,7 @@ struct TileArgs {
     int colour;
 };
 
-template <bool PT, bool UNITJ, int WG, int CH>
+template <bool PT, bool UNITJ, int WG, int CH, bool PAD = true>
 __global__ void __launch_bounds__(256, 2) sweep_tile_kernel(const TileArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -155,7 +155,7 @@ __global__ void __launch_bounds__(256, 2) sweep_tile_kernel(const TileArgs a)
     const int wbase = g * CH * WG;
 
     uint32_t vmask[CH][WG];
-    uint32_t acc[CH][WG], cnt[CH][WG];
+    uint32_t acc[CH][WG];
 #pragma unroll
     for (int ch = 0; ch < CH; ++ch)
 #pragma unroll
@@ -164,9 +164,8 @@ __global__ void __launch_bounds__(256, 2) sweep_tile_kernel(const TileArgs a)
 #pragma unroll
             for (int b = 0; b < 4; ++b)
                 if (4 * (wbase + ch * WG + wi) + b < a.Rvalid) m |= 0x80u << (8 * b);
-            vmask[ch][wi] = m;
+            vmask[ch][wi] = PAD ? m : 0x80808080u;
             acc[ch][wi] = 0;
-            cnt[ch][wi] = 0;
         }
 
 
@@ -184,7 +183,7 @@ __global__ void __launch_bounds__(256, 2) sweep_tile_kernel(const TileArgs a)
 #pragma unroll
                 for (int b = 0; b < 4; ++b) {
                     const int slot = 4 * (wbase + ch * WG + wi) + b;
-                    int d = mp::lane_energy(acc[ch][wi], cnt[ch][wi], b);
+                    int d = 2 * mp::lane_sum(acc[ch][wi], b);
                     if (full_warp_same) {
                         d = __reduce_add_sync(0xFFFFFFFFu, d);
                         if (lane == 0 && d) atomicAdd(&s_dE[slot], d);
@@ -196,7 +195,6 @@ __global__ void __launch_bounds__(256, 2) sweep_tile_kernel(const TileArgs a)
                     }
                 }
                 acc[ch][wi] = 0;
-                cnt[ch][wi] = 0;
             }
     };
 
@@ -223,20 +221,24 @@ __global__ void __launch_bounds__(256, 2) sweep_tile_kernel(const TileArgs a)
             const uint32_t* own_row = b0 + (size_t)(r + 1) * rowW;
             for (int j = j0; j < H; j += JX) {
                 const int x = 2 * j + par;
-                const int xp = x + 1 == L ? 0 : x + 1, xm = x == 0 ? L - 1 : x - 1;
-                const int i = (z * L + y) * L + x;
+                const int i = (z * L + y) * L + x;  // logical site (counters, couplings)
+                // storage positions in a row (colour-split): this site is entry j of half
+                // `par`, its x neighbours entries j + par and j + par - 1 of the other half
+                const int px = par * H + j;
+                const int jp = j + par == H ? 0 : j + par, jm = j + par == 0 ? H - 1 : j + par - 1;
+                const int xp = (1 - par) * H + jp, xm = (1 - par) * H + jm;
                 const mp::Couplings cp = UNITJ ? mp::decode_unit(a.j1_ptrs[inst][i])
                                                : mp::decode_general(a.j6_ptrs[inst][i]);
                 const uint32_t* nbp[6] = {own_row + xp * Wn, own_row + xm * Wn,
-                                          b0 + (size_t)(r + 2) * rowW + x * Wn,
-                                          b0 + (size_t)r * rowW + x * Wn,
-                                          bp + (size_t)(r + 1) * rowW + x * Wn,
-                                          bm + (size_t)(r + 1) * rowW + x * Wn};
+                                          b0 + (size_t)(r + 2) * rowW + px * Wn,
+                                          b0 + (size_t)r * rowW + px * Wn,
+                                          bp + (size_t)(r + 1) * rowW + px * Wn,
+                                          bm + (size_t)(r + 1) * rowW + px * Wn};
 #pragma unroll
                 for (int ch = 0; ch < CH; ++ch) {
                     const int w0 = wbase + ch * WG;
                     uint32_t self[WG], P[WG];
-                    mp::load_words<WG>(own_row + x * Wn + w0, self);
+                    mp::load_words<WG>(own_row + px * Wn + w0, self);
 #pragma unroll
                     for (int wi = 0; wi < WG; ++wi) P[wi] = 0;
 #pragma unroll
@@ -249,8 +251,8 @@ __global__ void __launch_bounds__(256, 2) sweep_tile_kernel(const TileArgs a)
                     const uint32_t* thr = PT ? s_thr + 4 * w0 * kThrStrideT : s_thr;
                     if (mp::update_words<PT, WG, kThrStrideT>(self, P, vmask[ch], cp.msum, (uint32_t)i,
                                                               a.sweep, (uint32_t)w0, key, thr,
-                                                              acc[ch], cnt[ch]))
-                        mp::store_words<WG>(s + (size_t)i * Wn + w0, self);
+                                                              acc[ch]))
+                        mp::store_words<WG>(s + ((size_t)(z * L + y) * L + px) * Wn + w0, self);
                 }
             }
         }
