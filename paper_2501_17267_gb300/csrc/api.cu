@@ -40,6 +40,24 @@ Stats& stats()
     return s;
 }
 
+}  // namespace
+
+bool stats_timing()
+{
+    std::lock_guard<std::mutex> g(stats().mu);
+    return stats().timing;
+}
+
+void stats_add(int kind, int64_t launches, int64_t units, double device_ms)
+{
+    std::lock_guard<std::mutex> g(stats().mu);
+    stats().totals.launches[kind] += launches;
+    stats().totals.units[kind] += units;
+    stats().totals.device_ms[kind] += device_ms;
+}
+
+namespace {
+
 // Per-run recorder.  Each launch is counted; with timing on it is bracketed by two
 // events on its stream, resolved by finish() once the run has synchronised.
 class LaunchLog {
@@ -575,6 +593,35 @@ extern "C" int32_t sg_sa_run_batch(const sg_instance* const* insts, const sg_sa_
         const sg_sa_params& p = ps[a];
         groups[std::make_tuple(insts[a]->L, p.replicas, p.sweeps, p.beta0, p.beta1, p.schedule)]
             .push_back(a);
+    }
+    // A batch of uneven shapes runs in one persistent launch (batch.cu); a batch of one
+    // shape uses the sweep kernels that spread each instance over many blocks.  Knob
+    // SG_BATCH_PLANES = 1 / 0 forces one or the other.
+    const char* knob = getenv("SG_BATCH_PLANES");
+    const bool planes = knob ? atoi(knob) == 1 : groups.size() > 1;
+    if (planes && n > 0) {
+        std::vector<int> all(n);
+        for (int a = 0; a < n; ++a) all[a] = a;
+        int64_t units = 0;
+        for (int a = 0; a < n; ++a) units += insts[a]->N * (int64_t)ps[a].replicas * ps[a].sweeps;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        const bool timing = stats_timing();
+        if (timing) {
+            cudaEventCreate(&e0);
+            cudaEventCreate(&e1);
+            cudaEventRecord(e0, st);
+        }
+        const int32_t rc = run_sa_planes(all, insts, ps, outs, st, nullptr, nullptr);
+        float ms = 0.f;
+        if (timing) {
+            cudaEventRecord(e1, st);
+            cudaEventSynchronize(e1);
+            cudaEventElapsedTime(&ms, e0, e1);
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+        if (rc == SG_OK) stats_add(SG_KERNEL_SWEEP, 1, units, ms);
+        return rc;
     }
     for (auto& g : groups)
         for (size_t at = 0; at < g.second.size(); at += kMaxGroup) {

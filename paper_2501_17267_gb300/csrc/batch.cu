@@ -1,0 +1,634 @@
+// batch.cu -- simulated annealing of many instances of uneven size in one persistent
+// launch (App. D.1 run on a batch).
+//
+// Annealing chains are independent: replicas never interact.  A batch is cut into
+// "planes", one per (instance, group of WG consecutive replica words); a plane holds
+// its chain's spins for every site, [N][WG] words in storage order, so the threads of
+// a block read consecutive 4*WG-byte records.  One persistent kernel runs every plane
+// from the first sweep to the last: each block takes the next plane from an atomic
+// counter (planes are ordered by decreasing work, largest first), sweeps it colour
+// by colour with only block barriers in between -- no other block touches its
+// replicas -- and takes another.  No block ever waits on another.
+//
+// Results are byte-identical to separate runs: every draw is named by (site, sweep,
+// word of the instance), independent of how the batch is cut.
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <fstream>
+#include <map>
+#include <mutex>
+#include <sstream>
+#include <string>
+#include <vector>
+
+#include "metropolis.cuh"
+#include "philox.cuh"
+#include "sg_internal.h"
+
+namespace sg {
+
+struct Plane {
+    uint32_t* spins;        // [N][WG] words, storage order
+    const uint8_t* j1;      // sign bits (unit couplings) or nullptr
+    const uint2* j6;        // six-coupling records
+    const uint32_t* thr;    // [S][kThrRow] thresholds of the plane's schedule
+    uint32_t k0, k1;        // Philox key of the run
+    int L, S, w0, R;        // side, sweeps, first word (of the instance) in the plane, replicas
+    uint32_t Lmagic, Hmagic;  // ceil(2^32 / L), ceil(2^32 / (L/2))
+    int out;                // index of the instance in the batch
+};
+
+namespace {
+
+__device__ __forceinline__ int div_magic(int v, uint32_t m) { return (int)__umulhi((uint32_t)v, m); }
+
+// Persistent sweep kernel.  `order` lists plane indices by decreasing work.
+template <int WG, bool UNITJ>
+__global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict__ planes,
+                                                        const int* __restrict__ order, int n_planes,
+                                                        unsigned* __restrict__ next)
+{
+    __shared__ int s_item;
+    __shared__ uint32_t s_thr[kThrRow];
+    const int tid = threadIdx.x, nthreads = blockDim.x;
+    for (;;) {
+        if (tid == 0) s_item = (int)atomicAdd(next, 1u);
+        __syncthreads();
+        const int it = s_item;
+        if (it >= n_planes) break;
+        const Plane p = planes[order[it]];
+        const int L = p.L, H = L >> 1, LL = L * L;
+        const int half = LL * H;  // sites of one colour
+        const RunKeys key{p.k0, p.k1};
+        uint32_t vmask[WG], acc[WG];
+#pragma unroll
+        for (int wi = 0; wi < WG; ++wi) {
+            uint32_t m = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (4 * (p.w0 + wi) + b < p.R) m |= 0x80u << (8 * b);
+            vmask[wi] = m;
+            acc[wi] = 0;
+        }
+        for (int sw = 0; sw < p.S; ++sw) {
+            if (tid < kThrRow) s_thr[tid] = p.thr[(size_t)sw * kThrRow + tid];
+            __syncthreads();
+            for (int colour = 0; colour < 2; ++colour) {
+                for (int q = tid; q < half; q += nthreads) {
+                    const int row = div_magic(q, p.Hmagic);
+                    const int j = q - row * H;
+                    const int z = div_magic(row, p.Lmagic);
+                    const int y = row - z * L;
+                    const int par = (y + z + colour) & 1;
+                    const int rowoff = row * L;
+                    const int i = rowoff + 2 * j + par;  // logical site
+                    const int is = rowoff + par * H + j;  // storage position
+                    const int ho = rowoff + (1 - par) * H;
+                    const int jp = j + par == H ? 0 : j + par, jm = j + par == 0 ? H - 1 : j + par - 1;
+                    const int dyp = (y + 1 == L ? 1 - L : 1) * L, dym = (y == 0 ? L - 1 : -1) * L;
+                    const int dzp = (z + 1 == L ? 1 - L : 1) * LL, dzm = (z == 0 ? L - 1 : -1) * LL;
+                    const int nb[6] = {ho + jp, ho + jm, is + dyp, is + dym, is + dzp, is + dzm};
+                    const mp::Couplings cp = UNITJ ? mp::decode_unit(p.j1[i]) : mp::decode_general(p.j6[i]);
+                    uint32_t self[WG], P[WG];
+                    mp::load_words<WG>(p.spins + (size_t)is * WG, self);
+#pragma unroll
+                    for (int wi = 0; wi < WG; ++wi) P[wi] = 0;
+#pragma unroll
+                    for (int qq = 0; qq < 6; ++qq) {
+                        uint32_t n[WG];
+                        mp::load_words<WG>(p.spins + (size_t)nb[qq] * WG, n);
+#pragma unroll
+                        for (int wi = 0; wi < WG; ++wi) P[wi] += mp::bond_term(n[wi], cp, qq);
+                    }
+                    if (mp::update_words<false, WG, 0, true>(self, P, vmask, cp.msum, (uint32_t)i,
+                                                             (uint32_t)sw, (uint32_t)p.w0, key, s_thr,
+                                                             acc))
+                        mp::store_words<WG>(p.spins + (size_t)is * WG, self);
+                }
+                __syncthreads();
+            }
+        }
+    }
+}
+
+// Initial spins of every plane (grid.y = plane).
+template <int WG>
+__global__ void planes_init_kernel(const Plane* __restrict__ planes)
+{
+    const Plane p = planes[blockIdx.y];
+    const int N = p.L * p.L * p.L;
+    for (int is = blockIdx.x * blockDim.x + threadIdx.x; is < N; is += gridDim.x * blockDim.x) {
+        const uint32_t i = (uint32_t)logical_of(p.L, is);
+        uint32_t words[WG];
+#pragma unroll
+        for (int wi = 0; wi < WG; ++wi) {
+            const Philox4 r = philox4x32_10(i, kSweepInit, (uint32_t)(p.w0 + wi), kDomainMetropolis, p.k0, p.k1);
+            uint32_t word = 0;
+#pragma unroll
+            for (int b = 0; b < 4; ++b) {
+                const bool down = (4 * (p.w0 + wi) + b < p.R) && (r.v[b] >> 31);
+                word |= (down ? 0xFFu : 0x01u) << (8 * b);
+            }
+            words[wi] = word;
+        }
+        mp::store_words<WG>(p.spins + (size_t)is * WG, words);
+    }
+}
+
+// Energies (Eq. 1) of every replica of every plane: E_out[plane][4*WG] (grid.y = plane).
+template <int WG>
+__global__ void planes_energy_kernel(const Plane* __restrict__ planes, unsigned long long* __restrict__ E_out)
+{
+    __shared__ long long s_E[4 * WG];
+    const Plane p = planes[blockIdx.y];
+    const int L = p.L, N = L * L * L;
+    if (threadIdx.x < 4 * WG) s_E[threadIdx.x] = 0;
+    __syncthreads();
+    long long acc[4 * WG];
+#pragma unroll
+    for (int q = 0; q < 4 * WG; ++q) acc[q] = 0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
+        const int x = i % L, y = (i / L) % L, z = i / (L * L);
+        const uint2 r = p.j6[i];
+        const int J[3] = {(int)(int8_t)(r.x & 0xFF), (int)(int8_t)((r.x >> 16) & 0xFF),
+                          (int)(int8_t)(r.y & 0xFF)};
+        const int64_t fwd[3] = {storage_of(L, (x + 1 == L ? 0 : x + 1) + L * (y + L * z)),
+                                storage_of(L, x + L * ((y + 1 == L ? 0 : y + 1) + L * z)),
+                                storage_of(L, x + L * (y + L * (z + 1 == L ? 0 : z + 1)))};
+        uint32_t me[WG];
+        mp::load_words<WG>(p.spins + (size_t)storage_of(L, i) * WG, me);
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            uint32_t nb[WG];
+            mp::load_words<WG>(p.spins + (size_t)fwd[d] * WG, nb);
+#pragma unroll
+            for (int wi = 0; wi < WG; ++wi)
+#pragma unroll
+                for (int b = 0; b < 4; ++b)
+                    acc[4 * wi + b] += J[d] * (int)(int8_t)((me[wi] >> (8 * b)) & 0xFF) *
+                                       (int)(int8_t)((nb[wi] >> (8 * b)) & 0xFF);
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < 4 * WG; ++q)
+        if (acc[q]) atomicAdd((unsigned long long*)&s_E[q], (unsigned long long)acc[q]);
+    __syncthreads();
+    if (threadIdx.x < 4 * WG && s_E[threadIdx.x])
+        atomicAdd(&E_out[(size_t)blockIdx.y * 4 * WG + threadIdx.x], (unsigned long long)s_E[threadIdx.x]);
+}
+
+// Spins of one plane into the instance's [R][N] output (grid.y = plane).
+template <int WG>
+__global__ void planes_unpack_kernel(const Plane* __restrict__ planes, int8_t* const* __restrict__ outs)
+{
+    const Plane p = planes[blockIdx.y];
+    int8_t* out = outs[p.out];
+    if (!out) return;
+    const int L = p.L;
+    const int64_t N = (int64_t)L * L * L;
+    const int8_t* src = reinterpret_cast<const int8_t*>(p.spins);
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * 4 * WG;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        const int rb = (int)(q / N);            // replica within the plane
+        const int64_t i = q - (int64_t)rb * N;  // logical site
+        const int r = 4 * p.w0 + rb;
+        if (r < p.R) out[(int64_t)r * N + i] = src[storage_of(L, i) * 4 * WG + rb];
+    }
+}
+
+int check(const char* what)
+{
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        set_error("%s: %s", what, cudaGetErrorString(e));
+        return SG_ECUDA;
+    }
+    return SG_OK;
+}
+
+template <int WG>
+int32_t launch_planes(const Plane* d_planes, const int* d_order, int n, unsigned* d_next, bool unit,
+                      int blocks, cudaStream_t st)
+{
+    if (unit)
+        sa_planes_kernel<WG, true><<<blocks, 256, 0, st>>>(d_planes, d_order, n, d_next);
+    else
+        sa_planes_kernel<WG, false><<<blocks, 256, 0, st>>>(d_planes, d_order, n, d_next);
+    return check("sa_planes_kernel");
+}
+
+}  // namespace
+
+int32_t launch_sa_planes(int WG, const Plane* d_planes, const int* d_order, int n, unsigned* d_next,
+                         bool unit, int blocks, cudaStream_t st)
+{
+    switch (WG) {
+    case 4: return launch_planes<4>(d_planes, d_order, n, d_next, unit, blocks, st);
+    case 2: return launch_planes<2>(d_planes, d_order, n, d_next, unit, blocks, st);
+    default: return launch_planes<1>(d_planes, d_order, n, d_next, unit, blocks, st);
+    }
+}
+
+int32_t launch_planes_init(int WG, const Plane* d_planes, int n, cudaStream_t st)
+{
+    dim3 grid(64, n);
+    if (WG == 4) planes_init_kernel<4><<<grid, 256, 0, st>>>(d_planes);
+    else if (WG == 2) planes_init_kernel<2><<<grid, 256, 0, st>>>(d_planes);
+    else planes_init_kernel<1><<<grid, 256, 0, st>>>(d_planes);
+    return check("planes_init_kernel");
+}
+
+int32_t launch_planes_energy(int WG, const Plane* d_planes, int n, unsigned long long* E_out, cudaStream_t st)
+{
+    dim3 grid(64, n);
+    if (WG == 4) planes_energy_kernel<4><<<grid, 256, 0, st>>>(d_planes, E_out);
+    else if (WG == 2) planes_energy_kernel<2><<<grid, 256, 0, st>>>(d_planes, E_out);
+    else planes_energy_kernel<1><<<grid, 256, 0, st>>>(d_planes, E_out);
+    return check("planes_energy_kernel");
+}
+
+int32_t launch_planes_unpack(int WG, const Plane* d_planes, int n, int8_t* const* outs, cudaStream_t st)
+{
+    dim3 grid(64, n);
+    if (WG == 4) planes_unpack_kernel<4><<<grid, 256, 0, st>>>(d_planes, outs);
+    else if (WG == 2) planes_unpack_kernel<2><<<grid, 256, 0, st>>>(d_planes, outs);
+    else planes_unpack_kernel<1><<<grid, 256, 0, st>>>(d_planes, outs);
+    return check("planes_unpack_kernel");
+}
+
+// ------------------------------------------------------------------ host side
+
+namespace {
+
+uint32_t magic(int d) { return (uint32_t)((0x100000000ull + (uint64_t)d - 1) / (uint64_t)d); }
+
+// Stream-ordered device buffer (freed at scope exit).
+struct Buf {
+    void* p = nullptr;
+    cudaStream_t st = nullptr;
+    ~Buf()
+    {
+        if (p) cudaFreeAsync(p, st);
+    }
+    int32_t alloc(size_t bytes, cudaStream_t s)
+    {
+        st = s;
+        if (cudaMallocAsync(&p, bytes ? bytes : 16, s) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            set_error("device allocation of %zu bytes failed", bytes);
+            return SG_ENOMEM;
+        }
+        return SG_OK;
+    }
+};
+
+#define SG_B(expr)                      \
+    do {                                \
+        int32_t _rc = (expr);           \
+        if (_rc != SG_OK) return _rc;   \
+    } while (0)
+
+// ---- autotuner cache: key -> words per plane, kept in a small JSON object file ----
+std::mutex g_tune_mu;
+std::map<std::string, int> g_tune_mem;
+bool g_tune_loaded = false;
+
+std::string tune_path()
+{
+    const char* e = getenv("SG_AUTOTUNE_CACHE");
+    if (e && *e) return e;
+    const char* home = getenv("HOME");
+    return std::string(home ? home : "/tmp") + "/.cache/sg_autotune.json";
+}
+
+void tune_load()
+{
+    if (g_tune_loaded) return;
+    g_tune_loaded = true;
+    std::ifstream f(tune_path());
+    if (!f) return;
+    std::stringstream ss;
+    ss << f.rdbuf();
+    const std::string t = ss.str();
+    // flat object {"key": value, ...} written by tune_store
+    size_t pos = 0;
+    while ((pos = t.find('"', pos)) != std::string::npos) {
+        const size_t end = t.find('"', pos + 1);
+        if (end == std::string::npos) break;
+        const std::string key = t.substr(pos + 1, end - pos - 1);
+        const size_t colon = t.find(':', end);
+        if (colon == std::string::npos) break;
+        g_tune_mem[key] = atoi(t.c_str() + colon + 1);
+        pos = t.find_first_of(",}", colon);
+        if (pos == std::string::npos) break;
+    }
+}
+
+void tune_store()
+{
+    const std::string path = tune_path();
+    const size_t slash = path.rfind('/');
+    if (slash != std::string::npos) {
+        const std::string dir = path.substr(0, slash);
+        std::string cmd = "mkdir -p '" + dir + "' 2>/dev/null";
+        if (system(cmd.c_str()) != 0) return;
+    }
+    std::ofstream f(path);
+    if (!f) return;
+    f << "{";
+    bool first = true;
+    for (auto& kv : g_tune_mem) {
+        f << (first ? "" : ",") << "\n \"" << kv.first << "\": " << kv.second;
+        first = false;
+    }
+    f << "\n}\n";
+}
+
+}  // namespace
+
+// Runs the members of a batch (any sizes) through the persistent plane kernel.
+int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const* insts,
+                      const sg_sa_params* ps, sg_sa_result* outs, cudaStream_t st, bool* used_graph,
+                      int* chosen_wg)
+{
+    const int I = (int)members.size();
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+
+    // words per plane: a common divisor of every instance's word count
+    int wg_max = 4;
+    for (int a = 0; a < I; ++a) {
+        const int Wn = (ps[members[a]].replicas + 3) / 4;
+        while (Wn % wg_max) wg_max >>= 1;
+    }
+
+    // schedules (one threshold table per distinct schedule)
+    std::map<std::tuple<int, double, double, int>, size_t> sched_off;
+    std::vector<uint32_t> thr;
+    std::vector<size_t> inst_thr(I);
+    for (int a = 0; a < I; ++a) {
+        const sg_sa_params& p = ps[members[a]];
+        auto key = std::make_tuple(p.sweeps, p.beta0, p.beta1, p.schedule);
+        auto it = sched_off.find(key);
+        if (it == sched_off.end()) {
+            const size_t off = thr.size();
+            std::vector<double> beta((size_t)std::max(p.sweeps, 1));
+            beta_schedule(p.sweeps, p.beta0, p.beta1, p.schedule == SG_SCHEDULE_GEOMETRIC, beta.data());
+            thr.resize(off + (size_t)std::max(p.sweeps, 1) * kThrRow);
+            for (int sw = 0; sw < p.sweeps; ++sw) metropolis_row(beta[sw], &thr[off + (size_t)sw * kThrRow]);
+            it = sched_off.emplace(key, off).first;
+        }
+        inst_thr[a] = it->second;
+    }
+    bool unit = true;
+    for (int a = 0; a < I; ++a) unit &= insts[members[a]]->unit_couplings;
+
+    std::vector<const uint2*> j6(I);
+    std::vector<const uint8_t*> j1(I);
+    for (int a = 0; a < I; ++a)
+        SG_B(instance_device_j6(const_cast<sg_instance*>(insts[members[a]]), st, &j6[a], &j1[a]));
+
+    Buf d_thr;
+    SG_B(d_thr.alloc(sizeof(uint32_t) * std::max<size_t>(thr.size(), 1), st));
+    SG_TRY_CUDA(cudaMemcpyAsync(d_thr.p, thr.data(), sizeof(uint32_t) * thr.size(), cudaMemcpyHostToDevice, st));
+
+    // planes for a given words-per-plane choice; spins laid out plane after plane
+    auto make_planes = [&](int WG, uint32_t* spins_base, std::vector<Plane>* planes,
+                           std::vector<double>* work, size_t* words_total) {
+        planes->clear();
+        work->clear();
+        size_t wo = 0;
+        for (int a = 0; a < I; ++a) {
+            const sg_instance* in = insts[members[a]];
+            const sg_sa_params& p = ps[members[a]];
+            const int Wn = (p.replicas + 3) / 4;
+            for (int w0 = 0; w0 < Wn; w0 += WG) {
+                Plane pl{};
+                pl.spins = spins_base ? spins_base + wo : nullptr;
+                pl.j1 = j1[a];
+                pl.j6 = j6[a];
+                pl.thr = static_cast<const uint32_t*>(d_thr.p) + inst_thr[a];
+                const RunKeys k{(uint32_t)p.seed, (uint32_t)(p.seed >> 32) ^ p.instance_id};
+                pl.k0 = k.k0;
+                pl.k1 = k.k1;
+                pl.L = in->L;
+                pl.S = p.sweeps;
+                pl.w0 = w0;
+                pl.R = p.replicas;
+                pl.Lmagic = magic(in->L);
+                pl.Hmagic = magic(in->L / 2);
+                pl.out = a;
+                planes->push_back(pl);
+                work->push_back((double)in->N * 4 * WG * std::max(p.sweeps, 1));
+                wo += (size_t)in->N * WG;
+            }
+        }
+        *words_total = wo;
+    };
+    auto lpt_order = [](const std::vector<double>& work) {
+        std::vector<int> order(work.size());
+        for (size_t q = 0; q < order.size(); ++q) order[q] = (int)q;
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
+        return order;
+    };
+    auto blocks_for = [&](int WG) {
+        int per_sm = 0;
+        cudaError_t e;
+        if (WG == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unit ? sa_planes_kernel<4, true> : sa_planes_kernel<4, false>, 256, 0);
+        else if (WG == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unit ? sa_planes_kernel<2, true> : sa_planes_kernel<2, false>, 256, 0);
+        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unit ? sa_planes_kernel<1, true> : sa_planes_kernel<1, false>, 256, 0);
+        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
+        return sms * per_sm;
+    };
+
+    // ---- autotune the words per plane: measured throughput on the batch itself, then the
+    // makespan bound max(total / rate, largest plane / per-block rate) ----
+    std::vector<int> cands;
+    for (int wg = wg_max; wg >= 1; wg >>= 1) cands.push_back(wg);
+    std::string key;
+    {
+        std::map<std::tuple<int, int, int>, int> mix;
+        for (int a = 0; a < I; ++a)
+            mix[std::make_tuple(insts[members[a]]->L, ps[members[a]].replicas, ps[members[a]].sweeps)]++;
+        cudaDeviceProp prop;
+        cudaGetDeviceProperties(&prop, dev);
+        std::ostringstream ks;
+        ks << prop.name << "/" << sms << "/" << (unit ? "u" : "g");
+        for (auto& m : mix)
+            ks << "/" << std::get<0>(m.first) << "x" << std::get<1>(m.first) << "x" << std::get<2>(m.first) << "x" << m.second;
+        key = ks.str();
+        for (auto& c : key)
+            if (c == '"' || c == '\\') c = '_';
+    }
+    int WG = cands.front();
+    const char* force = getenv("SG_BATCH_WG");
+    if (force && atoi(force) >= 1 && wg_max % atoi(force) == 0) {
+        WG = atoi(force);
+    } else if (cands.size() > 1) {
+        std::lock_guard<std::mutex> lock(g_tune_mu);
+        tune_load();
+        auto hit = g_tune_mem.find(key);
+        if (hit != g_tune_mem.end() && wg_max % hit->second == 0) {
+            WG = hit->second;
+        } else {
+            double best = 1e300;
+            for (int wg : cands) {
+                std::vector<Plane> planes;
+                std::vector<double> work;
+                size_t words = 0;
+                make_planes(wg, nullptr, &planes, &work, &words);
+                Buf d_sp, d_pl, d_ord, d_next;
+                SG_B(d_sp.alloc(words * 4, st));
+                make_planes(wg, static_cast<uint32_t*>(d_sp.p), &planes, &work, &words);
+                // trial: a few sweeps of every plane
+                const int trial_sweeps = 2;
+                double trial_work = 0;
+                for (auto& pl : planes) {
+                    pl.S = std::min(pl.S, trial_sweeps);
+                    trial_work += (double)pl.L * pl.L * pl.L * 4 * wg * pl.S;
+                }
+                const std::vector<int> order = lpt_order(work);
+                SG_B(d_pl.alloc(sizeof(Plane) * planes.size(), st));
+                SG_B(d_ord.alloc(sizeof(int) * order.size(), st));
+                SG_B(d_next.alloc(sizeof(unsigned), st));
+                SG_TRY_CUDA(cudaMemcpyAsync(d_pl.p, planes.data(), sizeof(Plane) * planes.size(), cudaMemcpyHostToDevice, st));
+                SG_TRY_CUDA(cudaMemcpyAsync(d_ord.p, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, st));
+                SG_B(launch_planes_init(wg, static_cast<Plane*>(d_pl.p), (int)planes.size(), st));
+                const int blocks = blocks_for(wg);
+                double t_best = 1e300;
+                for (int rep = 0; rep < 2; ++rep) {
+                    SG_TRY_CUDA(cudaMemsetAsync(d_next.p, 0, sizeof(unsigned), st));
+                    SG_TRY_CUDA(cudaStreamSynchronize(st));
+                    const auto t0 = std::chrono::steady_clock::now();
+                    SG_B(launch_sa_planes(wg, static_cast<Plane*>(d_pl.p), static_cast<int*>(d_ord.p),
+                                          (int)planes.size(), static_cast<unsigned*>(d_next.p), unit, blocks, st));
+                    SG_TRY_CUDA(cudaStreamSynchronize(st));
+                    t_best = std::min(t_best, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
+                }
+                const double rate = trial_work / t_best;  // attempts per second, whole GPU
+                double total = 0, biggest = 0;
+                for (double w : work) {
+                    total += w;
+                    biggest = std::max(biggest, w);
+                }
+                const double est = std::max(total / rate, biggest / (rate / std::min<double>(blocks, work.size())));
+                if (est < best) {
+                    best = est;
+                    WG = wg;
+                }
+            }
+            g_tune_mem[key] = WG;
+            tune_store();
+        }
+    }
+    if (chosen_wg) *chosen_wg = WG;
+
+    // ---- the run ----
+    std::vector<Plane> planes;
+    std::vector<double> work;
+    size_t words = 0;
+    make_planes(WG, nullptr, &planes, &work, &words);
+    Buf d_sp, d_pl, d_ord, d_next, d_E, d_outs, d_stage;
+    SG_B(d_sp.alloc(words * 4, st));
+    make_planes(WG, static_cast<uint32_t*>(d_sp.p), &planes, &work, &words);
+    const std::vector<int> order = lpt_order(work);
+    const int n = (int)planes.size();
+    SG_B(d_pl.alloc(sizeof(Plane) * n, st));
+    SG_B(d_ord.alloc(sizeof(int) * n, st));
+    SG_B(d_next.alloc(sizeof(unsigned), st));
+    SG_B(d_E.alloc(sizeof(unsigned long long) * (size_t)n * 4 * WG, st));
+    // spin outputs: device targets directly, host targets through one staging area
+    std::vector<int8_t*> outp(I, nullptr);
+    size_t stage_bytes = 0;
+    std::vector<size_t> stage_off(I, 0);
+    for (int a = 0; a < I; ++a) {
+        const sg_sa_result& o = outs[members[a]];
+        if (o.spins && o.spins_mem == SG_MEM_HOST) {
+            stage_off[a] = stage_bytes;
+            stage_bytes += (size_t)ps[members[a]].replicas * insts[members[a]]->N;
+        }
+    }
+    if (stage_bytes) SG_B(d_stage.alloc(stage_bytes, st));
+    for (int a = 0; a < I; ++a) {
+        const sg_sa_result& o = outs[members[a]];
+        if (!o.spins) continue;
+        outp[a] = o.spins_mem == SG_MEM_DEVICE ? o.spins : static_cast<int8_t*>(d_stage.p) + stage_off[a];
+    }
+    SG_B(d_outs.alloc(sizeof(int8_t*) * I, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(d_pl.p, planes.data(), sizeof(Plane) * n, cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(d_ord.p, order.data(), sizeof(int) * n, cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(d_outs.p, outp.data(), sizeof(int8_t*) * I, cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaStreamSynchronize(st));  // host arrays above are stack/heap temporaries
+
+    const int blocks = blocks_for(WG);
+    auto device_work = [&](cudaStream_t s) -> int32_t {
+        SG_TRY_CUDA(cudaMemsetAsync(d_next.p, 0, sizeof(unsigned), s));
+        SG_TRY_CUDA(cudaMemsetAsync(d_E.p, 0, sizeof(unsigned long long) * (size_t)n * 4 * WG, s));
+        SG_B(launch_planes_init(WG, static_cast<Plane*>(d_pl.p), n, s));
+        SG_B(launch_sa_planes(WG, static_cast<Plane*>(d_pl.p), static_cast<int*>(d_ord.p), n,
+                              static_cast<unsigned*>(d_next.p), unit, blocks, s));
+        SG_B(launch_planes_energy(WG, static_cast<Plane*>(d_pl.p), n, static_cast<unsigned long long*>(d_E.p), s));
+        SG_B(launch_planes_unpack(WG, static_cast<Plane*>(d_pl.p), n, static_cast<int8_t* const*>(d_outs.p), s));
+        return SG_OK;
+    };
+    // the device part of the run is one CUDA graph (knob SG_BATCH_GRAPH=0 launches directly)
+    const char* g = getenv("SG_BATCH_GRAPH");
+    const bool graph = !(g && atoi(g) == 0);
+    if (used_graph) *used_graph = graph;
+    if (graph) {
+        cudaStream_t cs = nullptr;
+        SG_TRY_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+        cudaGraph_t gr = nullptr;
+        cudaGraphExec_t ge = nullptr;
+        int32_t rc = SG_OK;
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) rc = SG_ECUDA;
+        if (rc == SG_OK) rc = device_work(cs);
+        cudaError_t e = cudaStreamEndCapture(cs, &gr);
+        if (rc == SG_OK && e != cudaSuccess) rc = SG_ECUDA;
+        if (rc == SG_OK && cudaGraphInstantiate(&ge, gr, 0) != cudaSuccess) rc = SG_ECUDA;
+        if (rc == SG_OK && cudaGraphLaunch(ge, st) != cudaSuccess) rc = SG_ECUDA;
+        if (ge) cudaGraphExecDestroy(ge);
+        if (gr) cudaGraphDestroy(gr);
+        cudaStreamDestroy(cs);
+        if (rc != SG_OK) {
+            cudaGetLastError();
+            if (!*sg_last_error_string()) set_error("graph capture of the batch failed");
+            return rc;
+        }
+    } else {
+        SG_B(device_work(st));
+    }
+
+    std::vector<unsigned long long> E((size_t)n * 4 * WG);
+    SG_TRY_CUDA(cudaMemcpyAsync(E.data(), d_E.p, sizeof(unsigned long long) * E.size(), cudaMemcpyDeviceToHost, st));
+    for (int a = 0; a < I; ++a) {
+        const sg_sa_result& o = outs[members[a]];
+        if (o.spins && o.spins_mem == SG_MEM_HOST)
+            SG_TRY_CUDA(cudaMemcpyAsync(o.spins, static_cast<int8_t*>(d_stage.p) + stage_off[a],
+                                        (size_t)ps[members[a]].replicas * insts[members[a]]->N,
+                                        cudaMemcpyDeviceToHost, st));
+    }
+    SG_TRY_CUDA(cudaStreamSynchronize(st));
+    for (int q = 0; q < n; ++q) {
+        const Plane& pl = planes[q];
+        const int a = pl.out;
+        const sg_sa_result& o = outs[members[a]];
+        const int64_t egs = insts[members[a]]->e_gs;
+        for (int rb = 0; rb < 4 * WG; ++rb) {
+            const int r = 4 * pl.w0 + rb;
+            if (r >= pl.R) continue;
+            o.E[r] = (int64_t)(long long)E[(size_t)q * 4 * WG + rb];
+            if (o.eps) o.eps[r] = (double)(o.E[r] - egs) / (double)(-egs);
+        }
+    }
+    return SG_OK;
+}
+
+}  // namespace sg

@@ -104,6 +104,18 @@ SG_HDI int64_t logical_of(int L, int64_t storage)
     return row * L + (pos < H ? 2 * pos : 2 * (pos - H) + 1);
 }
 
+// ---- batched annealing of uneven instances (batch.cu) ----
+// Runs members of a batch through one persistent plane kernel (device part captured as
+// one CUDA graph unless disabled); reports whether a graph was used and the words per
+// plane the autotuner chose.
+int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const* insts,
+                      const sg_sa_params* ps, sg_sa_result* outs, cudaStream_t st, bool* used_graph,
+                      int* chosen_wg);
+
+// ---- launch statistics shared by all run paths (api.cu) ----
+bool stats_timing();
+void stats_add(int kind, int64_t launches, int64_t units, double device_ms);
+
 // ---- kernels (kernels.cu) ----
 struct RunKeys {
     uint32_t k0, k1;

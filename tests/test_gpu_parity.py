@@ -220,3 +220,72 @@ def test_sa_kernel_shapes(sg, monkeypatch, kernel, L, R):
     inst = sg.Instance.create(L, 40 + L)
     J3, _, egs = inst.get()
     _sa_compare(sg, inst, J3, egs, R, 12, 0.1, 3.0, seed=6, reps=[0, 5, R - 1])
+
+
+# --------------------------------------------------------------------------- uneven batches
+
+def _uneven_batch(sg, seed=0):
+    shapes = [(4, 8, 30), (6, 64, 12), (8, 16, 25), (12, 8, 7), (6, 8, 40), (16, 12, 5), (10, 4, 9)]
+    insts, params = [], []
+    for k, (L, R, S) in enumerate(shapes):
+        insts.append(sg.Instance.create(L, 3 * 2 ** 32 + 100 * seed + k))
+        params.append(dict(replicas=R, sweeps=S, beta0=0.1, beta1=3.0,
+                           schedule="geometric" if k % 2 else "linear", seed=seed + 5, instance_id=k))
+    return insts, params
+
+
+def test_uneven_batch_equals_separate_runs_and_oracle(sg, monkeypatch, tmp_path):
+    """Instances of several sizes in one persistent launch: byte-identical to separate
+    runs; two instances also against the oracle."""
+    monkeypatch.setenv("SG_AUTOTUNE_CACHE", str(tmp_path / "tune.json"))
+    insts, params = _uneven_batch(sg)
+    batch = sg.sa_run_batch(insts, params, spins="host")
+    for inst, p, b in zip(insts, params, batch):
+        single = sg.sa_run(inst, spins="host", **p)
+        assert np.array_equal(single["spins"], b["spins"])
+        assert np.array_equal(single["E"], b["E"])
+        assert np.array_equal(single["eps"], b["eps"])
+    for k in (1, 3):
+        J3, _, egs = insts[k].get()
+        p = params[k]
+        reps = [0, p["replicas"] - 1]
+        ospins, oE = o.sa_run(insts[k].L, J3, p["seed"], p["instance_id"], p["sweeps"], p["beta0"],
+                              p["beta1"], p["schedule"] == "geometric", reps=reps)
+        assert np.array_equal(batch[k]["spins"][reps], ospins)
+        assert np.array_equal(batch[k]["E"][reps], oE)
+
+
+def test_batch_autotuner_records_and_reuses_choice(sg, monkeypatch, tmp_path):
+    """With several plane widths possible the autotuner measures them, stores its choice,
+    and a second run with the same mix reuses it; results do not depend on it."""
+    cache = tmp_path / "tune.json"
+    monkeypatch.setenv("SG_AUTOTUNE_CACHE", str(cache))
+    insts = [sg.Instance.create(L, 500 + L) for L in (8, 12, 16)]
+    params = [dict(replicas=32, sweeps=10, beta0=0.1, beta1=3.0, schedule="linear", seed=1,
+                   instance_id=k) for k in range(3)]
+    first = sg.sa_run_batch(insts, params, spins="host")
+    assert cache.exists()
+    text = cache.read_text()
+    assert "8x32x10x1" in text and "16x32x10x1" in text
+    second = sg.sa_run_batch(insts, params, spins="host")
+    assert cache.read_text() == text
+    for a, b in zip(first, second):
+        assert np.array_equal(a["spins"], b["spins"])
+
+
+@pytest.mark.parametrize("wg,graph", [("1", "1"), ("2", "0"), ("4", "1")])
+def test_uneven_batch_any_plane_width(sg, monkeypatch, wg, graph):
+    """Every words-per-plane choice and graph capture on or off give the same bytes
+    (R is a multiple of 16 so all widths apply)."""
+    insts = [sg.Instance.create(L, 77 + L) for L in (4, 8, 6)]
+    params = [dict(replicas=16, sweeps=S, beta0=0.2, beta1=2.5, schedule="linear", seed=3,
+                   instance_id=k) for k, S in enumerate((20, 9, 14))]
+    monkeypatch.setenv("SG_BATCH_PLANES", "0")
+    ref = sg.sa_run_batch(insts, params, spins="host")
+    monkeypatch.setenv("SG_BATCH_PLANES", "1")
+    monkeypatch.setenv("SG_BATCH_WG", wg)
+    monkeypatch.setenv("SG_BATCH_GRAPH", graph)
+    got = sg.sa_run_batch(insts, params, spins="device")
+    for a, b in zip(ref, got):
+        assert np.array_equal(a["spins"], b["spins"].cpu().numpy())
+        assert np.array_equal(a["E"], b["E"])
