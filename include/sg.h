@@ -55,6 +55,7 @@ extern "C" {
 #define SG_ETIMEOUT (-4)  /* a bounded device-side wait gave up */
 #define SG_EBUSY (-5)     /* a queue or slot pool is full */
 #define SG_EINTERNAL (-6) /* a self-check failed (e.g. incremental energy != recomputed) */
+#define SG_ECANCELED (-7) /* the request was cancelled */
 #define SG_PENDING 1      /* sg_poll: the request has not finished */
 
 #define SG_MEM_HOST 0
@@ -182,6 +183,81 @@ int32_t sg_pt_run_batch(const sg_instance* const* insts, const sg_pt_params* ps,
  * E_out is host.  Errors: SG_EINVAL (also for a spin not in {-1,+1}), SG_ECUDA. */
 int32_t sg_energy(const sg_instance* inst, const int8_t* spins, int32_t n_configs,
                   int32_t mem_kind, int64_t* E_out, void* stream);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: solve requests to a target gap, continuously batched.            */
+/* ------------------------------------------------------------------------ */
+/* A server owns one worker thread and the device it was created on.  Requests (a
+ * fresh tile-planted instance plus SA or PT parameters, Sec. II and App. D) wait in a
+ * FIFO queue and are admitted while their device memory fits the budget and a slot
+ * is free; admitted requests stay resident and advance together, chunk_sweeps sweeps
+ * per round: all SA requests in one persistent launch, each PT request as a captured
+ * CUDA graph on its own stream, so their work overlaps on the GPU.  A request is done
+ * at the first round boundary where its lowest energy E satisfies
+ * E <= E_gs + floor(eps_target * |E_gs|) (time to target, TT-eps, Eq. 2), or at the
+ * first round boundary at or past sweep_cap sweeps (censored; SA rounds also end
+ * exactly at the cap and at the end of every restart, PT rounds are whole chunks).
+ * "Lowest energy" is the minimum over replicas at round boundaries for SA and the
+ * running minimum PT keeps after every exchange (as sg_pt_run reports it).  Results do not depend on what else is running:
+ * every draw is named by the request's own seed, sites, sweeps and replicas, and the
+ * checks happen at fixed sweep counts.  SA requests anneal in restarts of
+ * sweeps_per_restart sweeps; restart k is the run sg_sa_run gives with instance_id = k. */
+
+#define SG_REQ_SA 0
+#define SG_REQ_PT 1
+
+typedef struct sg_server sg_server;
+
+typedef struct sg_server_config {
+    uint64_t hbm_budget_bytes;  /* device memory the server may hold for admitted requests */
+    int32_t max_active;         /* requests resident at once (>= 1) */
+    int32_t chunk_sweeps;       /* sweeps per round; completion is checked between rounds */
+    int32_t queue_capacity;     /* waiting requests; beyond it sg_submit returns SG_EBUSY */
+} sg_server_config;
+
+typedef struct sg_request {
+    int32_t kind;               /* SG_REQ_SA or SG_REQ_PT */
+    sg_instance_desc instance;  /* the instance the server generates for this request */
+    int32_t width;              /* SA: replicas R; PT: temperatures K (1..256) */
+    int32_t sweeps_per_restart; /* SA: sweeps of one anneal; ignored for PT */
+    double beta0, beta1;        /* SA: schedule ends; PT: geometric ladder ends; > 0 */
+    int32_t schedule;           /* SA: SG_SCHEDULE_LINEAR or _GEOMETRIC */
+    uint64_t seed;              /* run seed */
+    double eps_target;          /* target optimality gap (>= 0) */
+    int64_t sweep_cap;          /* stop after this many sweeps (all restarts) */
+} sg_request;
+
+typedef struct sg_result {
+    int32_t status;             /* SG_OK, SG_ECANCELED, or the error that ended the request */
+    int32_t reached;            /* 1: target reached; 0: stopped at the sweep cap */
+    int64_t sweeps;             /* sweeps run when it stopped (all restarts) */
+    int64_t minE;               /* lowest energy seen */
+    int64_t e_gs;               /* planted ground-state energy */
+    double min_eps;             /* gap of minE (Eq. 2) */
+    double queue_s;             /* submit -> admitted */
+    double run_s;               /* admitted -> done */
+    double total_s;             /* submit -> done: the time to target */
+} sg_result;
+
+/* Start a server on the current CUDA device.  Errors: SG_EINVAL (bad config),
+ * SG_ECUDA, SG_ENOMEM. */
+int32_t sg_server_create(const sg_server_config* cfg, sg_server** out);
+
+/* Queue a request; *ticket identifies it.  Errors: SG_EINVAL (bad request), SG_ENOMEM
+ * (it alone needs more than the budget), SG_EBUSY (queue full). */
+int32_t sg_submit(sg_server* srv, const sg_request* req, uint64_t* ticket);
+
+/* Wait up to timeout_ms (0: just look; < 0: wait until done) for a request.  Returns
+ * SG_OK with *out filled once it is done (a ticket is reported once, then forgotten),
+ * SG_PENDING while it is not, SG_EINVAL for an unknown ticket. */
+int32_t sg_poll(sg_server* srv, uint64_t ticket, int32_t timeout_ms, sg_result* out);
+
+/* Cancel a request: a waiting one leaves the queue, a running one stops at the next
+ * round boundary; its result has status SG_ECANCELED.  SG_EINVAL for an unknown ticket. */
+int32_t sg_cancel(sg_server* srv, uint64_t ticket);
+
+/* Stop the worker (running requests are cancelled) and release everything. */
+int32_t sg_server_destroy(sg_server* srv);
 
 /* ------------------------------------------------------------------------ */
 /* Energy without device allocation (no counterpart in the paper).           */

@@ -483,6 +483,7 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     xa.xtail = d_xtail.as<uint32_t>();
     xa.Rp = Rp;
     xa.K = K;
+    xa.sweep_base = nullptr;
     unsigned* done = d_done.as<unsigned>();
     for (int s = 0; s < S; ++s) {
         bool fused = false;

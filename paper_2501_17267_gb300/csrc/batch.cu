@@ -32,17 +32,6 @@
 
 namespace sg {
 
-struct Plane {
-    uint32_t* spins;        // [N][WG] words, storage order
-    const uint8_t* j1;      // sign bits (unit couplings) or nullptr
-    const uint2* j6;        // six-coupling records
-    const uint32_t* thr;    // [S][kThrRow] thresholds of the plane's schedule
-    uint32_t k0, k1;        // Philox key of the run
-    int L, S, w0, R;        // side, sweeps, first word (of the instance) in the plane, replicas
-    uint32_t Lmagic, Hmagic;  // ceil(2^32 / L), ceil(2^32 / (L/2))
-    int out;                // index of the instance in the batch
-};
-
 namespace {
 
 __device__ __forceinline__ int div_magic(int v, uint32_t m) { return (int)__umulhi((uint32_t)v, m); }
@@ -75,7 +64,7 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
             vmask[wi] = m;
             acc[wi] = 0;
         }
-        for (int sw = 0; sw < p.S; ++sw) {
+        for (int sw = p.s_begin; sw < p.s_end; ++sw) {
             if (tid < kThrRow) s_thr[tid] = p.thr[(size_t)sw * kThrRow + tid];
             __syncthreads();
             for (int colour = 0; colour < 2; ++colour) {
@@ -232,6 +221,25 @@ int32_t launch_sa_planes(int WG, const Plane* d_planes, const int* d_order, int 
     case 2: return launch_planes<2>(d_planes, d_order, n, d_next, unit, blocks, st);
     default: return launch_planes<1>(d_planes, d_order, n, d_next, unit, blocks, st);
     }
+}
+
+int planes_blocks(int WG, bool unit)
+{
+    int dev = 0, sms = 148, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e;
+    if (WG == 4)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unit ? sa_planes_kernel<4, true> : sa_planes_kernel<4, false>, 256, 0);
+    else if (WG == 2)
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unit ? sa_planes_kernel<2, true> : sa_planes_kernel<2, false>, 256, 0);
+    else
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unit ? sa_planes_kernel<1, true> : sa_planes_kernel<1, false>, 256, 0);
+    if (e != cudaSuccess || per_sm < 1) {
+        cudaGetLastError();
+        per_sm = 1;
+    }
+    return sms * per_sm;
 }
 
 int32_t launch_planes_init(int WG, const Plane* d_planes, int n, cudaStream_t st)
@@ -420,6 +428,8 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
                 pl.k1 = k.k1;
                 pl.L = in->L;
                 pl.S = p.sweeps;
+                pl.s_begin = 0;
+                pl.s_end = p.sweeps;
                 pl.w0 = w0;
                 pl.R = p.replicas;
                 pl.Lmagic = magic(in->L);
@@ -438,15 +448,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
         return order;
     };
-    auto blocks_for = [&](int WG) {
-        int per_sm = 0;
-        cudaError_t e;
-        if (WG == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unit ? sa_planes_kernel<4, true> : sa_planes_kernel<4, false>, 256, 0);
-        else if (WG == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unit ? sa_planes_kernel<2, true> : sa_planes_kernel<2, false>, 256, 0);
-        else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unit ? sa_planes_kernel<1, true> : sa_planes_kernel<1, false>, 256, 0);
-        if (e != cudaSuccess || per_sm < 1) per_sm = 1;
-        return sms * per_sm;
-    };
+    auto blocks_for = [&](int WG) { return planes_blocks(WG, unit); };
 
     // ---- autotune the words per plane: measured throughput on the batch itself, then the
     // makespan bound max(total / rate, largest plane / per-block rate) ----
@@ -491,8 +493,8 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
                 const int trial_sweeps = 2;
                 double trial_work = 0;
                 for (auto& pl : planes) {
-                    pl.S = std::min(pl.S, trial_sweeps);
-                    trial_work += (double)pl.L * pl.L * pl.L * 4 * wg * pl.S;
+                    pl.s_end = std::min(pl.S, trial_sweeps);
+                    trial_work += (double)pl.L * pl.L * pl.L * 4 * wg * pl.s_end;
                 }
                 const std::vector<int> order = lpt_order(work);
                 SG_B(d_pl.alloc(sizeof(Plane) * planes.size(), st));

@@ -28,6 +28,7 @@ struct ExchangeArgs {
     const uint32_t* xlen;
     const uint32_t* xtail;       // threshold for d > xlen[k]
     int Rp, K;
+    const uint32_t* sweep_base;  // stand-alone kernel: if set, the sweep is *sweep_base + sweep
 };
 
 // Called by every thread of one block (tid in [0, nthreads)); s_min is shared scratch.

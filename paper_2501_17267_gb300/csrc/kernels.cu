@@ -325,7 +325,8 @@ __global__ void pt_setup_kernel(const unsigned long long* __restrict__ E64, int3
 __global__ void pt_exchange_kernel(const ExchangeArgs x, uint32_t sweep)
 {
     __shared__ int32_t s_min;
-    pt_exchange_block(x, blockIdx.x, sweep, threadIdx.x, blockDim.x, &s_min);
+    const uint32_t s = sweep + (x.sweep_base ? *x.sweep_base : 0u);
+    pt_exchange_block(x, blockIdx.x, s, threadIdx.x, blockDim.x, &s_min);
 }
 
 // ---------------------------------------------------------------- checks and layout

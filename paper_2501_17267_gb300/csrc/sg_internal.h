@@ -105,6 +105,25 @@ SG_HDI int64_t logical_of(int L, int64_t storage)
 }
 
 // ---- batched annealing of uneven instances (batch.cu) ----
+// One annealing chain slice: an instance and a group of WG consecutive replica words,
+// spins [N][WG] words in storage order.
+struct Plane {
+    uint32_t* spins;        // [N][WG] words, storage order
+    const uint8_t* j1;      // sign bits (unit couplings) or nullptr
+    const uint2* j6;        // six-coupling records
+    const uint32_t* thr;    // [S][kThrRow] thresholds of the plane's schedule
+    uint32_t k0, k1;        // Philox key of the run
+    int L, S, w0, R;        // side, sweeps, first word (of the instance) in the plane, replicas
+    int s_begin, s_end;     // sweeps run by this launch: [s_begin, s_end)
+    uint32_t Lmagic, Hmagic;  // ceil(2^32 / L), ceil(2^32 / (L/2))
+    int out;                // index of the instance in the batch
+};
+int32_t launch_sa_planes(int WG, const Plane* d_planes, const int* d_order, int n, unsigned* d_next,
+                         bool unit, int blocks, cudaStream_t st);
+int32_t launch_planes_init(int WG, const Plane* d_planes, int n, cudaStream_t st);
+int32_t launch_planes_energy(int WG, const Plane* d_planes, int n, unsigned long long* E_out,
+                             cudaStream_t st);
+int planes_blocks(int WG, bool unit);  // resident blocks of the plane kernel on this device
 // Runs members of a batch through one persistent plane kernel (device part captured as
 // one CUDA graph unless disabled); reports whether a graph was used and the words per
 // plane the autotuner chose.
@@ -154,7 +173,8 @@ int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
-                             const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st);
+                             const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st,
+                             const uint32_t* sweep_base = nullptr);
 // tile.cu: shared-memory streaming sweep (used when it supports the shape)
 bool tile_kernel_supports(int I, int L, int Wn);
 int32_t launch_sweep_tile(int8_t* spins, const uint2* const* j6_ptrs, const uint8_t* const* j1_ptrs,

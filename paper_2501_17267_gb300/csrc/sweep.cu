@@ -48,6 +48,7 @@ struct SweepArgs {
     int colour;
     ExchangeArgs x;               // PT exchange performed by the last block of each instance
     unsigned* done;               // [I] blocks finished in this launch (reset by the last one)
+    const uint32_t* sweep_base;   // if set, the sweep index is *sweep_base + sweep
 };
 
 template <bool PT, bool UNITJ, int WG, int CH, bool PAD, int MINB = 2, bool DRAW = false,
@@ -63,6 +64,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
     const int H = L >> 1;
     const int LL = L * L;
     const RunKeys key = a.keys[inst];
+    const uint32_t sweep = a.sweep + (a.sweep_base ? *a.sweep_base : 0u);
     uint32_t* __restrict__ s = a.spins + (size_t)inst * (size_t)LL * L * Wn;
     const int nthreads = blockDim.x * blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
@@ -166,7 +168,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
                 }
                 const uint32_t* thr = PT ? s_thr + 4 * w0 * kThrStride : s_thr;
                 if (mp::update_words<PT, WG, kThrStride, DRAW>(self, P, vmask[ch], cp.msum, (uint32_t)i,
-                                                         a.sweep, (uint32_t)w0, key, thr, acc[ch]))
+                                                         sweep, (uint32_t)w0, key, thr, acc[ch]))
                     mp::store_words<WG>(s + (size_t)is * Wn + w0, self);
             }
             if (PT && ++items == mp::kLaneCapacity<KMAX>) {
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
             __syncthreads();
             if (s_last) {
                 __threadfence();
-                pt_exchange_block(a.x, inst, a.sweep, tid, nthreads, &s_min);
+                pt_exchange_block(a.x, inst, sweep, tid, nthreads, &s_min);
                 if (tid == 0) a.done[inst] = 0;
             }
         }
@@ -366,7 +368,8 @@ int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
-                             const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st)
+                             const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st,
+                             const uint32_t* sweep_base)
 {
     SweepArgs a{};
     a.spins = reinterpret_cast<uint32_t*>(spins);
@@ -383,6 +386,7 @@ int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
     a.colour = colour;
     if (xch) a.x = *xch;
     a.done = done;
+    a.sweep_base = sweep_base;
     return launch_rows<true>(a, I, unit_j, xch != nullptr, fused, st);
 }
 

@@ -17,7 +17,9 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libsg.so")
 
 SG_OK, SG_EINVAL, SG_ENOMEM, SG_ECUDA, SG_ETIMEOUT, SG_EBUSY, SG_EINTERNAL = 0, -1, -2, -3, -4, -5, -6
+SG_ECANCELED = -7
 SG_PENDING = 1
+SG_REQ_SA, SG_REQ_PT = 0, 1
 SG_MEM_HOST, SG_MEM_DEVICE = 0, 1
 SG_SCHEDULE_LINEAR, SG_SCHEDULE_GEOMETRIC = 0, 1
 SG_JMAX = 2
@@ -67,6 +69,24 @@ class KernelStats(ctypes.Structure):
                 ("units", ctypes.c_int64 * 5)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("hbm_budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_int32),
+                ("chunk_sweeps", ctypes.c_int32), ("queue_capacity", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("instance", InstanceDesc), ("width", ctypes.c_int32),
+                ("sweeps_per_restart", ctypes.c_int32), ("beta0", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("schedule", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("eps_target", ctypes.c_double), ("sweep_cap", ctypes.c_int64)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int32), ("reached", ctypes.c_int32), ("sweeps", ctypes.c_int64),
+                ("minE", ctypes.c_int64), ("e_gs", ctypes.c_int64), ("min_eps", ctypes.c_double),
+                ("queue_s", ctypes.c_double), ("run_s", ctypes.c_double), ("total_s", ctypes.c_double)]
+
+
 _SIGS = {
     "sg_instance_create": [ctypes.POINTER(InstanceDesc), ctypes.POINTER(_P)],
     "sg_instance_create_from_couplings": [ctypes.c_int32, _P, ctypes.c_int32, ctypes.c_int64,
@@ -82,6 +102,11 @@ _SIGS = {
     "sg_version": [],
     "sg_stats_enable": [ctypes.c_int32],
     "sg_stats_read": [ctypes.POINTER(KernelStats), ctypes.c_int32],
+    "sg_server_create": [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)],
+    "sg_submit": [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
+    "sg_poll": [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(Result)],
+    "sg_cancel": [_P, ctypes.c_uint64],
+    "sg_server_destroy": [_P],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -317,3 +342,59 @@ def energy_noalloc(L: int, J3_dev, spins_dev, E_dev, stream=None):
     assert E_dev.numel() == n
     _check(_lib.sg_energy_noalloc(L, _P(J3_dev.data_ptr()), _P(spins_dev.data_ptr()), n,
                                   _P(E_dev.data_ptr()), _stream_handle(stream)))
+
+
+def request(kind: int, L: int, seed: int, width: int, beta0: float, beta1: float, eps_target: float,
+            sweep_cap: int, run_seed: int = 0, sweeps_per_restart: int = 1000,
+            schedule: int = SG_SCHEDULE_LINEAR, class_prob=(1 / 3, 1 / 3, 1 / 3),
+            gauge: bool = True) -> Request:
+    """A solve request: a fresh tile-planted instance (L, seed, class_prob, gauge) solved by
+    SA (width replicas, restarts of sweeps_per_restart sweeps) or PT (width temperatures)
+    until its gap reaches eps_target (Eq. 2) or sweep_cap sweeps have run."""
+    d = InstanceDesc(L, int(bool(gauge)), seed, (ctypes.c_double * 3)(*class_prob))
+    return Request(kind, d, width, sweeps_per_restart, beta0, beta1, schedule, run_seed, eps_target,
+                   sweep_cap)
+
+
+class Server:
+    """Continuously batched solve server on the current CUDA device (sg_server_*)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_active: int = 64, chunk_sweeps: int = 50,
+                 queue_capacity: int = 1 << 16):
+        self._h = _P()
+        cfg = ServerConfig(hbm_budget_bytes, max_active, chunk_sweeps, queue_capacity)
+        _check(_lib.sg_server_create(ctypes.byref(cfg), ctypes.byref(self._h)))
+
+    def submit(self, req: Request) -> int:
+        t = ctypes.c_uint64()
+        _check(_lib.sg_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        return int(t.value)
+
+    def poll(self, ticket: int, timeout_ms: int = -1):
+        """The result as a dict once done (reported once), else None."""
+        r = Result()
+        rc = _lib.sg_poll(self._h, ticket, timeout_ms, ctypes.byref(r))
+        if rc == SG_PENDING:
+            return None
+        _check(rc)
+        return {f: getattr(r, f) for f, _ in Result._fields_}
+
+    def cancel(self, ticket: int):
+        _check(_lib.sg_cancel(self._h, ticket))
+
+    def close(self):
+        if self._h:
+            _check(_lib.sg_server_destroy(self._h))
+            self._h = _P()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -91,3 +91,21 @@ def test_invalid_arguments(sg):
         with pytest.raises(sg.SGError) as e:
             sg.pt_run(inst, **args)
         assert e.value.code == sg.SG_EINVAL
+
+
+def test_server_rejects_bad_config_and_null_handles(sg):
+    for bad in [dict(hbm_budget_bytes=0), dict(max_active=0), dict(chunk_sweeps=0),
+                dict(queue_capacity=0)]:
+        args = dict(hbm_budget_bytes=1 << 30, max_active=4, chunk_sweeps=10, queue_capacity=8)
+        args.update(bad)
+        with pytest.raises(sg.SGError) as e:
+            sg.Server(**args)
+        assert e.value.code == sg.SG_EINVAL
+    lib = sg._lib
+    req = sg.request(sg.SG_REQ_SA, 8, 1, 8, 0.1, 3.0, 0.0, 10)
+    t = ctypes.c_uint64()
+    assert lib.sg_submit(None, ctypes.byref(req), ctypes.byref(t)) == sg.SG_EINVAL
+    res = sg.Result()
+    assert lib.sg_poll(None, 1, 0, ctypes.byref(res)) == sg.SG_EINVAL
+    assert lib.sg_cancel(None, 1) == sg.SG_EINVAL
+    assert lib.sg_server_destroy(None) == sg.SG_OK
