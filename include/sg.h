@@ -247,6 +247,11 @@ int32_t sg_server_create(const sg_server_config* cfg, sg_server** out);
  * (it alone needs more than the budget), SG_EBUSY (queue full). */
 int32_t sg_submit(sg_server* srv, const sg_request* req, uint64_t* ticket);
 
+/* Device memory the server would hold for this request while it runs (the amount
+ * admission counts against hbm_budget_bytes): spins, couplings, tables and run state.
+ * The instance is generated to size its tables.  Errors: SG_EINVAL. */
+int32_t sg_request_bytes(const sg_request* req, uint64_t* bytes);
+
 /* Wait up to timeout_ms (0: just look; < 0: wait until done) for a request.  Returns
  * SG_OK with *out filled once it is done (a ticket is reported once, then forgotten),
  * SG_PENDING while it is not, SG_EINVAL for an unknown ticket. */

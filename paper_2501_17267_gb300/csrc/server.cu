@@ -1,18 +1,23 @@
 // server.cu -- continuously batched solve server: requests run until their lowest energy
 // reaches a target gap (time to target, TT-eps, Eq. 2) or a sweep cap.
 //
-// One worker thread per server owns the device work.  Requests wait in a FIFO queue;
-// the worker admits them while their device memory fits the budget and a slot is free,
-// keeps their state resident, and advances every admitted request by one chunk of
-// sweeps per round:
-//   - all SA requests together in one persistent plane launch (batch.cu), each with its
-//     own sweep range inside its current restart;
-//   - each PT request by replaying its own CUDA graph (one chunk of sweeps and
-//     exchanges, the sweep index read from device memory) on its own stream,
-// so requests that arrive while others run join the next round and their kernels
-// overlap on the GPU.  Completion is checked between rounds, at sweep counts that do
-// not depend on what else runs, so each result is the same alone and in any mix.
+// sg_submit generates the request's instance and host tables in the caller's thread and
+// queues it.  One worker thread per server owns the device work: it admits queued
+// requests (FIFO) while their device memory fits the budget and a slot is free, keeps
+// their state resident in one stream-ordered allocation each, and keeps every admitted
+// request busy, one chunk of sweeps at a time, with no barrier between requests:
+//   - PT requests, and SA requests on lattices too large for one thread block, replay
+//     their own CUDA graph (a chunk of multi-block sweeps whose sweep index lives in
+//     device memory, then the energy check) on their own stream;
+//   - small SA requests share a persistent plane launch (batch.cu) per plane width,
+//     relaunched with whatever small requests are ready whenever the previous one ends.
+// The worker polls events, so a chunk that ends lets its request check for completion
+// and start the next chunk at once, and arrivals join as soon as they are admitted.
+// Completion is checked only at chunk ends, at sweep counts fixed by the request alone,
+// so each result is the same alone and in any mix.
+#include <limits.h>
 #include <math.h>
+#include <stdlib.h>
 #include <string.h>
 
 #include <algorithm>
@@ -36,68 +41,48 @@ using Clock = std::chrono::steady_clock;
 
 __global__ void advance_kernel(uint32_t* base, uint32_t by) { *base += by; }
 
-// Device allocation owned by a request (freed synchronously at retirement).
-struct DMem {
-    void* p = nullptr;
-    DMem() = default;
-    DMem(const DMem&) = delete;
-    DMem& operator=(const DMem&) = delete;
-    ~DMem() { reset(); }
-    void reset()
-    {
-        if (p) cudaFree(p);
-        p = nullptr;
+// Start of an SA restart: key (k0, k1) and sweep index 0.
+__global__ void restart_kernel(RunKeys* keys, uint32_t k0, uint32_t k1, uint32_t* base)
+{
+    keys->k0 = k0;
+    keys->k1 = k1;
+    *base = 0;
+}
+
+// out = min over the R valid replicas of the energy sums (two's complement in 64 bits).
+__global__ void min_energy_kernel(const unsigned long long* E64, int R, long long* out)
+{
+    __shared__ long long s[256];
+    long long m = LLONG_MAX;
+    for (int r = threadIdx.x; r < R; r += blockDim.x) m = min(m, (long long)E64[r]);
+    s[threadIdx.x] = m;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w) s[threadIdx.x] = min(s[threadIdx.x], s[threadIdx.x + w]);
+        __syncthreads();
     }
-    bool alloc(size_t bytes)
-    {
-        reset();
-        if (cudaMalloc(&p, bytes ? bytes : 16) != cudaSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-            return false;
-        }
-        return true;
-    }
-    template <class T>
-    T* as() const
-    {
-        return static_cast<T*>(p);
-    }
+    if (threadIdx.x == 0) *out = s[0];
+}
+
+// The PT running minimum (int32) as the 64-bit word the host reads.
+__global__ void widen_kernel(const int32_t* minE, long long* out) { *out = *minE; }
+
+enum Mode { kPlanes = 0, kRowsSA = 1, kPT = 2 };
+
+// A stream, an event and a little pinned memory, reused by successive requests.
+struct Slot {
+    cudaStream_t st = nullptr;
+    cudaEvent_t ev = nullptr;
+    long long* h_out = nullptr;  // pinned: [0] min energy of the last chunk
 };
 
-// Device or pinned host buffer that only grows (reused across rounds).
-struct GrowBuf {
-    void* p = nullptr;
-    size_t cap = 0;
-    bool host = false;
-    GrowBuf() = default;
-    GrowBuf(const GrowBuf&) = delete;
-    GrowBuf& operator=(const GrowBuf&) = delete;
-    ~GrowBuf() { release(); }
-    void release()
-    {
-        if (p) host ? cudaFreeHost(p) : cudaFree(p);
-        p = nullptr;
-        cap = 0;
-    }
-    bool ensure(size_t bytes)
-    {
-        if (bytes <= cap) return true;
-        release();
-        const size_t n = std::max<size_t>(bytes, 4096);
-        if ((host ? cudaMallocHost(&p, n) : cudaMalloc(&p, n)) != cudaSuccess) {
-            cudaGetLastError();
-            p = nullptr;
-            return false;
-        }
-        cap = n;
-        return true;
-    }
-    template <class T>
-    T* as() const
-    {
-        return static_cast<T*>(p);
-    }
+size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
+
+// Offsets into the request's single device allocation.
+struct Layout {
+    size_t j6 = 0, j1 = 0, J3 = 0, spins = 0, thr = 0, keys = 0, jp = 0, base = 0, E = 0, E64 = 0,
+           perm = 0, inv = 0, acc = 0, minE = 0, done = 0, xtab = 0, xoff = 0, xlen = 0, xtail = 0,
+           out = 0, total = 0;
 };
 
 struct Request {
@@ -106,52 +91,104 @@ struct Request {
     Clock::time_point t_submit, t_admit, t_done;
     size_t bytes = 0;
     bool admitted = false;
-    bool finished = false;  // guarded by the server mutex: the result may be read
-    bool cancelled = false; // guarded by the server mutex
-    bool done = false;      // worker only: stop after this round
+    bool finished = false;   // guarded by the server mutex: the result may be read
+    bool cancelled = false;  // guarded by the server mutex
+    // worker only
+    bool stopping = false;   // cancelled or server stopping: stop when idle
+    bool done = false;       // retire
+    bool inflight = false;   // a chunk (own stream or plane launch) is running
     sg_result result{};
-    sg_instance* inst = nullptr;
-    int64_t target = 0;       // done when min energy <= target
-    int64_t sweeps = 0;       // sweeps run so far (all restarts)
+    std::unique_ptr<sg_instance, int32_t (*)(sg_instance*)> inst{nullptr, sg_instance_destroy};
+    int mode = kPlanes;
+    int L = 0, Wn = 0, Rp = 0, WG = 1;
+    int64_t N = 0;
+    int64_t target = 0;        // done when min energy <= target
+    int64_t sweeps = 0;        // sweeps run so far (all restarts)
     int64_t minE = INT64_MAX;
+    int step = 0;              // sweeps of the chunk in flight
+    // host tables made at submit
+    std::shared_ptr<const std::vector<uint32_t>> thr;  // SA: [S][kThrRow]; PT: [K][kThrRow]
+    ExchangeTables xt;
     // SA
-    int WG = 1, restart = 0, in_restart = 0;
+    int restart = 0, in_restart = 0;
     bool need_init = true;
-    const uint32_t* thr = nullptr;  // shared schedule table (owned by the server)
-    DMem sa_spins;
-    // PT
-    cudaStream_t stream = nullptr;
-    cudaGraphExec_t graph = nullptr;
-    DMem pt_spins, pt_E, pt_E64, pt_thr, pt_keys, pt_jp, pt_perm, pt_inv, pt_acc, pt_min, pt_done,
-        pt_base, pt_xtab, pt_xoff, pt_xlen, pt_xtail;
-    int32_t* h_min = nullptr;  // pinned
-    // Frees every device resource (the result stays).
-    void release()
+    // device state
+    Layout lay;
+    unsigned char* mem = nullptr;
+    Slot* slot = nullptr;
+    std::map<int, cudaGraphExec_t> graphs;  // chunk length -> graph
+    template <class T>
+    T* at(size_t off) const
     {
-        if (graph) cudaGraphExecDestroy(graph);
-        graph = nullptr;
-        if (stream) cudaStreamDestroy(stream);
-        stream = nullptr;
-        if (h_min) cudaFreeHost(h_min);
-        h_min = nullptr;
-        for (DMem* d : {&sa_spins, &pt_spins, &pt_E, &pt_E64, &pt_thr, &pt_keys, &pt_jp, &pt_perm, &pt_inv,
-                        &pt_acc, &pt_min, &pt_done, &pt_base, &pt_xtab, &pt_xoff, &pt_xlen, &pt_xtail})
-            d->reset();
-        if (inst) sg_instance_destroy(inst);
-        inst = nullptr;
+        return reinterpret_cast<T*>(mem + off);
     }
-    ~Request() { release(); }
 };
 
-// Per plane width: a stream and reusable launch buffers for the SA requests of a round.
-struct SaGroup {
+Layout layout_of(const Request& q)
+{
+    Layout y;
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = o;
+        o = align_up(o + std::max<size_t>(bytes, 1));
+        return at;
+    };
+    const size_t N = (size_t)q.N, Rp = (size_t)q.Rp;
+    y.j6 = take(8 * N);
+    y.j1 = take(N);
+    y.J3 = take(3 * N);
+    y.spins = take(N * Rp);
+    if (q.mode == kPlanes) {
+        y.thr = take(4 * q.thr->size());
+    } else if (q.mode == kRowsSA) {
+        y.thr = take(4 * q.thr->size());
+        y.keys = take(sizeof(RunKeys));
+        y.jp = take(2 * sizeof(void*));
+        y.base = take(4);
+        y.E64 = take(8 * Rp);
+        y.out = take(8);
+    } else {
+        const size_t K = (size_t)q.req.width, Kp = std::max<size_t>(K - 1, 1);
+        y.thr = take(4 * q.thr->size());
+        y.keys = take(sizeof(RunKeys));
+        y.jp = take(2 * sizeof(void*));
+        y.base = take(4);
+        y.E = take(4 * Rp);
+        y.E64 = take(8 * Rp);
+        y.perm = take(Rp);
+        y.inv = take(K);
+        y.acc = take(8 * Kp);
+        y.minE = take(4);
+        y.done = take(4);
+        y.xtab = take(4 * q.xt.tab.size());
+        y.xoff = take(4 * q.xt.off.size());
+        y.xlen = take(4 * q.xt.len.size());
+        y.xtail = take(4 * q.xt.tail.size());
+        y.out = take(8);
+    }
+    y.total = o;
+    return y;
+}
+
+// Small SA requests of one plane width: one persistent launch over all their planes, each
+// plane running sweeps [in_restart, in_restart + step) of its current restart.
+struct PlaneGroup {
     int WG = 1;
     cudaStream_t st = nullptr;
-    GrowBuf pl, ord, next, E, init, hE;
+    cudaEvent_t ev = nullptr;
+    bool inflight = false;
+    void *pl = nullptr, *ord = nullptr, *next = nullptr, *E = nullptr, *init = nullptr;
+    unsigned long long* hE = nullptr;  // pinned
+    size_t cap_planes = 0;
     std::vector<Request*> reqs;
     std::vector<Plane> planes, init_planes;
-    std::vector<int> first, steps;
-    int32_t rc = SG_OK;
+    std::vector<int> first;
+};
+
+// Host schedule tables shared by requests with the same SA schedule.
+struct ScheduleCache {
+    std::mutex mu;
+    std::map<std::tuple<int, double, double, int>, std::shared_ptr<const std::vector<uint32_t>>> tables;
 };
 
 int largest_wg(int Wn)
@@ -161,16 +198,16 @@ int largest_wg(int Wn)
     return wg;
 }
 
-size_t request_bytes(const sg_request& r)
+// Largest side that runs in the shared plane launch (one thread block per plane); larger
+// SA lattices run multi-block sweeps on their own stream.  Knob: SG_SERVER_PLANE_MAX_L.
+int plane_max_L()
 {
-    const size_t N = (size_t)r.instance.L * r.instance.L * r.instance.L;
-    const size_t Rp = 4 * (size_t)((r.width + 3) / 4);
-    size_t b = N * Rp + 9 * N + 4096;  // spins, coupling records, small state
-    if (r.kind == SG_REQ_SA)
-        b += (size_t)r.sweeps_per_restart * 64;
-    else
-        b += 16 * Rp * sizeof(uint32_t) + (size_t)r.width * (1u << 14);  // thresholds, exchange tables
-    return b;
+    static const int v = [] {
+        const char* e = getenv("SG_SERVER_PLANE_MAX_L");
+        const int x = e ? atoi(e) : 16;
+        return x < 0 ? 0 : x;
+    }();
+    return v;
 }
 
 }  // namespace
@@ -188,19 +225,28 @@ struct sg_server {
     size_t in_use = 0;
     bool stop = false;
     std::thread worker;
+    sg::ScheduleCache schedules;  // used by the submitting threads
     // device resources of the worker
-    cudaStream_t setup_stream = nullptr;
-    sg::SaGroup groups[3];  // plane widths 4, 2, 1
-    std::map<std::tuple<int, double, double, int>, sg::DMem*> schedules;
+    cudaMemPool_t pool = nullptr;
+    std::vector<std::unique_ptr<sg::Slot>> slots;  // all slots made
+    std::vector<sg::Slot*> free_slots;
+    sg::PlaneGroup groups[3];  // plane widths 4, 2, 1
     ~sg_server()
     {
-        for (auto& kv : schedules) delete kv.second;
         all.clear();
         for (auto& g : groups) {
-            g.pl.release(), g.ord.release(), g.next.release(), g.E.release(), g.init.release(), g.hE.release();
+            for (void* p : {g.pl, g.ord, g.next, g.E, g.init})
+                if (p) cudaFree(p);
+            if (g.hE) cudaFreeHost(g.hE);
+            if (g.ev) cudaEventDestroy(g.ev);
             if (g.st) cudaStreamDestroy(g.st);
         }
-        if (setup_stream) cudaStreamDestroy(setup_stream);
+        for (auto& s : slots) {
+            if (s->h_out) cudaFreeHost(s->h_out);
+            if (s->ev) cudaEventDestroy(s->ev);
+            if (s->st) cudaStreamDestroy(s->st);
+        }
+        if (pool) cudaMemPoolDestroy(pool);
     }
 };
 
@@ -212,175 +258,338 @@ double secs(Clock::time_point a, Clock::time_point b)
     return std::chrono::duration<double>(b - a).count();
 }
 
-// Device state of an admitted request; false on failure (result.status set).
-bool admit_request(sg_server* srv, Request* q)
+Slot* take_slot(sg_server* srv)
+{
+    if (!srv->free_slots.empty()) {
+        Slot* s = srv->free_slots.back();
+        srv->free_slots.pop_back();
+        return s;
+    }
+    auto s = std::make_unique<Slot>();
+    if (cudaStreamCreateWithFlags(&s->st, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&s->ev, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMallocHost(&s->h_out, 64) != cudaSuccess) {
+        cudaGetLastError();
+        if (s->h_out) cudaFreeHost(s->h_out);
+        if (s->ev) cudaEventDestroy(s->ev);
+        if (s->st) cudaStreamDestroy(s->st);
+        return nullptr;
+    }
+    srv->slots.push_back(std::move(s));
+    return srv->slots.back().get();
+}
+
+// Host part of a request, in the submitting thread: the instance, its target and the
+// acceptance tables.  SG_OK or SG_EINVAL.
+int32_t prepare_request(ScheduleCache& cache, Request* q)
 {
     const sg_request& r = q->req;
-    auto fail = [&](int32_t code) {
-        q->result.status = code;
-        return false;
-    };
-    if (sg_instance_create(&r.instance, &q->inst) != SG_OK) return fail(SG_EINVAL);
-    q->result.e_gs = q->inst->e_gs;
-    const int64_t abs_gs = q->inst->e_gs < 0 ? -q->inst->e_gs : q->inst->e_gs;
-    q->target = q->inst->e_gs + (int64_t)floor(r.eps_target * (double)abs_gs);
-    const uint2* j6 = nullptr;
-    const uint8_t* j1 = nullptr;
-    if (instance_device_j6(q->inst, srv->setup_stream, &j6, &j1) != SG_OK) return fail(SG_ENOMEM);
-    const int L = q->inst->L;
-    const size_t N = (size_t)q->inst->N;
-    const int Wn = (r.width + 3) / 4, Rp = 4 * Wn;
+    sg_instance* inst = nullptr;
+    int32_t rc = sg_instance_create(&r.instance, &inst);
+    if (rc != SG_OK) return rc;
+    q->inst.reset(inst);
+    q->L = inst->L;
+    q->N = inst->N;
+    q->Wn = (r.width + 3) / 4;
+    q->Rp = 4 * q->Wn;
+    q->WG = largest_wg(q->Wn);
+    q->result.e_gs = inst->e_gs;
+    const int64_t abs_gs = inst->e_gs < 0 ? -inst->e_gs : inst->e_gs;
+    q->target = inst->e_gs + (int64_t)floor(r.eps_target * (double)abs_gs);
     if (r.kind == SG_REQ_SA) {
-        auto key = std::make_tuple(r.sweeps_per_restart, r.beta0, r.beta1, r.schedule);
-        auto it = srv->schedules.find(key);
-        if (it == srv->schedules.end()) {
+        q->mode = q->L <= plane_max_L() ? kPlanes : kRowsSA;
+        if (q->mode == kRowsSA && !rows_kernel_supports(q->Wn)) q->mode = kPlanes;
+        const auto key = std::make_tuple(r.sweeps_per_restart, r.beta0, r.beta1, r.schedule);
+        std::lock_guard<std::mutex> lock(cache.mu);
+        auto it = cache.tables.find(key);
+        if (it == cache.tables.end()) {
             const int S = r.sweeps_per_restart;
             std::vector<double> beta(S);
             beta_schedule(S, r.beta0, r.beta1, r.schedule == SG_SCHEDULE_GEOMETRIC, beta.data());
-            std::vector<uint32_t> t((size_t)S * kThrRow);
-            for (int s = 0; s < S; ++s) metropolis_row(beta[s], &t[(size_t)s * kThrRow]);
-            DMem* d = new DMem;
-            if (!d->alloc(t.size() * 4) ||
-                cudaMemcpy(d->p, t.data(), t.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) {
-                delete d;
-                return fail(SG_ENOMEM);
-            }
-            it = srv->schedules.emplace(key, d).first;
+            auto t = std::make_shared<std::vector<uint32_t>>((size_t)S * kThrRow);
+            for (int s = 0; s < S; ++s) metropolis_row(beta[s], t->data() + (size_t)s * kThrRow);
+            it = cache.tables.emplace(key, std::move(t)).first;
         }
-        q->thr = it->second->as<uint32_t>();
-        q->WG = largest_wg(Wn);
-        if (!q->sa_spins.alloc(N * Rp)) return fail(SG_ENOMEM);
-        return true;
+        q->thr = it->second;
+    } else {
+        q->mode = kPT;
+        if (!rows_kernel_supports(q->Wn)) {
+            set_error("PT with %d temperatures is not supported", r.width);
+            return SG_EINVAL;
+        }
+        const int K = r.width;
+        std::vector<double> ladder(K);
+        beta_schedule(K, r.beta0, r.beta1, 1, ladder.data());
+        auto t = std::make_shared<std::vector<uint32_t>>((size_t)K * kThrRow);
+        for (int k = 0; k < K; ++k) metropolis_row(ladder[k], t->data() + (size_t)k * kThrRow);
+        q->thr = t;
+        rc = build_exchange_tables(ladder, 4 * (int64_t)inst->abs_sum, &q->xt);
+        if (rc != SG_OK) return rc;
     }
-    // PT: state, thresholds, exchange tables, and the captured chunk graph
-    if (!rows_kernel_supports(Wn)) return fail(SG_EINVAL);
-    const int K = r.width;
-    std::vector<double> ladder(K);
-    beta_schedule(K, r.beta0, r.beta1, 1, ladder.data());
-    std::vector<uint32_t> thr((size_t)K * kThrRow);
-    for (int k = 0; k < K; ++k) metropolis_row(ladder[k], &thr[(size_t)k * kThrRow]);
-    ExchangeTables xt;
-    if (build_exchange_tables(ladder, 4 * (int64_t)q->inst->abs_sum, &xt) != SG_OK) return fail(SG_EINVAL);
-    const int Kp = std::max(K - 1, 1);
-    const RunKeys key{(uint32_t)r.seed, (uint32_t)(r.seed >> 32)};
-    const void* jp[2] = {j6, j1};
-    bool ok = q->pt_spins.alloc(N * Rp) && q->pt_E.alloc(4 * Rp) && q->pt_E64.alloc(8 * Rp) &&
-              q->pt_thr.alloc(thr.size() * 4) && q->pt_keys.alloc(sizeof(RunKeys)) &&
-              q->pt_jp.alloc(sizeof(jp)) && q->pt_perm.alloc(Rp) && q->pt_inv.alloc(K) &&
-              q->pt_acc.alloc(8 * Kp) && q->pt_min.alloc(4) && q->pt_done.alloc(4) &&
-              q->pt_base.alloc(4) && q->pt_xtab.alloc(4 * xt.tab.size()) &&
-              q->pt_xoff.alloc(4 * xt.off.size()) && q->pt_xlen.alloc(4 * xt.len.size()) &&
-              q->pt_xtail.alloc(4 * xt.tail.size());
-    if (!ok) return fail(SG_ENOMEM);
-    if (cudaStreamCreateWithFlags(&q->stream, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaMallocHost(&q->h_min, sizeof(int32_t)) != cudaSuccess)
-        return fail(SG_ECUDA);
-    cudaStream_t st = q->stream;
-    bool cu = cudaMemcpyAsync(q->pt_thr.p, thr.data(), thr.size() * 4, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-              cudaMemcpyAsync(q->pt_keys.p, &key, sizeof(key), cudaMemcpyHostToDevice, st) == cudaSuccess &&
-              cudaMemcpyAsync(q->pt_jp.p, jp, sizeof(jp), cudaMemcpyHostToDevice, st) == cudaSuccess &&
-              cudaMemcpyAsync(q->pt_xtab.p, xt.tab.data(), 4 * xt.tab.size(), cudaMemcpyHostToDevice, st) == cudaSuccess &&
-              cudaMemcpyAsync(q->pt_xoff.p, xt.off.data(), 4 * xt.off.size(), cudaMemcpyHostToDevice, st) == cudaSuccess &&
-              cudaMemcpyAsync(q->pt_xlen.p, xt.len.data(), 4 * xt.len.size(), cudaMemcpyHostToDevice, st) == cudaSuccess &&
-              cudaMemcpyAsync(q->pt_xtail.p, xt.tail.data(), 4 * xt.tail.size(), cudaMemcpyHostToDevice, st) == cudaSuccess &&
-              cudaMemsetAsync(q->pt_E64.p, 0, 8 * Rp, st) == cudaSuccess &&
-              cudaMemsetAsync(q->pt_done.p, 0, 4, st) == cudaSuccess &&
-              cudaMemsetAsync(q->pt_base.p, 0, 4, st) == cudaSuccess;
-    if (!cu) return fail(SG_ECUDA);
-    int8_t* spins = q->pt_spins.as<int8_t>();
-    const uint2* const* j6p = q->pt_jp.as<const uint2*>();
-    const uint8_t* const* j1p = reinterpret_cast<const uint8_t* const*>(q->pt_jp.as<const void*>() + 1);
-    const RunKeys* kp = q->pt_keys.as<RunKeys>();
-    if (launch_init_spins(spins, kp, 1, L, Wn, K, st) != SG_OK ||
-        launch_energy(spins, j6p, 1, L, Wn, q->pt_E64.as<unsigned long long>(), st) != SG_OK ||
-        launch_pt_setup(q->pt_E64.as<unsigned long long>(), q->pt_E.as<int32_t>(), q->pt_perm.as<uint8_t>(),
-                        q->pt_inv.as<uint8_t>(), q->pt_acc.as<unsigned long long>(), q->pt_min.as<int32_t>(), 1,
-                        Rp, K, st) != SG_OK)
-        return fail(SG_ECUDA);
-    // one chunk as a graph: chunk x (colour 0, colour 1 with the exchange), then advance
-    ExchangeArgs xa;
-    xa.keys = kp;
-    xa.E = q->pt_E.as<int32_t>();
-    xa.rung_of_slot = q->pt_perm.as<uint8_t>();
-    xa.slot_of_rung = q->pt_inv.as<uint8_t>();
-    xa.accepts = q->pt_acc.as<unsigned long long>();
-    xa.minE = q->pt_min.as<int32_t>();
-    xa.xtab = q->pt_xtab.as<uint32_t>();
-    xa.xoff = q->pt_xoff.as<uint32_t>();
-    xa.xlen = q->pt_xlen.as<uint32_t>();
-    xa.xtail = q->pt_xtail.as<uint32_t>();
-    xa.Rp = Rp;
-    xa.K = K;
-    xa.sweep_base = q->pt_base.as<uint32_t>();
+    q->lay = layout_of(*q);
+    q->bytes = q->lay.total;
+    return SG_OK;
+}
+
+// Device part of admission, on the request's own stream: one allocation from the
+// server's pool, couplings and tables uploaded, PT state initialised.  Returns a status;
+// on failure the caller releases what was taken.
+int32_t admit_request(sg_server* srv, Request* q)
+{
+    q->slot = take_slot(srv);
+    if (!q->slot) return SG_ECUDA;
+    cudaStream_t st = q->slot->st;
+    void* p = nullptr;
+    if (cudaMallocFromPoolAsync(&p, q->lay.total, srv->pool, st) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("device memory for a request of %zu bytes is not available", q->lay.total);
+        return SG_ENOMEM;
+    }
+    q->mem = static_cast<unsigned char*>(p);
+    const Layout& y = q->lay;
+    const sg_instance* inst = q->inst.get();
+    const size_t N = (size_t)q->N;
+    SG_TRY_CUDA(cudaMemcpyAsync(q->at<void>(y.J3), inst->J3.data(), 3 * N, cudaMemcpyHostToDevice, st));
+    int32_t rc = launch_prepare_j6(q->at<int8_t>(y.J3), q->at<uint2>(y.j6), q->at<uint8_t>(y.j1), q->L, st);
+    if (rc != SG_OK) return rc;
+    SG_TRY_CUDA(cudaMemcpyAsync(q->at<void>(y.thr), q->thr->data(), 4 * q->thr->size(), cudaMemcpyHostToDevice, st));
+    if (q->mode == kPlanes) {  // the shared plane launch waits for these uploads
+        SG_TRY_CUDA(cudaEventRecord(q->slot->ev, st));
+        return SG_OK;
+    }
+    const void* jp[2] = {q->at<void>(y.j6), q->at<void>(y.j1)};
+    SG_TRY_CUDA(cudaMemcpyAsync(q->at<void>(y.jp), jp, sizeof(jp), cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemsetAsync(q->at<void>(y.base), 0, 4, st));
+    if (q->mode == kRowsSA) return SG_OK;
+    // PT: keys, exchange tables, initial spins and energies, the identity permutation
+    const RunKeys key{(uint32_t)q->req.seed, (uint32_t)(q->req.seed >> 32)};
+    SG_TRY_CUDA(cudaMemcpyAsync(q->at<void>(y.keys), &key, sizeof(key), cudaMemcpyHostToDevice, st));
+    const ExchangeTables& xt = q->xt;
+    SG_TRY_CUDA(cudaMemcpyAsync(q->at<void>(y.xtab), xt.tab.data(), 4 * xt.tab.size(), cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(q->at<void>(y.xoff), xt.off.data(), 4 * xt.off.size(), cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(q->at<void>(y.xlen), xt.len.data(), 4 * xt.len.size(), cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(q->at<void>(y.xtail), xt.tail.data(), 4 * xt.tail.size(), cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemsetAsync(q->at<void>(y.E64), 0, 8 * (size_t)q->Rp, st));
+    SG_TRY_CUDA(cudaMemsetAsync(q->at<void>(y.done), 0, 4, st));
+    const RunKeys* kp = q->at<RunKeys>(y.keys);
+    const uint2* const* j6p = q->at<const uint2*>(y.jp);
+    rc = launch_init_spins(q->at<int8_t>(y.spins), kp, 1, q->L, q->Wn, q->req.width, st);
+    if (rc == SG_OK) rc = launch_energy(q->at<int8_t>(y.spins), j6p, 1, q->L, q->Wn, q->at<unsigned long long>(y.E64), st);
+    if (rc == SG_OK)
+        rc = launch_pt_setup(q->at<unsigned long long>(y.E64), q->at<int32_t>(y.E), q->at<uint8_t>(y.perm),
+                             q->at<uint8_t>(y.inv), q->at<unsigned long long>(y.acc), q->at<int32_t>(y.minE), 1,
+                             q->Rp, q->req.width, st);
+    return rc;
+}
+
+// Captures one chunk of n sweeps of a PT or large-SA request as a graph: the sweeps
+// (sweep index = device base + c), the base advanced by n, and the chunk's lowest energy
+// copied to the slot's pinned word.
+int32_t capture_chunk(Request* q, int n, cudaGraphExec_t* out)
+{
+    const Layout& y = q->lay;
+    cudaStream_t st = q->slot->st;
+    int8_t* spins = q->at<int8_t>(y.spins);
+    const uint2* const* j6p = q->at<const uint2*>(y.jp);
+    const uint8_t* const* j1p = reinterpret_cast<const uint8_t* const*>(q->at<const void*>(y.jp) + 1);
+    const RunKeys* kp = q->at<RunKeys>(y.keys);
+    uint32_t* base = q->at<uint32_t>(y.base);
+    const uint32_t* thr = q->at<uint32_t>(y.thr);
     const bool unit = q->inst->unit_couplings;
-    cudaGraph_t g = nullptr;
-    if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return fail(SG_ECUDA);
+    ExchangeArgs xa{};
+    if (q->mode == kPT) {
+        xa.keys = kp;
+        xa.E = q->at<int32_t>(y.E);
+        xa.rung_of_slot = q->at<uint8_t>(y.perm);
+        xa.slot_of_rung = q->at<uint8_t>(y.inv);
+        xa.accepts = q->at<unsigned long long>(y.acc);
+        xa.minE = q->at<int32_t>(y.minE);
+        xa.xtab = q->at<uint32_t>(y.xtab);
+        xa.xoff = q->at<uint32_t>(y.xoff);
+        xa.xlen = q->at<uint32_t>(y.xlen);
+        xa.xtail = q->at<uint32_t>(y.xtail);
+        xa.Rp = q->Rp;
+        xa.K = q->req.width;
+        xa.sweep_base = base;
+    }
+    SG_TRY_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     int32_t rc = SG_OK;
-    for (int c = 0; c < srv->cfg.chunk_sweeps && rc == SG_OK; ++c) {
-        bool fused = false;
-        rc = launch_sweep_rows_pt(spins, j6p, j1p, kp, q->pt_thr.as<uint32_t>(), q->pt_perm.as<uint8_t>(),
-                                  q->pt_E.as<int32_t>(), unit, 1, L, Wn, K, (uint32_t)c, 0, nullptr,
-                                  q->pt_done.as<unsigned>(), nullptr, st, q->pt_base.as<uint32_t>());
-        if (rc == SG_OK)
-            rc = launch_sweep_rows_pt(spins, j6p, j1p, kp, q->pt_thr.as<uint32_t>(), q->pt_perm.as<uint8_t>(),
-                                      q->pt_E.as<int32_t>(), unit, 1, L, Wn, K, (uint32_t)c, 1, &xa,
-                                      q->pt_done.as<unsigned>(), &fused, st, q->pt_base.as<uint32_t>());
-        if (rc == SG_OK && !fused) rc = launch_pt_exchange(xa, 1, (uint32_t)c, st);
+    for (int c = 0; c < n && rc == SG_OK; ++c) {
+        if (q->mode == kRowsSA) {
+            for (int colour = 0; colour < 2 && rc == SG_OK; ++colour)
+                rc = launch_sweep_rows_sa(spins, j6p, j1p, kp, thr, unit, 1, q->L, q->Wn, q->req.width,
+                                          (uint32_t)c, colour, st, base);
+        } else {
+            bool fused = false;
+            rc = launch_sweep_rows_pt(spins, j6p, j1p, kp, thr, xa.rung_of_slot, xa.E, unit, 1, q->L, q->Wn,
+                                      q->req.width, (uint32_t)c, 0, nullptr, q->at<unsigned>(y.done), nullptr,
+                                      st, base);
+            if (rc == SG_OK)
+                rc = launch_sweep_rows_pt(spins, j6p, j1p, kp, thr, xa.rung_of_slot, xa.E, unit, 1, q->L,
+                                          q->Wn, q->req.width, (uint32_t)c, 1, &xa, q->at<unsigned>(y.done),
+                                          &fused, st, base);
+            if (rc == SG_OK && !fused) rc = launch_pt_exchange(xa, 1, (uint32_t)c, st);
+        }
     }
     if (rc == SG_OK) {
-        advance_kernel<<<1, 1, 0, st>>>(q->pt_base.as<uint32_t>(), (uint32_t)srv->cfg.chunk_sweeps);
-        if (cudaGetLastError() != cudaSuccess) rc = SG_ECUDA;
+        advance_kernel<<<1, 1, 0, st>>>(base, (uint32_t)n);
+        if (q->mode == kRowsSA) {
+            cudaMemsetAsync(q->at<void>(y.E64), 0, 8 * (size_t)q->Rp, st);
+            rc = launch_energy(spins, j6p, 1, q->L, q->Wn, q->at<unsigned long long>(y.E64), st);
+            if (rc == SG_OK)
+                min_energy_kernel<<<1, 256, 0, st>>>(q->at<unsigned long long>(y.E64), q->req.width,
+                                                     q->at<long long>(y.out));
+        } else {
+            widen_kernel<<<1, 1, 0, st>>>(q->at<int32_t>(y.minE), q->at<long long>(y.out));
+        }
+        if (cudaGetLastError() != cudaSuccess ||
+            cudaMemcpyAsync(q->slot->h_out, q->at<void>(y.out), 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            rc = SG_ECUDA;
     }
-    cudaError_t e = cudaStreamEndCapture(st, &g);
-    if (rc == SG_OK && (e != cudaSuccess || cudaGraphInstantiate(&q->graph, g, 0) != cudaSuccess)) rc = SG_ECUDA;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(st, &g);
+    if (rc == SG_OK && e != cudaSuccess) rc = SG_ECUDA;
+    if (rc == SG_OK && cudaGraphInstantiate(out, g, 0) != cudaSuccess) rc = SG_ECUDA;
     if (g) cudaGraphDestroy(g);
     if (rc != SG_OK) {
         cudaGetLastError();
-        return fail(rc);
+        set_error("capturing a chunk of %d sweeps failed", n);
     }
-    if (cudaStreamSynchronize(st) != cudaSuccess) return fail(SG_ECUDA);
+    return rc;
+}
+
+// Sweeps of the next chunk: a whole chunk, cut at the end of an SA restart and at the cap.
+int next_step(const Request* q, int chunk)
+{
+    if (q->mode == kPT) return chunk;
+    return (int)std::min<int64_t>({(int64_t)chunk, (int64_t)(q->req.sweeps_per_restart - q->in_restart),
+                                   q->req.sweep_cap - q->sweeps});
+}
+
+// Folds a finished chunk into the request: lowest energy, sweep counts, restart end,
+// and the completion test.
+void finish_chunk(Request* q, int64_t chunk_min)
+{
+    q->minE = std::min(q->minE, chunk_min);
+    q->sweeps += q->step;
+    if (q->mode != kPT) {
+        q->in_restart += q->step;
+        if (q->in_restart == q->req.sweeps_per_restart) {  // the next chunk starts restart + 1
+            q->restart += 1;
+            q->in_restart = 0;
+            q->need_init = true;
+        }
+    }
+    q->step = 0;
+    q->inflight = false;
+    if (q->minE <= q->target) {
+        q->result.reached = 1;
+        q->done = true;
+    } else if (q->sweeps >= q->req.sweep_cap) {
+        q->done = true;
+    }
+}
+
+void fail_request(Request* q, int32_t code)
+{
+    q->result.status = code;
+    q->inflight = false;
+    q->done = true;
+}
+
+// Launches the next chunk of a PT or large-SA request on its own stream.
+void launch_own_chunk(Request* q, int chunk)
+{
+    cudaStream_t st = q->slot->st;
+    const int n = next_step(q, chunk);
+    if (q->mode == kRowsSA && q->need_init) {
+        const uint32_t k0 = (uint32_t)q->req.seed;
+        const uint32_t k1 = (uint32_t)(q->req.seed >> 32) ^ (uint32_t)q->restart;  // restart k = instance id k
+        restart_kernel<<<1, 1, 0, st>>>(q->at<RunKeys>(q->lay.keys), k0, k1, q->at<uint32_t>(q->lay.base));
+        if (cudaGetLastError() != cudaSuccess ||
+            launch_init_spins(q->at<int8_t>(q->lay.spins), q->at<RunKeys>(q->lay.keys), 1, q->L, q->Wn,
+                              q->req.width, st) != SG_OK) {
+            cudaGetLastError();
+            return fail_request(q, SG_ECUDA);
+        }
+        q->need_init = false;
+    }
+    auto it = q->graphs.find(n);
+    if (it == q->graphs.end()) {
+        cudaGraphExec_t g = nullptr;
+        if (capture_chunk(q, n, &g) != SG_OK) return fail_request(q, SG_ECUDA);
+        it = q->graphs.emplace(n, g).first;
+    }
+    if (cudaGraphLaunch(it->second, st) != cudaSuccess || cudaEventRecord(q->slot->ev, st) != cudaSuccess) {
+        cudaGetLastError();
+        return fail_request(q, SG_ECUDA);
+    }
+    q->step = n;
+    q->inflight = true;
+}
+
+// True once the request's chunk has ended (and then folds it in).
+bool poll_own_chunk(Request* q)
+{
+    const cudaError_t e = cudaEventQuery(q->slot->ev);
+    if (e == cudaErrorNotReady) return false;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        fail_request(q, SG_ECUDA);
+        return true;
+    }
+    finish_chunk(q, *q->slot->h_out);
     return true;
 }
 
-// SA requests of one plane width: one persistent launch over all their planes, each
-// plane running sweeps [in_restart, in_restart + n) of its current restart; energies of
-// every replica come back through pinned memory.  Asynchronous on the group's stream.
-void launch_sa_group(SaGroup& g, int chunk)
+bool grow_group(PlaneGroup& g, size_t np)
 {
-    g.rc = SG_OK;
+    if (np <= g.cap_planes) return true;
+    size_t cap = std::max<size_t>(1024, g.cap_planes);
+    while (cap < np) cap *= 2;
+    for (void** p : {&g.pl, &g.ord, &g.next, &g.E, &g.init})
+        if (*p) cudaFree(*p), *p = nullptr;
+    if (g.hE) cudaFreeHost(g.hE), g.hE = nullptr;
+    g.cap_planes = 0;
+    if (cudaMalloc(&g.pl, sizeof(Plane) * cap) != cudaSuccess || cudaMalloc(&g.ord, sizeof(int) * cap) != cudaSuccess ||
+        cudaMalloc(&g.next, 16) != cudaSuccess || cudaMalloc(&g.E, 8 * 16 * cap) != cudaSuccess ||
+        cudaMalloc(&g.init, sizeof(Plane) * cap) != cudaSuccess ||
+        cudaMallocHost(&g.hE, 8 * 16 * cap) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    g.cap_planes = cap;
+    return true;
+}
+
+// Launches the ready small SA requests of one plane width together.
+void launch_group(PlaneGroup& g, const std::vector<Request*>& act, int chunk)
+{
+    g.reqs.clear();
+    for (Request* q : act)
+        if (q->mode == kPlanes && q->WG == g.WG && !q->done && !q->inflight && !q->stopping) g.reqs.push_back(q);
+    if (g.reqs.empty()) return;
     g.planes.clear();
     g.init_planes.clear();
     g.first.assign(1, 0);
-    g.steps.clear();
-    if (g.reqs.empty()) return;
     bool unit = true;
     for (Request* q : g.reqs) unit &= q->inst->unit_couplings;
     for (Request* q : g.reqs) {
-        const sg_request& r = q->req;
-        const int Wn = (r.width + 3) / 4;
-        const int n = (int)std::min<int64_t>({(int64_t)chunk, (int64_t)(r.sweeps_per_restart - q->in_restart),
-                                              r.sweep_cap - q->sweeps});
-        g.steps.push_back(n);
-        const uint2* j6 = nullptr;
-        const uint8_t* j1 = nullptr;
-        if (instance_device_j6(q->inst, g.st, &j6, &j1) != SG_OK) {
-            g.rc = SG_ENOMEM;
-            return;
-        }
-        for (int w0 = 0; w0 < Wn; w0 += g.WG) {
+        q->step = next_step(q, chunk);
+        for (int w0 = 0; w0 < q->Wn; w0 += g.WG) {
             Plane pl{};
-            pl.spins = q->sa_spins.as<uint32_t>() + (size_t)q->inst->N * w0;
-            pl.j1 = j1;
-            pl.j6 = j6;
-            pl.thr = q->thr;
-            pl.k0 = (uint32_t)r.seed;
-            pl.k1 = (uint32_t)(r.seed >> 32) ^ (uint32_t)q->restart;  // restart k runs as instance id k
-            pl.L = q->inst->L;
-            pl.S = r.sweeps_per_restart;
+            pl.spins = q->at<uint32_t>(q->lay.spins) + (size_t)q->N * w0;
+            pl.j1 = q->at<uint8_t>(q->lay.j1);
+            pl.j6 = q->at<uint2>(q->lay.j6);
+            pl.thr = q->at<uint32_t>(q->lay.thr);
+            pl.k0 = (uint32_t)q->req.seed;
+            pl.k1 = (uint32_t)(q->req.seed >> 32) ^ (uint32_t)q->restart;  // restart k = instance id k
+            pl.L = q->L;
+            pl.S = q->req.sweeps_per_restart;
             pl.w0 = w0;
-            pl.R = r.width;
+            pl.R = q->req.width;
             pl.s_begin = q->in_restart;
-            pl.s_end = q->in_restart + n;
+            pl.s_end = q->in_restart + q->step;
             pl.Lmagic = (uint32_t)((0x100000000ull + pl.L - 1) / pl.L);
             pl.Hmagic = (uint32_t)((0x100000000ull + pl.L / 2 - 1) / (pl.L / 2));
             pl.out = (int)(g.first.size() - 1);
@@ -390,108 +599,86 @@ void launch_sa_group(SaGroup& g, int chunk)
         g.first.push_back((int)g.planes.size());
     }
     const int np = (int)g.planes.size(), nI = (int)g.init_planes.size();
-    // longest planes first (work = sites x sweeps)
     std::vector<int> order(np);
     for (int k = 0; k < np; ++k) order[k] = k;
     auto work = [&](int k) {
         const Plane& p = g.planes[k];
         return (double)p.L * p.L * p.L * (p.s_end - p.s_begin);
     };
-    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });  // longest first
     const size_t nE = (size_t)np * 4 * g.WG;
     cudaStream_t st = g.st;
-    bool ok = g.pl.ensure(sizeof(Plane) * np) && g.ord.ensure(sizeof(int) * np) && g.next.ensure(4) &&
-              g.E.ensure(8 * nE) && g.hE.ensure(8 * nE) && g.init.ensure(sizeof(Plane) * std::max(nI, 1));
-    ok = ok && cudaMemcpyAsync(g.pl.p, g.planes.data(), sizeof(Plane) * np, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-         cudaMemcpyAsync(g.ord.p, order.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st) == cudaSuccess &&
-         cudaMemsetAsync(g.next.p, 0, 4, st) == cudaSuccess && cudaMemsetAsync(g.E.p, 0, 8 * nE, st) == cudaSuccess &&
-         (nI == 0 ||
-          cudaMemcpyAsync(g.init.p, g.init_planes.data(), sizeof(Plane) * nI, cudaMemcpyHostToDevice, st) == cudaSuccess);
-    int32_t rc = ok ? SG_OK : SG_ECUDA;
-    if (rc == SG_OK && nI) rc = launch_planes_init(g.WG, g.init.as<Plane>(), nI, st);
-    if (rc == SG_OK)
-        rc = launch_sa_planes(g.WG, g.pl.as<Plane>(), g.ord.as<int>(), np, g.next.as<unsigned>(), unit,
-                              planes_blocks(g.WG, unit), st);
-    if (rc == SG_OK) rc = launch_planes_energy(g.WG, g.pl.as<Plane>(), np, g.E.as<unsigned long long>(), st);
-    if (rc == SG_OK && cudaMemcpyAsync(g.hE.p, g.E.p, 8 * nE, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    int32_t rc = grow_group(g, (size_t)np) ? SG_OK : SG_ENOMEM;
+    // uploads of newly admitted requests ran on their own streams
+    for (Request* q : g.reqs)
+        if (rc == SG_OK && q->need_init && cudaStreamWaitEvent(st, q->slot->ev, 0) != cudaSuccess) rc = SG_ECUDA;
+    if (rc == SG_OK &&
+        (cudaMemcpyAsync(g.pl, g.planes.data(), sizeof(Plane) * np, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync(g.ord, order.data(), sizeof(int) * np, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+         cudaMemsetAsync(g.next, 0, 4, st) != cudaSuccess || cudaMemsetAsync(g.E, 0, 8 * nE, st) != cudaSuccess ||
+         (nI && cudaMemcpyAsync(g.init, g.init_planes.data(), sizeof(Plane) * nI, cudaMemcpyHostToDevice, st) !=
+                    cudaSuccess)))
         rc = SG_ECUDA;
-    for (Request* q : g.reqs) q->need_init = false;
-    g.rc = rc;
-}
-
-// One round: every admitted request advances by one chunk of sweeps, then the
-// completion tests run at sweep counts that do not depend on the other requests.
-void run_round(sg_server* srv, const std::vector<Request*>& act)
-{
-    const int chunk = srv->cfg.chunk_sweeps;
-    // PT requests: replay their graphs, then read the running minimum
-    for (Request* q : act) {
-        if (q->req.kind != SG_REQ_PT || q->done) continue;
-        if (cudaGraphLaunch(q->graph, q->stream) != cudaSuccess ||
-            cudaMemcpyAsync(q->h_min, q->pt_min.p, sizeof(int32_t), cudaMemcpyDeviceToHost, q->stream) !=
-                cudaSuccess) {
-            cudaGetLastError();
-            q->result.status = SG_ECUDA;
-            q->done = true;
-        }
-    }
-    // SA requests: one launch per plane width, each on its own stream
-    for (SaGroup& g : srv->groups) {
+    if (rc == SG_OK && nI) rc = launch_planes_init(g.WG, static_cast<Plane*>(g.init), nI, st);
+    if (rc == SG_OK)
+        rc = launch_sa_planes(g.WG, static_cast<Plane*>(g.pl), static_cast<int*>(g.ord), np,
+                              static_cast<unsigned*>(g.next), unit, planes_blocks(g.WG, unit), st);
+    if (rc == SG_OK) rc = launch_planes_energy(g.WG, static_cast<Plane*>(g.pl), np, static_cast<unsigned long long*>(g.E), st);
+    if (rc == SG_OK && (cudaMemcpyAsync(g.hE, g.E, 8 * nE, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                        cudaEventRecord(g.ev, st) != cudaSuccess))
+        rc = SG_ECUDA;
+    if (rc != SG_OK) {
+        cudaGetLastError();
+        for (Request* q : g.reqs) fail_request(q, rc);
         g.reqs.clear();
-        for (Request* q : act)
-            if (q->req.kind == SG_REQ_SA && !q->done && q->WG == g.WG) g.reqs.push_back(q);
-        launch_sa_group(g, chunk);
+        return;
     }
-    for (SaGroup& g : srv->groups)
-        if (!g.reqs.empty() && cudaStreamSynchronize(g.st) != cudaSuccess) g.rc = SG_ECUDA;
-    for (Request* q : act)
-        if (q->req.kind == SG_REQ_PT && !q->done && cudaStreamSynchronize(q->stream) != cudaSuccess) {
-            q->result.status = SG_ECUDA;
-            q->done = true;
-        }
-    cudaGetLastError();
-    for (Request* q : act)
-        if (q->req.kind == SG_REQ_PT && !q->done) {
-            q->sweeps += chunk;
-            q->minE = std::min<int64_t>(q->minE, *q->h_min);
-        }
-    for (SaGroup& g : srv->groups) {
-        for (size_t a = 0; a < g.reqs.size(); ++a) {
-            Request* q = g.reqs[a];
-            if (g.rc != SG_OK) {
-                q->result.status = g.rc;
-                q->done = true;
-                continue;
-            }
-            const unsigned long long* E = g.hE.as<unsigned long long>();
-            for (int k = g.first[a]; k < g.first[a + 1]; ++k)
-                for (int rb = 0; rb < 4 * g.WG; ++rb)
-                    if (4 * g.planes[k].w0 + rb < q->req.width)
-                        q->minE = std::min<int64_t>(q->minE, (int64_t)(long long)E[(size_t)k * 4 * g.WG + rb]);
-            q->sweeps += g.steps[a];
-            q->in_restart += g.steps[a];
-            if (q->in_restart == q->req.sweeps_per_restart) {  // next round starts restart + 1
-                q->restart += 1;
-                q->in_restart = 0;
-                q->need_init = true;
-            }
-        }
+    for (Request* q : g.reqs) {
+        q->need_init = false;
+        q->inflight = true;
     }
-    for (Request* q : act) {
-        if (q->done) continue;
-        if (q->minE <= q->target) {
-            q->result.reached = 1;
-            q->done = true;
-        } else if (q->sweeps >= q->req.sweep_cap) {
-            q->done = true;
-        }
-    }
+    g.inflight = true;
 }
 
+// True once the group's launch has ended (and then folds it into its requests).
+bool poll_group(PlaneGroup& g)
+{
+    if (!g.inflight) return false;
+    const cudaError_t e = cudaEventQuery(g.ev);
+    if (e == cudaErrorNotReady) return false;
+    g.inflight = false;
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        for (Request* q : g.reqs) fail_request(q, SG_ECUDA);
+        return true;
+    }
+    for (size_t a = 0; a < g.reqs.size(); ++a) {
+        Request* q = g.reqs[a];
+        int64_t m = INT64_MAX;
+        for (int k = g.first[a]; k < g.first[a + 1]; ++k)
+            for (int rb = 0; rb < 4 * g.WG; ++rb)
+                if (4 * g.planes[k].w0 + rb < q->req.width)
+                    m = std::min<int64_t>(m, (int64_t)(long long)g.hE[(size_t)k * 4 * g.WG + rb]);
+        finish_chunk(q, m);
+    }
+    return true;
+}
+
+// Gives back a request's device state (stream-ordered: no device synchronisation) and
+// marks its result readable.  Caller holds the server mutex; the request is idle.
 void retire(sg_server* srv, Request* q)
 {
+    for (auto& kv : q->graphs) cudaGraphExecDestroy(kv.second);
+    q->graphs.clear();
+    if (q->mem) cudaFreeAsync(q->mem, q->slot->st);
+    q->mem = nullptr;
+    if (q->slot) srv->free_slots.push_back(q->slot);
+    q->slot = nullptr;
+    cudaGetLastError();
+    q->inst.reset();
+    q->thr.reset();
+    q->xt = ExchangeTables();
     q->t_done = Clock::now();
-    q->release();
     q->finished = true;
     if (q->admitted) srv->in_use -= q->bytes;
 }
@@ -499,8 +686,10 @@ void retire(sg_server* srv, Request* q)
 void worker_main(sg_server* srv)
 {
     cudaSetDevice(srv->device);
+    const int chunk = srv->cfg.chunk_sweeps;
     std::unique_lock<std::mutex> lock(srv->mu);
     for (;;) {
+        bool progress = false;
         // admission: FIFO while memory and slots allow
         while (!srv->stop && !srv->queue.empty() && (int)srv->active.size() < srv->cfg.max_active) {
             Request* q = srv->queue.front();
@@ -510,43 +699,69 @@ void worker_main(sg_server* srv)
             q->admitted = true;
             q->t_admit = Clock::now();
             lock.unlock();
-            const bool ok = admit_request(srv, q);
+            const int32_t rc = admit_request(srv, q);
             lock.lock();
-            if (!ok) {
+            progress = true;
+            if (rc != SG_OK) {
+                q->result.status = rc;
                 retire(srv, q);
                 srv->cv_done.notify_all();
                 continue;
             }
             srv->active.push_back(q);
         }
-        if (srv->stop && srv->active.empty()) break;
-        if (srv->active.empty()) {
-            srv->cv_work.wait_for(lock, std::chrono::milliseconds(50));
-            continue;
-        }
         for (Request* q : srv->active)
-            if (q->cancelled || srv->stop) {
-                q->result.status = SG_ECANCELED;
-                q->done = true;
-            }
+            if (q->cancelled || srv->stop) q->stopping = true;
         const std::vector<Request*> act = srv->active;
         lock.unlock();
-        run_round(srv, act);
-        lock.lock();
-        std::vector<Request*> keep;
-        for (Request* q : srv->active) {
-            if (!q->done && q->cancelled) {
+
+        // chunks that ended
+        for (Request* q : act)
+            if (q->inflight && q->mode != kPlanes && poll_own_chunk(q)) progress = true;
+        for (PlaneGroup& g : srv->groups)
+            if (poll_group(g)) progress = true;
+        for (Request* q : act)
+            if (q->stopping && !q->inflight && !q->done) {
                 q->result.status = SG_ECANCELED;
                 q->done = true;
             }
-            if (q->done)
+        // next chunks
+        for (Request* q : act)
+            if (!q->done && !q->inflight && q->mode != kPlanes) {
+                launch_own_chunk(q, chunk);
+                progress = true;
+            }
+        for (PlaneGroup& g : srv->groups)
+            if (!g.inflight) {
+                launch_group(g, act, chunk);
+                progress |= g.inflight;
+            }
+
+        lock.lock();
+        std::vector<Request*> keep;
+        bool retired = false;
+        for (Request* q : srv->active) {
+            if (q->done && !q->inflight) {
                 retire(srv, q);
-            else
+                retired = true;
+            } else {
                 keep.push_back(q);
+            }
         }
         srv->active.swap(keep);
-        srv->cv_done.notify_all();
+        if (retired) srv->cv_done.notify_all();
+        if (srv->stop && srv->active.empty()) break;
+        if (!progress && !retired) {
+            // idle: wake on a submit, cancel or stop; poll the device every 50 us while busy
+            if (srv->active.empty())
+                srv->cv_work.wait_for(lock, std::chrono::milliseconds(20));
+            else
+                srv->cv_work.wait_for(lock, std::chrono::microseconds(50));
+        }
     }
+    lock.unlock();
+    for (auto& s : srv->slots) cudaStreamSynchronize(s->st);
+    for (PlaneGroup& g : srv->groups) cudaStreamSynchronize(g.st);
 }
 
 void finish_result(Request* q)
@@ -585,26 +800,36 @@ using namespace sg;
 extern "C" int32_t sg_server_create(const sg_server_config* cfg, sg_server** out)
 {
     clear_error();
-    if (!cfg || !out || cfg->max_active < 1 || cfg->chunk_sweeps < 1 || cfg->queue_capacity < 1 ||
-        cfg->hbm_budget_bytes == 0) {
-        set_error("bad server config (max_active, chunk_sweeps, queue_capacity >= 1; budget > 0)");
+    if (!cfg || !out || cfg->max_active < 1 || cfg->max_active > 65536 || cfg->chunk_sweeps < 1 ||
+        cfg->queue_capacity < 1 || cfg->hbm_budget_bytes == 0) {
+        set_error("bad server config (max_active in [1, 65536], chunk_sweeps and queue_capacity >= 1, "
+                  "budget > 0)");
         return SG_EINVAL;
     }
     sg_server* srv = new (std::nothrow) sg_server;
     if (!srv) return SG_ENOMEM;
     srv->cfg = *cfg;
-    bool ok = cudaGetDevice(&srv->device) == cudaSuccess &&
-              cudaStreamCreateWithFlags(&srv->setup_stream, cudaStreamNonBlocking) == cudaSuccess;
+    bool ok = cudaGetDevice(&srv->device) == cudaSuccess;
+    if (ok) {
+        // the requests' device memory: a pool of its own that keeps up to the budget cached
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = srv->device;
+        ok = cudaMemPoolCreate(&srv->pool, &props) == cudaSuccess;
+        uint64_t keep = cfg->hbm_budget_bytes;
+        ok = ok && cudaMemPoolSetAttribute(srv->pool, cudaMemPoolAttrReleaseThreshold, &keep) == cudaSuccess;
+    }
     const int widths[3] = {4, 2, 1};
     for (int k = 0; k < 3 && ok; ++k) {
         srv->groups[k].WG = widths[k];
-        srv->groups[k].hE.host = true;
-        ok = cudaStreamCreateWithFlags(&srv->groups[k].st, cudaStreamNonBlocking) == cudaSuccess;
+        ok = cudaStreamCreateWithFlags(&srv->groups[k].st, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&srv->groups[k].ev, cudaEventDisableTiming) == cudaSuccess;
     }
     if (!ok) {
         cudaGetLastError();
         delete srv;
-        set_error("server: creating streams failed");
+        set_error("server: CUDA set-up failed (device, memory pool or streams)");
         return SG_ECUDA;
     }
     try {
@@ -630,9 +855,14 @@ extern "C" int32_t sg_submit(sg_server* srv, const sg_request* req, uint64_t* ti
                   "sweep_cap >= 1, SA sweeps_per_restart >= 1 and schedule, class weights)", SG_LMAX);
         return SG_EINVAL;
     }
-    const size_t bytes = request_bytes(*req);
-    if (bytes > srv->cfg.hbm_budget_bytes) {
-        set_error("request needs %zu bytes of device memory, more than the server budget", bytes);
+    auto q = std::make_unique<Request>();
+    q->t_submit = Clock::now();
+    q->req = *req;
+    q->result.status = SG_OK;
+    int32_t rc = prepare_request(srv->schedules, q.get());
+    if (rc != SG_OK) return rc;
+    if (q->bytes > srv->cfg.hbm_budget_bytes) {
+        set_error("request needs %zu bytes of device memory, more than the server budget", q->bytes);
         return SG_ENOMEM;
     }
     std::lock_guard<std::mutex> lock(srv->mu);
@@ -644,13 +874,7 @@ extern "C" int32_t sg_submit(sg_server* srv, const sg_request* req, uint64_t* ti
         set_error("queue full (%d waiting)", (int)srv->queue.size());
         return SG_EBUSY;
     }
-    auto q = std::make_unique<Request>();
     q->ticket = srv->next_ticket++;
-    q->req = *req;
-    q->bytes = bytes;
-    q->t_submit = Clock::now();
-    q->result.status = SG_OK;
-    q->WG = largest_wg((req->width + 3) / 4);
     srv->queue.push_back(q.get());
     *ticket = q->ticket;
     srv->all.emplace(q->ticket, std::move(q));
@@ -700,13 +924,14 @@ extern "C" int32_t sg_cancel(sg_server* srv, uint64_t ticket)
     Request* q = it->second.get();
     if (q->finished) return SG_OK;
     auto pos = std::find(srv->queue.begin(), srv->queue.end(), q);
-    if (pos != srv->queue.end()) {
+    if (pos != srv->queue.end()) {  // waiting: no device state yet
         srv->queue.erase(pos);
         q->result.status = SG_ECANCELED;
         retire(srv, q);
         srv->cv_done.notify_all();
     } else {
-        q->cancelled = true;  // admitted: the worker stops it at the next round boundary
+        q->cancelled = true;  // admitted: the worker stops it when its chunk ends
+        srv->cv_work.notify_one();
     }
     return SG_OK;
 }
@@ -729,4 +954,19 @@ extern "C" int32_t sg_server_destroy(sg_server* srv)
     if (srv->worker.joinable()) srv->worker.join();
     delete srv;
     return SG_OK;
+}
+
+extern "C" int32_t sg_request_bytes(const sg_request* req, uint64_t* bytes)
+{
+    clear_error();
+    if (!req || !bytes || !valid_request(*req)) {
+        set_error("bad request");
+        return SG_EINVAL;
+    }
+    ScheduleCache cache;
+    Request q;
+    q.req = *req;
+    const int32_t rc = prepare_request(cache, &q);
+    if (rc == SG_OK) *bytes = q.bytes;
+    return rc;
 }

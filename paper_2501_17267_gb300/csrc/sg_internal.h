@@ -162,11 +162,13 @@ int32_t launch_half_sweep_pt(int8_t* spins, const uint2* const* j6_ptrs,
 // sweep.cu: row-mapped sweep kernel (used whenever it supports the word count)
 bool rows_kernel_supports(int Wn);
 // SA variant keeps no incremental energies (the run recomputes them at the end);
-// unit_j: every coupling of the group has |J| = 1.
+// unit_j: every coupling of the group has |J| = 1.  With sweep_base the sweep index is
+// *sweep_base + sweep, read on the device, and thr_row is the whole [S][kThrRow] table.
 int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_row, bool unit_j, int I, int L, int Wn, int R,
-                             uint32_t sweep, int colour, cudaStream_t st);
+                             uint32_t sweep, int colour, cudaStream_t st,
+                             const uint32_t* sweep_base = nullptr);
 // xch != nullptr: the launch may also perform the PT exchange (last block per instance);
 // *fused reports whether it did.  done: [I] zeroed counters.
 int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,

@@ -39,7 +39,7 @@ struct SweepArgs {
     const uint2* const* j6_ptrs;     // per instance: [N] records of the six int8 couplings
     const uint8_t* const* j1_ptrs;   // per instance: [N] sign bits (used when all |J| = 1)
     const RunKeys* keys;
-    const uint32_t* thr;          // SA: one row of kThrRow; PT: [K][kThrRow]
+    const uint32_t* thr;          // SA: one row of kThrRow ([S][kThrRow] with sweep_base); PT: [K][kThrRow]
     const uint8_t* rung_of_slot;  // PT: [I][Rp]
     int32_t* E;                   // PT: [I][Rp] energies, updated
     int L, Wn, Rvalid, G, rows_per_thread;
@@ -76,7 +76,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
         }
         for (int q = tid; q < Rp; q += nthreads) s_dE[q] = 0;
     } else {
-        for (int q = tid; q < kThrRow; q += nthreads) s_thr[q] = a.thr[q];
+        // with a device sweep index, thr is the run's [S][kThrRow] schedule table
+        const uint32_t* row = a.sweep_base ? a.thr + (size_t)sweep * kThrRow : a.thr;
+        for (int q = tid; q < kThrRow; q += nthreads) s_thr[q] = row[q];
     }
     __syncthreads();
 
@@ -348,7 +350,7 @@ bool rows_kernel_supports(int Wn)
 int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_row, bool unit_j, int I, int L, int Wn, int R,
-                             uint32_t sweep, int colour, cudaStream_t st)
+                             uint32_t sweep, int colour, cudaStream_t st, const uint32_t* sweep_base)
 {
     SweepArgs a{};
     a.spins = reinterpret_cast<uint32_t*>(spins);
@@ -361,6 +363,7 @@ int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
     a.Rvalid = R;
     a.sweep = sweep;
     a.colour = colour;
+    a.sweep_base = sweep_base;
     return launch_rows<false>(a, I, unit_j, false, nullptr, st);
 }
 

@@ -107,6 +107,7 @@ _SIGS = {
     "sg_poll": [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(Result)],
     "sg_cancel": [_P, ctypes.c_uint64],
     "sg_server_destroy": [_P],
+    "sg_request_bytes": [ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
 }
 for _name, _args in _SIGS.items():
     _fn = getattr(_lib, _name)
@@ -354,6 +355,13 @@ def request(kind: int, L: int, seed: int, width: int, beta0: float, beta1: float
     d = InstanceDesc(L, int(bool(gauge)), seed, (ctypes.c_double * 3)(*class_prob))
     return Request(kind, d, width, sweeps_per_restart, beta0, beta1, schedule, run_seed, eps_target,
                    sweep_cap)
+
+
+def request_bytes(req: Request) -> int:
+    """Device memory a server holds for `req` while it runs (what admission counts)."""
+    b = ctypes.c_uint64()
+    _check(_lib.sg_request_bytes(ctypes.byref(req), ctypes.byref(b)))
+    return int(b.value)
 
 
 class Server:

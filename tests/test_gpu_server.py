@@ -91,7 +91,9 @@ def test_pt_request_matches_pt_run(sg):
 @pytest.mark.parametrize("R", [4, 8, 12, 32])  # plane widths 1, 2, 1 (three planes), 4 words
 def test_sa_request_matches_sa_run_restarts(sg, R):
     S = 30
-    for L, eps, cap in [(4, 0.0, 3 * S), (8, 0.0, 4 * S), (12, 0.02, 2 * S)]:
+    # L <= 16 run in the shared plane launch, larger lattices as multi-block sweeps
+    for L, eps, cap in [(4, 0.0, 3 * S), (8, 0.0, 4 * S), (12, 0.02, 2 * S), (20, 0.0, 2 * S),
+                        (24, 0.01, 3 * S)]:
         req = sg.request(sg.SG_REQ_SA, L, seed=500 + L, width=R, beta0=0.1, beta1=3.0,
                          eps_target=eps, sweep_cap=cap, run_seed=9 + R, sweeps_per_restart=S,
                          schedule=sg.SG_SCHEDULE_GEOMETRIC)
@@ -114,8 +116,8 @@ def test_sa_request_restart0_matches_oracle(sg):
 
 def _mix(sg):
     reqs = []
-    for k in range(12):
-        L = (4, 6, 8, 10, 12, 16)[k % 6]
+    for k in range(16):
+        L = (4, 6, 8, 10, 12, 16, 20, 24)[k % 8]
         if k % 3 == 2:
             reqs.append(sg.request(sg.SG_REQ_PT, L, seed=9000 + k, width=(8, 12)[k % 2],
                                    beta0=0.2, beta1=3.0, eps_target=0.0, sweep_cap=90, run_seed=k))
@@ -138,16 +140,24 @@ def test_results_identical_alone_and_mixed(sg):
 
 
 def test_budget_limits_admission(sg):
-    """A budget that fits one request at a time still serves all of them, in order."""
-    reqs = [sg.request(sg.SG_REQ_PT, 8, seed=70 + k, width=8, beta0=0.2, beta1=3.0,
-                       eps_target=0.0, sweep_cap=40, run_seed=k) for k in range(4)]
-    one = 8 * 1024 * 1024
-    res = _solve(sg, reqs, 20, budget=one)
+    """A budget that fits one request at a time still serves all of them, one after the
+    other: each is admitted only after the previous one has finished."""
+    import time
+    reqs = [sg.request(sg.SG_REQ_PT, 16, seed=70 + k, width=16, beta0=0.2, beta1=3.0,
+                       eps_target=0.0, sweep_cap=200, run_seed=k) for k in range(4)]
+    one = max(sg.request_bytes(r) for r in reqs)
+    with sg.Server(one + one // 2, max_active=8, chunk_sweeps=20) as srv:
+        tickets, t_sub = [], []
+        for r in reqs:
+            t_sub.append(time.perf_counter())
+            tickets.append(srv.submit(r))
+        res = [srv.poll(t, timeout_ms=-1) for t in tickets]
     ref = _solve(sg, reqs, 20)
     for a, b in zip(res, ref):
         assert _key(a) == _key(b)
-    for a, b in zip(res, res[1:]):
-        assert b["queue_s"] >= a["queue_s"] - 1e-3
+    for k in range(1, len(res)):
+        # admitted (t_sub[k] + queue_s) no earlier than the previous one finished
+        assert t_sub[k] + res[k]["queue_s"] >= t_sub[k - 1] + res[k - 1]["total_s"] - 2e-3
 
 
 def test_cancel_queued_and_running(sg):
