@@ -196,6 +196,124 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- serving leg
+
+def _serving_request(sg, w, item, sa_cap, pt_cap):
+    if item["kind"] == "SA":
+        return sg.request(sg.SG_REQ_SA, item["L"], item["seed"], w.sa_replicas, w.sa_beta0, w.sa_beta1,
+                          w.eps_target, sa_cap, run_seed=item["run_seed"],
+                          sweeps_per_restart=w.sa_sweeps_per_restart, schedule=sg.SG_SCHEDULE_LINEAR,
+                          class_prob=w.class_prob)
+    return sg.request(sg.SG_REQ_PT, item["L"], item["seed"], w.pt_temps, w.pt_beta_min, w.pt_beta_max,
+                      w.eps_target, pt_cap, run_seed=item["run_seed"], class_prob=w.class_prob)
+
+
+def _pcts(xs):
+    import numpy as np
+    if not xs:
+        return {"p50": None, "p95": None, "p99": None}
+    a = np.asarray(xs, dtype=np.float64)
+    return {"p50": float(np.percentile(a, 50)), "p95": float(np.percentile(a, 95)),
+            "p99": float(np.percentile(a, 99))}
+
+
+def run_served(sg, w, stream, sa_cap, pt_cap, chunk, max_active, budget):
+    """The stream through the continuously batched server: each request is submitted at
+    its arrival time; latency = submit lateness + the server's submit-to-done time."""
+    reqs = [_serving_request(sg, w, it, sa_cap, pt_cap) for it in stream]
+    width = {"SA": w.sa_replicas, "PT": w.pt_temps}
+    with sg.Server(budget, max_active=max_active, chunk_sweeps=chunk, queue_capacity=1 << 20) as srv:
+        t0 = time.perf_counter()
+        tickets, late = [], []
+        for it, r in zip(stream, reqs):
+            now = time.perf_counter() - t0
+            if it["t"] > now:
+                time.sleep(it["t"] - now)
+            ts = time.perf_counter() - t0
+            tickets.append(srv.submit(r))
+            late.append(ts - it["t"])
+        res = [srv.poll(t, -1) for t in tickets]
+    lat = [lt + r["total_s"] for lt, r in zip(late, res)]
+    ends = [it["t"] + x for it, x in zip(stream, lat)]
+    makespan = max(ends) if ends else 0.0
+    reached = [x for x, r in zip(lat, res) if r["status"] == 0 and r["reached"]]
+    attempts = sum(r["sweeps"] * it["L"] ** 3 * width[it["kind"]] for it, r in zip(stream, res))
+    by_kind = {}
+    for kind in ("SA", "PT"):
+        ks = [(x, r) for x, r, it in zip(lat, res, stream) if it["kind"] == kind]
+        by_kind[kind] = {"requests": len(ks), "tte_s": _pcts([x for x, r in ks if r["reached"]]),
+                         "censored": sum(1 for x, r in ks if not r["reached"]) / max(len(ks), 1)}
+    return {"requests": len(stream), "errors": sum(1 for r in res if r["status"] != 0),
+            "tte_s": _pcts(reached), "latency_all_s": _pcts(lat),
+            "censored_fraction": 1 - len(reached) / max(len(stream), 1),
+            "throughput_req_s": len(stream) / makespan if makespan else None,
+            "attempts_per_s": attempts / makespan if makespan else None,
+            "makespan_s": makespan, "max_submit_late_s": max(late) if late else 0.0,
+            "queue_s": _pcts([r["queue_s"] for r in res]), "by_kind": by_kind}
+
+
+def run_one_at_a_time(sg, w, stream, sa_cap, pt_cap, limit_s):
+    """The same stream served the plain way: one request at a time in arrival order, each
+    through the one-shot calls with one instance per launch -- SA as successive sg_sa_run
+    restarts (instance_id = restart) checked after each, PT as one sg_pt_run of the cap.
+    Requests not finished within limit_s count as unfinished, their latency bounded below
+    by limit_s - arrival."""
+    import numpy as np
+    t0 = time.perf_counter()
+    lat, reached, unfinished = [], [], 0
+    for it in stream:
+        now = time.perf_counter() - t0
+        if now > limit_s:
+            unfinished += 1
+            lat.append(limit_s - it["t"])
+            continue
+        if it["t"] > now:
+            time.sleep(it["t"] - now)
+        inst = sg.Instance.create(it["L"], it["seed"], w.class_prob, True)
+        target = inst.e_gs + int(np.floor(w.eps_target * abs(inst.e_gs)))
+        ok = False
+        if it["kind"] == "SA":
+            S, done, k = w.sa_sweeps_per_restart, 0, 0
+            while done < sa_cap and not ok:
+                n = min(S, sa_cap - done)
+                r = sg.sa_run(inst, w.sa_replicas, n, w.sa_beta0, w.sa_beta1, "linear",
+                              seed=it["run_seed"], instance_id=k)
+                ok = int(r["E"].min()) <= target
+                done += n
+                k += 1
+        else:
+            r = sg.pt_run(inst, w.pt_temps, pt_cap, w.pt_beta_min, w.pt_beta_max, seed=it["run_seed"])
+            ok = r["minE"] <= target
+        inst.close()
+        x = time.perf_counter() - t0 - it["t"]
+        lat.append(x)
+        if ok:
+            reached.append(x)
+    return {"requests": len(stream), "unfinished_at_limit": unfinished, "limit_s": limit_s,
+            "tte_s": _pcts(reached), "latency_all_s": _pcts(lat),
+            "censored_fraction": 1 - len(reached) / max(len(stream), 1)}
+
+
+def serving_leg(sg, args, w):
+    stream = w.stream(args.serve_seconds)
+    sa_cap = args.sa_cap or w.sa_sweep_cap
+    pt_cap = args.pt_cap or w.pt_sweep_cap
+    budget = int(args.serve_budget_gb * (1 << 30))
+    served = run_served(sg, w, stream, sa_cap, pt_cap, args.serve_chunk, args.serve_max_active, budget)
+    out = {"workload": w.name, "rate_per_s": w.rate_per_s, "window_s": args.serve_seconds,
+           "eps_target": w.eps_target, "sa_sweep_cap": sa_cap, "pt_sweep_cap": pt_cap,
+           "chunk_sweeps": args.serve_chunk, "max_active": args.serve_max_active,
+           "hbm_budget_bytes": budget, "served": served}
+    if args.serve_baseline_seconds > 0:
+        base = [it for it in stream if it["t"] < args.serve_baseline_seconds]
+        out["one_at_a_time"] = run_one_at_a_time(sg, w, base, sa_cap, pt_cap, args.serve_baseline_limit)
+        out["one_at_a_time"]["window_s"] = args.serve_baseline_seconds
+        if args.serve_baseline_seconds < args.serve_seconds:
+            sub = run_served(sg, w, base, sa_cap, pt_cap, args.serve_chunk, args.serve_max_active, budget)
+            out["served_same_window"] = sub
+    return out
+
+
 # ---------------------------------------------------------------- GPU leg
 
 def main():
@@ -210,7 +328,27 @@ def main():
     ap.add_argument("--ref-sweeps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--workload", default="pt", choices=["pt", "serving"],
+                    help="pt: the PT throughput line (with a short serving leg); serving: the "
+                         "serving stream alone")
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving leg of the pt line")
+    ap.add_argument("--serve-seconds", type=float, default=None,
+                    help="arrival window (default: 10 s in the pt line, the workload's 60 s alone)")
+    ap.add_argument("--serve-baseline-seconds", type=float, default=None,
+                    help="window of the one-request-at-a-time comparison (default 5 s / 10 s)")
+    ap.add_argument("--serve-baseline-limit", type=float, default=30.0,
+                    help="wall-clock limit of the comparison arm")
+    ap.add_argument("--serve-chunk", type=int, default=100)
+    ap.add_argument("--serve-max-active", type=int, default=512)
+    ap.add_argument("--serve-budget-gb", type=float, default=160.0)
+    ap.add_argument("--sa-cap", type=int, default=0)
+    ap.add_argument("--pt-cap", type=int, default=0)
     args = ap.parse_args()
+    alone = args.workload == "serving"
+    if args.serve_seconds is None:
+        args.serve_seconds = wl.SERVING.duration_s if alone else 10.0
+    if args.serve_baseline_seconds is None:
+        args.serve_baseline_seconds = 10.0 if alone else 5.0
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -244,6 +382,22 @@ def main():
     def barrier():
         if world > 1:
             torch.distributed.barrier()
+
+    if alone:
+        if rank == 0:
+            res = serving_leg(sg, args, wl.SERVING)
+            sv = res["served"]
+            line = {"metric": "served TTe at eps <= 1% (p50)", "value": sv["tte_s"]["p50"], "unit": "s",
+                    "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak",
+                    "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+                    "config": {"workload": wl.SERVING.name, "rate_per_s": wl.SERVING.rate_per_s,
+                               "window_s": args.serve_seconds},
+                    "serving": res}
+            print(json.dumps(line), flush=True)
+        barrier()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
 
     S = args.sweeps
     base = rank * WORK.instances
@@ -340,6 +494,11 @@ def main():
                "h2d_bytes_per_step": WORK.instances * 3 * WORK.L ** 3,
                "d2h_bytes_per_step": WORK.instances * (8 * K + 4 * K + 8 * (K - 1) + 8 + 8)}
 
+    serving = None
+    if rank == 0 and not args.no_serve:
+        serving = serving_leg(sg, args, wl.SERVING)
+    barrier()
+
     if rank == 0:
         mins = [o["min_eps"] for o in out]
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -349,7 +508,7 @@ def main():
                 "pct_hbm_roofline": (value * BYTES_PER_ATTEMPT / 1e9) / peak,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "min_eps_mean": float(np.mean(mins)),
-                "kernel_stats": st}
+                "kernel_stats": st, "serving": serving}
         if S != WORK.sweeps:
             line["config"]["sweeps"] = S
             line["note"] = f"reduced sweeps ({S}) -- not the workload's number"

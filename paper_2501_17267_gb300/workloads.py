@@ -91,10 +91,35 @@ class ServingWorkload:
     pt_temps: int
     pt_beta_min: float
     pt_beta_max: float
-    sweep_cap: int
+    sa_sweep_cap: int
+    pt_sweep_cap: int
     eps_target: float
+    sa_beta0: float = 0.1
+    sa_beta1: float = 3.0
+    sa_fraction: float = 0.5
     arrival_seed: int = 2024
     class_prob: tuple = UNIFORM
+
+    def instance_seed(self, k: int) -> int:
+        return self.index * 2 ** 32 + k
+
+    def stream(self, seconds: float | None = None):
+        """The arrival stream over [0, seconds): Poisson arrivals at rate_per_s, each with
+        L uniform over L_choices (L_large with probability large_fraction), SA with
+        probability sa_fraction else PT, instance seed index*2^32 + k and run seed k for
+        the k-th arrival.  Deterministic in arrival_seed."""
+        T = self.duration_s if seconds is None else seconds
+        rng = np.random.default_rng(self.arrival_seed)
+        out, t, k = [], 0.0, 0
+        while True:
+            t += float(rng.exponential(1.0 / self.rate_per_s))
+            if t >= T:
+                return out
+            big = rng.random() < self.large_fraction
+            L = self.L_large if big else int(rng.choice(np.array(self.L_choices)))
+            kind = "SA" if rng.random() < self.sa_fraction else "PT"
+            out.append({"t": t, "L": L, "kind": kind, "seed": self.instance_seed(k), "run_seed": k})
+            k += 1
 
 
 # L=4, one instance, 8 replicas, 1000 sweeps, beta linear 0.1 -> 3.0, run seed 0
@@ -106,9 +131,12 @@ PT_L64 = PTWorkload("pt_L64_I16_K32_S10000", 2, 64, 16, 32, 10000, 0.2, 3.0)
 # 512 instances, L uniform in {8,12,16,24,32,48}, 64 replicas, sweeps in {100,1000,10000}
 BATCHED = BatchedWorkload("sa_batched_I512_R64", 3, 512, (8, 12, 16, 24, 32, 48), 64,
                           (100, 1000, 10000), 0.1, 3.0)
-# Poisson 200 req/s for 60 s, L in {8..64 step 8} plus 1% at L=128, SA/PT 50/50
+# Poisson 200 req/s for 60 s, L in {8..64 step 8} plus 1% at L=128, SA/PT 50/50, target
+# eps <= 1%; SA: 32 replicas, restarts of 1000 sweeps (beta linear 0.1 -> 3.0); PT: 32
+# temperatures geometric 0.2 -> 3.0; cap 1000 sweeps for both (one SA restart): at 2000
+# the offered load is about twice what one GPU sweeps
 SERVING = ServingWorkload("serve_poisson200", 4, 200.0, 60.0, tuple(range(8, 65, 8)), 128,
-                          0.01, 32, 1000, 32, 0.2, 3.0, 100000, 0.01)
+                          0.01, 32, 1000, 32, 0.2, 3.0, 1000, 1000, 0.01)
 
 ALL = [SA_L4, SA_L16, PT_L64, BATCHED, SERVING]
 
