@@ -459,7 +459,7 @@ int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs,
                                  unit_j, I, L, Wn, R, sweep, colour, st);
     if (rows_kernel_supports(Wn))
         return launch_sweep_rows_sa(spins, j6_ptrs, j1_ptrs, keys, thr_row, unit_j, I, L, Wn, R, sweep,
-                                    colour, st);
+                                    colour, st, nullptr, status);
     const int64_t N = (int64_t)L * L * L;
     dim3 grid(sweep_grid_x((N / 2) * Wn, Wn), I);
     half_sweep_kernel<false><<<grid, kBlock, 0, st>>>((uint32_t*)spins, j6_ptrs, keys, thr_row,
@@ -480,7 +480,7 @@ int32_t launch_half_sweep_pt(int8_t* spins, const uint2* const* j6_ptrs,
                                  true, unit_j, I, L, Wn, K, sweep, colour, st);
     if (rows_kernel_supports(Wn))
         return launch_sweep_rows_pt(spins, j6_ptrs, j1_ptrs, keys, thr_rungs, rung_of_slot, E, unit_j,
-                                    I, L, Wn, K, sweep, colour, xch, done, fused, st);
+                                    I, L, Wn, K, sweep, colour, xch, done, fused, st, nullptr, status);
     const int64_t N = (int64_t)L * L * L;
     dim3 grid(sweep_grid_x((N / 2) * Wn, Wn), I);
     half_sweep_kernel<true><<<grid, kBlock, 0, st>>>((uint32_t*)spins, j6_ptrs, keys, thr_rungs,

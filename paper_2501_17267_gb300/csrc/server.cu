@@ -73,7 +73,7 @@ enum Mode { kPlanes = 0, kRowsSA = 1, kPT = 2 };
 struct Slot {
     cudaStream_t st = nullptr;
     cudaEvent_t ev = nullptr;
-    long long* h_out = nullptr;  // pinned: [0] min energy of the last chunk
+    long long* h_out = nullptr;  // pinned: [0] min energy of the last chunk, [1] its status word
 };
 
 size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
@@ -82,7 +82,7 @@ size_t align_up(size_t v) { return (v + 255) & ~(size_t)255; }
 struct Layout {
     size_t j6 = 0, j1 = 0, J3 = 0, spins = 0, thr = 0, keys = 0, jp = 0, base = 0, E = 0, E64 = 0,
            perm = 0, inv = 0, acc = 0, minE = 0, done = 0, xtab = 0, xoff = 0, xlen = 0, xtail = 0,
-           out = 0, total = 0;
+           out = 0, status = 0, total = 0;
 };
 
 struct Request {
@@ -147,6 +147,7 @@ Layout layout_of(const Request& q)
         y.base = take(4);
         y.E64 = take(8 * Rp);
         y.out = take(8);
+        y.status = take(4);
     } else {
         const size_t K = (size_t)q.req.width, Kp = std::max<size_t>(K - 1, 1);
         y.thr = take(4 * q.thr->size());
@@ -165,6 +166,7 @@ Layout layout_of(const Request& q)
         y.xlen = take(4 * q.xt.len.size());
         y.xtail = take(4 * q.xt.tail.size());
         y.out = take(8);
+        y.status = take(4);
     }
     y.total = o;
     return y;
@@ -360,6 +362,7 @@ int32_t admit_request(sg_server* srv, Request* q)
     const void* jp[2] = {q->at<void>(y.j6), q->at<void>(y.j1)};
     SG_TRY_CUDA(cudaMemcpyAsync(q->at<void>(y.jp), jp, sizeof(jp), cudaMemcpyHostToDevice, st));
     SG_TRY_CUDA(cudaMemsetAsync(q->at<void>(y.base), 0, 4, st));
+    SG_TRY_CUDA(cudaMemsetAsync(q->at<void>(y.status), 0, 4, st));
     if (q->mode == kRowsSA) return SG_OK;
     // PT: keys, exchange tables, initial spins and energies, the identity permutation
     const RunKeys key{(uint32_t)q->req.seed, (uint32_t)(q->req.seed >> 32)};
@@ -396,6 +399,7 @@ int32_t capture_chunk(Request* q, int n, cudaGraphExec_t* out)
     uint32_t* base = q->at<uint32_t>(y.base);
     const uint32_t* thr = q->at<uint32_t>(y.thr);
     const bool unit = q->inst->unit_couplings;
+    int* status = q->at<int>(y.status);
     ExchangeArgs xa{};
     if (q->mode == kPT) {
         xa.keys = kp;
@@ -418,16 +422,16 @@ int32_t capture_chunk(Request* q, int n, cudaGraphExec_t* out)
         if (q->mode == kRowsSA) {
             for (int colour = 0; colour < 2 && rc == SG_OK; ++colour)
                 rc = launch_sweep_rows_sa(spins, j6p, j1p, kp, thr, unit, 1, q->L, q->Wn, q->req.width,
-                                          (uint32_t)c, colour, st, base);
+                                          (uint32_t)c, colour, st, base, status);
         } else {
             bool fused = false;
             rc = launch_sweep_rows_pt(spins, j6p, j1p, kp, thr, xa.rung_of_slot, xa.E, unit, 1, q->L, q->Wn,
                                       q->req.width, (uint32_t)c, 0, nullptr, q->at<unsigned>(y.done), nullptr,
-                                      st, base);
+                                      st, base, status);
             if (rc == SG_OK)
                 rc = launch_sweep_rows_pt(spins, j6p, j1p, kp, thr, xa.rung_of_slot, xa.E, unit, 1, q->L,
                                           q->Wn, q->req.width, (uint32_t)c, 1, &xa, q->at<unsigned>(y.done),
-                                          &fused, st, base);
+                                          &fused, st, base, status);
             if (rc == SG_OK && !fused) rc = launch_pt_exchange(xa, 1, (uint32_t)c, st);
         }
     }
@@ -443,7 +447,8 @@ int32_t capture_chunk(Request* q, int n, cudaGraphExec_t* out)
             widen_kernel<<<1, 1, 0, st>>>(q->at<int32_t>(y.minE), q->at<long long>(y.out));
         }
         if (cudaGetLastError() != cudaSuccess ||
-            cudaMemcpyAsync(q->slot->h_out, q->at<void>(y.out), 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            cudaMemcpyAsync(q->slot->h_out, q->at<void>(y.out), 8, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+            cudaMemcpyAsync(q->slot->h_out + 1, status, 4, cudaMemcpyDeviceToHost, st) != cudaSuccess)
             rc = SG_ECUDA;
     }
     cudaGraph_t g = nullptr;
@@ -538,7 +543,11 @@ bool poll_own_chunk(Request* q)
         fail_request(q, SG_ECUDA);
         return true;
     }
-    finish_chunk(q, *q->slot->h_out);
+    if (*reinterpret_cast<const int*>(q->slot->h_out + 1) != 0) {  // a bounded device wait gave up
+        fail_request(q, SG_ETIMEOUT);
+        return true;
+    }
+    finish_chunk(q, q->slot->h_out[0]);
     return true;
 }
 

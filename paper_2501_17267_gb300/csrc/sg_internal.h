@@ -168,15 +168,16 @@ int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_row, bool unit_j, int I, int L, int Wn, int R,
                              uint32_t sweep, int colour, cudaStream_t st,
-                             const uint32_t* sweep_base = nullptr);
+                             const uint32_t* sweep_base = nullptr, int* status = nullptr);
 // xch != nullptr: the launch may also perform the PT exchange (last block per instance);
-// *fused reports whether it did.  done: [I] zeroed counters.
+// *fused reports whether it did.  done: [I] zeroed counters.  status (optional): set to
+// SG_ETIMEOUT when a bounded wait of the staged variant gives up.
 int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
                              const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st,
-                             const uint32_t* sweep_base = nullptr);
+                             const uint32_t* sweep_base = nullptr, int* status = nullptr);
 // tile.cu: shared-memory streaming sweep (used when it supports the shape)
 bool tile_kernel_supports(int I, int L, int Wn);
 int32_t launch_sweep_tile(int8_t* spins, const uint2* const* j6_ptrs, const uint8_t* const* j1_ptrs,

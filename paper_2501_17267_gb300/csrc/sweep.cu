@@ -25,6 +25,7 @@
 #include <stdlib.h>
 
 #include "exchange.cuh"
+#include "async_copy.cuh"
 #include "metropolis.cuh"
 #include "philox.cuh"
 #include "sg_internal.h"
@@ -33,6 +34,10 @@ namespace sg {
 namespace {
 
 constexpr int kThrStride = 17;   // per-slot threshold row stride in shared memory (bank spread)
+
+// Words of the staged PT variant's threshold table in dynamic shared memory (Rp slots),
+// rounded so that the row buffers after it stay 128-byte aligned.
+__host__ __device__ constexpr int staged_thr_words(int Rp) { return (Rp * kThrStride + 31) & ~31; }
 
 struct SweepArgs {
     uint32_t* spins;
@@ -49,14 +54,25 @@ struct SweepArgs {
     ExchangeArgs x;               // PT exchange performed by the last block of each instance
     unsigned* done;               // [I] blocks finished in this launch (reset by the last one)
     const uint32_t* sweep_base;   // if set, the sweep index is *sweep_base + sweep
+    int* status;                  // staged variant: set to SG_ETIMEOUT when a copy wait gives up
+    int segw;                     // staged variant: words of one half row, (L/2) * Wn
 };
 
+// NST > 0: the staged variant.  Each warp owns one row at a time (blockDim.x == 32, one
+// site per thread) and keeps NST rows in flight: for row (y, z) the six half rows it
+// reads -- its own sites, their x neighbours, and the matching halves of rows y+-1 and
+// z+-1 -- arrive in shared memory by bulk asynchronous copies that complete on the
+// warp's mbarrier for that ring slot, issued NST rows ahead of use.  The updated spins
+// go straight back to global memory; a half sweep never reads what it writes.
 template <bool PT, bool UNITJ, int WG, int CH, bool PAD, int MINB = 2, bool DRAW = false,
-          bool XCH = false>
+          bool XCH = false, int NST = 0>
 __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a)
 {
-    __shared__ uint32_t s_thr[PT ? 256 * kThrStride : kThrRow];
+    // staged PT: the slot thresholds live at the start of the dynamic array, sized to Rp
+    __shared__ uint32_t s_thr_fixed[PT ? (NST > 0 ? 1 : 256 * kThrStride) : kThrRow];
     __shared__ int s_dE[PT ? 256 : 1];
+    extern __shared__ __align__(128) uint32_t s_stage[];  // NST > 0: [thr][TY][NST][6][segw]
+    __shared__ uint64_t s_bar[NST > 0 ? 8 * NST : 1];
 
     const int inst = blockIdx.y;
     const int L = a.L, Wn = a.Wn, G = a.G;
@@ -68,6 +84,8 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
     uint32_t* __restrict__ s = a.spins + (size_t)inst * (size_t)LL * L * Wn;
     const int nthreads = blockDim.x * blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
+    uint32_t* s_thr = (PT && NST > 0) ? s_stage : s_thr_fixed;
+    const int thr_words = (PT && NST > 0) ? staged_thr_words(Rp) : 0;
 
     if (PT) {
         for (int q = tid; q < Rp * kThrRow; q += nthreads) {
@@ -79,6 +97,12 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
         // with a device sweep index, thr is the run's [S][kThrRow] schedule table
         const uint32_t* row = a.sweep_base ? a.thr + (size_t)sweep * kThrRow : a.thr;
         for (int q = tid; q < kThrRow; q += nthreads) s_thr[q] = row[q];
+    }
+    if constexpr (NST > 0) {
+        if (threadIdx.x == 0) {
+            for (int k = 0; k < NST; ++k) ac::mbar_init(&s_bar[threadIdx.y * NST + k], 1);
+            ac::mbar_fence_init();
+        }
     }
     __syncthreads();
 
@@ -132,52 +156,139 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
     };
     int items = 0;  // site updates folded into the 8-bit lanes since the last flush
 
-    // rows are dealt out grid-stride, so the blocks of an instance advance together
-    // through the lattice and the +-z neighbour rows they read are still in L2
-    for (int c = 0; c < a.rows_per_thread; ++c) {
-        const int row = (c * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y;
-        if (row >= LL) break;
-        const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
-        const int y = row - z * L;
-        const int par = (y + z + a.colour) & 1;
-        const int dyp = (y + 1 == L ? 1 - L : 1) * L, dym = (y == 0 ? L - 1 : -1) * L;
-        const int dzp = (z + 1 == L ? 1 - L : 1) * LL, dzm = (z == 0 ? L - 1 : -1) * LL;
-        const int rowoff = row * L;
-        for (int j = j0; j < H; j += JX) {
-            const int x = 2 * j + par;
-            const int i = rowoff + x;  // logical site (counters, couplings)
-            // storage positions (colour-split rows): this site is entry j of half `par`;
-            // its x neighbours are entries j + par and j + par - 1 of the other half
-            const int is = rowoff + par * H + j;
-            const int ho = rowoff + (1 - par) * H;
+    if constexpr (NST > 0) {
+        // rows c = 0, 1, ... of this warp: (c * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y
+        const int segw = a.segw;
+        const uint32_t seg_bytes = (uint32_t)segw * 4u;
+        uint32_t* ring = s_stage + thr_words + (size_t)threadIdx.y * NST * 6 * segw;
+        uint64_t* bars = s_bar + threadIdx.y * NST;
+        const int lane = threadIdx.x;
+        auto row_of = [&](int c) { return (c * (int)gridDim.x + (int)blockIdx.x) * (int)blockDim.y + (int)threadIdx.y; };
+        // lane 0: the six half rows of row c into ring slot c % NST
+        auto issue = [&](int c) {
+            const int row = row_of(c);
+            const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
+            const int y = row - z * L;
+            const int par = (y + z + a.colour) & 1;
+            const int src[6] = {row, row, row + (y + 1 == L ? 1 - L : 1), row + (y == 0 ? L - 1 : -1),
+                                row + (z + 1 == L ? 1 - L : 1) * L, row + (z == 0 ? L - 1 : -1) * L};
+            uint32_t* dst = ring + (size_t)(c % NST) * 6 * segw;
+            uint64_t* bar = &bars[c % NST];
+            ac::mbar_expect_tx(bar, 6u * seg_bytes);
+#pragma unroll
+            for (int k = 0; k < 6; ++k) {
+                const int half = k == 1 ? 1 - par : par;  // x neighbours sit in the other half
+                ac::bulk_g2s(dst + (size_t)k * segw, s + ((size_t)src[k] * L + (size_t)half * H) * Wn, seg_bytes, bar);
+            }
+        };
+        if (lane == 0)
+            for (int c = 0; c < NST && c < a.rows_per_thread; ++c)
+                if (row_of(c) < LL) issue(c);
+        bool ok = true;
+        int c = 0;
+        for (; c < a.rows_per_thread; ++c) {
+            const int row = row_of(c);
+            if (row >= LL) break;
+            ok = __all_sync(0xFFFFFFFFu, ac::mbar_wait(&bars[c % NST], (uint32_t)((c / NST) & 1)));
+            if (!ok) break;
+            const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
+            const int y = row - z * L;
+            const int par = (y + z + a.colour) & 1;
+            const int rowoff = row * L;
+            const int j = j0;  // one site per thread: blockDim.x == G * H
+            const int i = rowoff + 2 * j + par;  // logical site (counters, couplings)
+            const int is = rowoff + par * H + j;  // storage position
             const int jp = j + par == H ? 0 : j + par, jm = j + par == 0 ? H - 1 : j + par - 1;
-            const int nb[6] = {ho + jp, ho + jm, is + dyp, is + dym, is + dzp, is + dzm};
+            const uint32_t* buf = ring + (size_t)(c % NST) * 6 * segw;
             const mp::Couplings cp = UNITJ ? mp::decode_unit(a.j1_ptrs[inst][i])
                                            : mp::decode_general(a.j6_ptrs[inst][i]);
 #pragma unroll
             for (int ch = 0; ch < CH; ++ch) {
                 const int w0 = wbase + ch * WG;
                 uint32_t self[WG], P[WG];
-                mp::load_words<WG>(s + (size_t)is * Wn + w0, self);
+                mp::load_words<WG>(buf + j * Wn + w0, self);
 #pragma unroll
                 for (int wi = 0; wi < WG; ++wi) P[wi] = 0;
 #pragma unroll
                 for (int q = 0; q < 6; ++q) {
+                    // q = +x, -x, +y, -y, +z, -z: half row 1 (at jp, jm), then rows 2..5 at j
+                    const int at = q == 0 ? segw + jp * Wn : q == 1 ? segw + jm * Wn : (q) * segw + j * Wn;
                     uint32_t n[WG];
-                    mp::load_words<WG>(s + (size_t)nb[q] * Wn + w0, n);
+                    mp::load_words<WG>(buf + at + w0, n);
 #pragma unroll
                     for (int wi = 0; wi < WG; ++wi) P[wi] += mp::bond_term(n[wi], cp, q);
                 }
                 const uint32_t* thr = PT ? s_thr + 4 * w0 * kThrStride : s_thr;
                 if (mp::update_words<PT, WG, kThrStride, DRAW>(self, P, vmask[ch], cp.msum, (uint32_t)i,
-                                                         sweep, (uint32_t)w0, key, thr, acc[ch]))
+                                                               sweep, (uint32_t)w0, key, thr, acc[ch]))
                     mp::store_words<WG>(s + (size_t)is * Wn + w0, self);
             }
             if (PT && ++items == mp::kLaneCapacity<KMAX>) {
                 flush();
                 items = 0;
             }
+            __syncwarp();  // every lane is done with slot c % NST
+            if (lane == 0 && c + NST < a.rows_per_thread && row_of(c + NST) < LL) {
+                ac::fence_proxy_async();
+                issue(c + NST);
+            }
         }
+        if (!ok) {
+            // a copy did not arrive: report it, then wait (bounded) for the copies this
+            // warp still has in flight before the block may exit
+            if (lane == 0 && a.status) atomicExch(a.status, SG_ETIMEOUT);
+            for (int k = c; k < c + NST && k < a.rows_per_thread; ++k)
+                if (row_of(k) < LL) ac::mbar_wait(&bars[k % NST], (uint32_t)((k / NST) & 1));
+        }
+    } else {
+        // rows are dealt out grid-stride, so the blocks of an instance advance together
+        // through the lattice and the +-z neighbour rows they read are still in L2
+        for (int c = 0; c < a.rows_per_thread; ++c) {
+            const int row = (c * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y;
+            if (row >= LL) break;
+            const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
+            const int y = row - z * L;
+            const int par = (y + z + a.colour) & 1;
+            const int dyp = (y + 1 == L ? 1 - L : 1) * L, dym = (y == 0 ? L - 1 : -1) * L;
+            const int dzp = (z + 1 == L ? 1 - L : 1) * LL, dzm = (z == 0 ? L - 1 : -1) * LL;
+            const int rowoff = row * L;
+            for (int j = j0; j < H; j += JX) {
+                const int x = 2 * j + par;
+                const int i = rowoff + x;  // logical site (counters, couplings)
+                // storage positions (colour-split rows): this site is entry j of half `par`;
+                // its x neighbours are entries j + par and j + par - 1 of the other half
+                const int is = rowoff + par * H + j;
+                const int ho = rowoff + (1 - par) * H;
+                const int jp = j + par == H ? 0 : j + par, jm = j + par == 0 ? H - 1 : j + par - 1;
+                const int nb[6] = {ho + jp, ho + jm, is + dyp, is + dym, is + dzp, is + dzm};
+                const mp::Couplings cp = UNITJ ? mp::decode_unit(a.j1_ptrs[inst][i])
+                                               : mp::decode_general(a.j6_ptrs[inst][i]);
+    #pragma unroll
+                for (int ch = 0; ch < CH; ++ch) {
+                    const int w0 = wbase + ch * WG;
+                    uint32_t self[WG], P[WG];
+                    mp::load_words<WG>(s + (size_t)is * Wn + w0, self);
+    #pragma unroll
+                    for (int wi = 0; wi < WG; ++wi) P[wi] = 0;
+    #pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        uint32_t n[WG];
+                        mp::load_words<WG>(s + (size_t)nb[q] * Wn + w0, n);
+    #pragma unroll
+                        for (int wi = 0; wi < WG; ++wi) P[wi] += mp::bond_term(n[wi], cp, q);
+                    }
+                    const uint32_t* thr = PT ? s_thr + 4 * w0 * kThrStride : s_thr;
+                    if (mp::update_words<PT, WG, kThrStride, DRAW>(self, P, vmask[ch], cp.msum, (uint32_t)i,
+                                                             sweep, (uint32_t)w0, key, thr, acc[ch]))
+                        mp::store_words<WG>(s + (size_t)is * Wn + w0, self);
+                }
+                if (PT && ++items == mp::kLaneCapacity<KMAX>) {
+                    flush();
+                    items = 0;
+                }
+            }
+        }
+
     }
 
     if (PT) {
@@ -204,10 +315,32 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
     }
 }
 
+// Tuning knob SG_DRAW_ALWAYS (default 1): compute the draws unconditionally in the
+// padding-free variants (0: only when some lane of the warp needs one).
+bool draw_always()
+{
+    static const bool v = [] {
+        const char* e = getenv("SG_DRAW_ALWAYS");
+        return !(e && atoi(e) == 0);
+    }();
+    return v;
+}
+
 struct SweepShape {
     dim3 block, grid;
     int G, CH, WG, rows_per_thread;
+    int nst = 0;      // staged variant: rows in flight per warp (0: plain loads)
+    size_t smem = 0;  // staged variant: dynamic shared memory per block
 };
+
+// Tuning knob SG_ROWS_STAGE: rows in flight per warp in the staged variant, 2 (default)
+// or 3; 0 turns the staged variant off.  Read at every launch.
+int stage_depth()
+{
+    const char* e = getenv("SG_ROWS_STAGE");
+    const int d = e ? atoi(e) : 2;
+    return (d == 0 || d == 3) ? d : 2;
+}
 
 // Tuning knob: largest number of 4-word chunks per thread (1 or 2), from the
 // environment variable SG_SWEEP_MAX_CH (default 2).
@@ -232,7 +365,7 @@ int rows_min_blocks()
     return v;
 }
 
-SweepShape sweep_shape(int I, int L, int Wn)
+SweepShape sweep_shape(int I, int L, int Wn, bool pt, bool pad)
 {
     SweepShape sh;
     sh.WG = (Wn % 4 == 0) ? 4 : (Wn % 2 == 0) ? 2 : 1;
@@ -250,9 +383,28 @@ SweepShape sweep_shape(int I, int L, int Wn)
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    long long bps = rows_min_blocks();
+    // staged variant: one warp per row (a half row is exactly 32 threads' sites), rows
+    // whose halves are whole 16-byte units, and room for the ring in shared memory
+    if (stage_depth() > 0 && !pad && sh.WG == 4 && TX == 32 && sh.G * H == 32 && (H * Wn) % 4 == 0 &&
+        rows_min_blocks() == 2 && draw_always()) {
+        int per_sm = 0, per_block = 0;
+        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+        cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+        const int nst = stage_depth();
+        const size_t ring = (size_t)TY * nst * 6 * (size_t)(H * Wn) * 4;
+        const size_t thr = pt ? (size_t)staged_thr_words(4 * Wn) * 4 : 0;
+        const size_t fixed = pt ? 256 * 4 + 8 * 8 * 3 + 64 : kThrRow * 4 + 8 * 8 * 3 + 64;
+        const size_t need = ring + thr;
+        const long long fit = (long long)per_sm / (long long)(need + fixed + 1024);
+        if ((long long)need <= per_block && fit >= 1) {
+            sh.nst = nst;
+            sh.smem = need;
+            bps = fit < 2 ? fit : 2;
+        }
+    }
     // rows per thread: enough blocks for about two per SM, so that each block fills
     // its threshold table and reduces its energies once for many rows
-    const long long bps = rows_min_blocks();
     long long rpt = ((long long)LL * I + (long long)TY * bps * sms - 1) / ((long long)TY * bps * sms);
     if (rpt < 1) rpt = 1;
     const char* e = getenv("SG_ROWS_RPT");  // tuning knob: rows per thread
@@ -263,20 +415,30 @@ SweepShape sweep_shape(int I, int L, int Wn)
     return sh;
 }
 
-// Tuning knob SG_DRAW_ALWAYS (default 1): compute the draws unconditionally in the
-// padding-free variants (0: only when some lane of the warp needs one).
-bool draw_always()
+// Launches one instantiation with the shape's dynamic shared memory (raising the
+// kernel's limit when the staged ring needs more than the default 48 KB).
+template <typename K>
+void launch_with_smem(K kernel, const SweepShape& sh, const SweepArgs& a, cudaStream_t st)
 {
-    static const bool v = [] {
-        const char* e = getenv("SG_DRAW_ALWAYS");
-        return !(e && atoi(e) == 0);
-    }();
-    return v;
+    if (sh.smem > 48 * 1024)
+        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
+    kernel<<<sh.grid, sh.block, sh.smem, st>>>(a);
 }
 
 template <bool PT, bool UNITJ, int CH>
 void launch_nopad(const SweepShape& sh, const SweepArgs& a, bool xch, cudaStream_t st)
 {
+    if (sh.nst == 2 || sh.nst == 3) {
+        if (PT && xch)
+            launch_with_smem(sh.nst == 2 ? sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2, true, true, 2>
+                                         : sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2, true, true, 3>,
+                             sh, a, st);
+        else
+            launch_with_smem(sh.nst == 2 ? sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2, true, false, 2>
+                                         : sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2, true, false, 3>,
+                             sh, a, st);
+        return;
+    }
     if (draw_always() && rows_min_blocks() == 2) {
         if (PT && xch)
             sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2, true, true><<<sh.grid, sh.block, 0, st>>>(a);
@@ -322,11 +484,12 @@ bool launch_variant(const SweepShape& sh, const SweepArgs& a, bool pad, bool xch
 template <bool PT>
 int32_t launch_rows(SweepArgs a, int I, bool unit_j, bool xch, bool* fused, cudaStream_t st)
 {
-    const SweepShape sh = sweep_shape(I, a.L, a.Wn);
+    const bool pad = a.Rvalid != 4 * a.Wn;  // padding replicas in the last word
+    const SweepShape sh = sweep_shape(I, a.L, a.Wn, PT, pad);
     a.G = sh.G;
     a.rows_per_thread = sh.rows_per_thread;
     a.Lmagic = (uint32_t)((0x100000000ull + (uint64_t)a.L - 1) / (uint64_t)a.L);
-    const bool pad = a.Rvalid != 4 * a.Wn;  // padding replicas in the last word
+    a.segw = (a.L / 2) * a.Wn;
     const bool f = unit_j ? launch_variant<PT, true>(sh, a, pad, xch, st)
                           : launch_variant<PT, false>(sh, a, pad, xch, st);
     if (fused) *fused = f;
@@ -350,7 +513,8 @@ bool rows_kernel_supports(int Wn)
 int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_row, bool unit_j, int I, int L, int Wn, int R,
-                             uint32_t sweep, int colour, cudaStream_t st, const uint32_t* sweep_base)
+                             uint32_t sweep, int colour, cudaStream_t st, const uint32_t* sweep_base,
+                             int* status)
 {
     SweepArgs a{};
     a.spins = reinterpret_cast<uint32_t*>(spins);
@@ -364,6 +528,7 @@ int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
     a.sweep = sweep;
     a.colour = colour;
     a.sweep_base = sweep_base;
+    a.status = status;
     return launch_rows<false>(a, I, unit_j, false, nullptr, st);
 }
 
@@ -372,7 +537,7 @@ int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
                              const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st,
-                             const uint32_t* sweep_base)
+                             const uint32_t* sweep_base, int* status)
 {
     SweepArgs a{};
     a.spins = reinterpret_cast<uint32_t*>(spins);
@@ -390,6 +555,7 @@ int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
     if (xch) a.x = *xch;
     a.done = done;
     a.sweep_base = sweep_base;
+    a.status = status;
     return launch_rows<true>(a, I, unit_j, xch != nullptr, fused, st);
 }
 

@@ -17,6 +17,7 @@
 #include <stdint.h>
 #include <stdlib.h>
 
+#include "async_copy.cuh"
 #include "metropolis.cuh"
 #include "philox.cuh"
 #include "sg_internal.h"
@@ -27,51 +28,10 @@ namespace {
 constexpr int kThrStrideT = 17;
 constexpr int kRing = 4;
 constexpr int kMaxLaneSteps = 10;  // site updates a thread may add to its 8-bit energy lanes
-constexpr uint32_t kSpinLimit = 1u << 24;  // try_wait rounds before a wait gives up
-
-__device__ __forceinline__ uint32_t smem_addr(const void* p)
-{
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
-{
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
-        : "memory");
-}
-
-// Bounded wait for phase `parity` of the barrier; returns false when it gave up.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity)
-{
-    const uint32_t a = smem_addr(bar);
-    for (uint32_t n = 0; n < kSpinLimit; ++n) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
+using ac::bulk_g2s;
+using ac::mbar_expect_tx;
+using ac::mbar_init;
+using ac::mbar_wait;
 
 struct TileArgs {
     uint32_t* spins;               // [I][N][Wn] words
@@ -114,7 +74,7 @@ __global__ void __launch_bounds__(256, 2) sweep_tile_kernel(const TileArgs a)
 
     if (tid == 0) {
         for (int b = 0; b < kRing; ++b) mbar_init(&bars[b], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        ac::mbar_fence_init();
         s_abort = 0;
     }
     if (PT) {
@@ -204,7 +164,7 @@ __global__ void __launch_bounds__(256, 2) sweep_tile_kernel(const TileArgs a)
     for (int t = 0; t < ZC; ++t) {
         if (tid == 0 && t + 2 <= ZC && ok) {
             // buffer of slab t+2 held slab t-2, whose last reader finished at step t-1
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            ac::fence_proxy_async();
             issue(t + 2);
             issued_to = t + 2;
         }

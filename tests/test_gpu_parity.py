@@ -289,3 +289,41 @@ def test_uneven_batch_any_plane_width(sg, monkeypatch, wg, graph):
     for a, b in zip(ref, got):
         assert np.array_equal(a["spins"], b["spins"].cpu().numpy())
         assert np.array_equal(a["E"], b["E"])
+
+
+# --------------------------------------------------------------------------- staged rows
+
+# Shapes whose half row is exactly one warp's sites (the staged variant: bulk copies of
+# the six half rows into shared memory, NST rows ahead).
+@pytest.mark.parametrize("L,K,S", [(64, 16, 2), (32, 64, 2), (16, 128, 3), (8, 256, 4)])
+def test_pt_staged_shapes_match_oracle(sg, L, K, S):
+    inst = sg.Instance.create(L, 7000 + L)
+    J3, _, egs = inst.get()
+    _pt_compare(sg, inst, J3, egs, K, S, 0.2, 3.0, seed=21, iid=3)
+
+
+@pytest.mark.parametrize("L,R,S", [(64, 32, 2), (32, 64, 3), (16, 128, 4), (8, 256, 5), (2, 1024, 6)])
+def test_sa_staged_shapes_match_oracle(sg, L, R, S):
+    inst = sg.Instance.create(L, 7100 + L)
+    J3, _, egs = inst.get()
+    _sa_compare(sg, inst, J3, egs, R, S, 0.1, 3.0, seed=5, iid=1)
+
+
+@pytest.mark.parametrize("depth", ["2", "3"])
+def test_staged_equals_plain_loads(sg, monkeypatch, depth):
+    """The staged variant (either ring depth) and the plain-load variant give the same bytes."""
+    insts = [sg.Instance.create(64, 7200 + k) for k in range(3)]
+    params = [dict(temps=32, sweeps=12, beta_min=0.2, beta_max=3.0, seed=8, instance_id=k)
+              for k in range(3)]
+    monkeypatch.setenv("SG_ROWS_STAGE", "0")
+    plain = sg.pt_run_batch(insts, params, spins="host")
+    sa_plain = sg.sa_run(insts[0], 32, 10, 0.1, 3.0, seed=2, spins="host")
+    monkeypatch.setenv("SG_ROWS_STAGE", depth)
+    staged = sg.pt_run_batch(insts, params, spins="host")
+    sa_staged = sg.sa_run(insts[0], 32, 10, 0.1, 3.0, seed=2, spins="host")
+    for a, b in zip(plain, staged):
+        assert np.array_equal(a["spins"], b["spins"]) and np.array_equal(a["E"], b["E"])
+        assert a["minE"] == b["minE"] and np.array_equal(a["perm"], b["perm"])
+        assert np.array_equal(a["accepts"], b["accepts"])
+    assert np.array_equal(sa_plain["spins"], sa_staged["spins"])
+    assert np.array_equal(sa_plain["E"], sa_staged["E"])
