@@ -314,6 +314,114 @@ def serving_leg(sg, args, w):
     return out
 
 
+# ---------------------------------------------------------------- batched leg
+
+def batched_line(sg, args, torch, clocks_cls, local):
+    """Batched uneven SA: 512 instances, L uniform over {8,12,16,24,32,48}, 64 replicas,
+    sweeps uniform over {100, 1000, 10000}, all in one sg_sa_run_batch (one persistent
+    graph-captured launch, plane width from the autotuner)."""
+    w = wl.BATCHED
+    shapes = w.draw()
+    insts = [sg.Instance.create(L, w.instance_seed(k), w.class_prob, True) for k, (L, S) in enumerate(shapes)]
+    params = [dict(replicas=w.replicas, sweeps=S, beta0=w.beta0, beta1=w.beta1, schedule="linear", seed=0,
+                   instance_id=k) for k, (L, S) in enumerate(shapes)]
+    attempts = sum(L ** 3 * w.replicas * S for L, S in shapes)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        out = sg.sa_run_batch(insts, params)
+    clocks = clocks_cls(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        out = sg.sa_run_batch(insts, params)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    ms = ev0.elapsed_time(ev1)
+    # one more step with launch timing on: the persistent sweep launch alone
+    sg.stats_read(reset=True)
+    sg.stats_enable(True)
+    sg.sa_run_batch(insts, params)
+    torch.cuda.synchronize()
+    sg.stats_enable(False)
+    st = sg.stats_read(reset=True)
+    sw = st["sweep"]
+    peak, peak_kind, sm_mhz = _peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = sms * WIDE_MULS_PER_SM_CLOCK / MULS_PER_ATTEMPT * sm_mhz * 1e6
+    bpa = 2.0 + 3.0 / w.replicas
+    roof = None
+    if sw["device_ms"] > 0:
+        rate = sw["units"] / (sw["device_ms"] / 1000.0)
+        roof = {"bound": "alu", "achieved": rate, "peak": alu_peak, "unit": "attempts/s",
+                "frac": rate / alu_peak, "traffic": None, "kernel": "sa_planes_kernel",
+                "launch_ms": sw["device_ms"] / max(sw["launches"], 1),
+                "hbm": {"achieved": rate * bpa / 1e9, "peak": peak, "unit": "GB/s",
+                        "frac": rate * bpa / 1e9 / peak, "peak_source": peak_kind}}
+    value = attempts * args.steps / (ms / 1000.0)
+    eps = [float(e) for o in out for e in o["eps"][:4]]
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "config": {"workload": w.name, "instances": w.instances, "L": list(w.L_choices),
+                       "replicas": w.replicas, "sweeps": list(w.sweep_choices),
+                       "attempts_per_step": attempts, "beta": f"linear {w.beta0}->{w.beta1}"},
+            "roofline": roof, "gpu_launches": sum(v["launches"] for v in st.values()),
+            "clocks": clk, "eps_mean_sample": sum(eps) / len(eps)}
+
+
+# ---------------------------------------------------------------- SA throughput leg
+
+def sa_line(sg, args, torch, clocks_cls, local):
+    """SA throughput: one L=16 instance, 1024 replicas, 1000 sweeps, beta linear 0.1 -> 3.0;
+    a step is one sg_sa_run.  The spins (4 MB) stay in L2: the integer roof binds."""
+    w = wl.SA_L16
+    inst = sg.Instance.create(w.L, w.instance_seed(0), w.class_prob, True)
+    attempts = w.L ** 3 * w.replicas * w.sweeps
+    stream = torch.cuda.current_stream()
+    steps = max(args.steps, 20)
+    for _ in range(max(args.warmup, 3)):
+        out = sg.sa_run(inst, w.replicas, w.sweeps, w.beta0, w.beta1, "linear", w.run_seed, 0)
+    sg.stats_read(reset=True)
+    sg.stats_enable(True)
+    clocks = clocks_cls(local)
+    clocks.start()
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(steps):
+        out = sg.sa_run(inst, w.replicas, w.sweeps, w.beta0, w.beta1, "linear", w.run_seed, 0)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sg.stats_enable(False)
+    st = sg.stats_read(reset=True)
+    ms = ev0.elapsed_time(ev1)
+    sw = st["sweep"]
+    peak, peak_kind, sm_mhz = _peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    alu_peak = sms * WIDE_MULS_PER_SM_CLOCK / MULS_PER_ATTEMPT * sm_mhz * 1e6
+    roof = None
+    if sw["launches"] and sw["device_ms"] > 0:
+        rate = sw["units"] / (sw["device_ms"] / 1000.0)
+        roof = {"bound": "alu", "achieved": rate, "peak": alu_peak, "unit": "attempts/s",
+                "frac": rate / alu_peak, "traffic": None, "kernel": "sweep_rows_kernel<SA>",
+                "launch_ms": sw["device_ms"] / sw["launches"],
+                "share_of_step": sw["device_ms"] / ms}
+    eps = out["eps"]
+    return {"metric": METRIC, "value": attempts * steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+            "data": "synthetic",
+            "config": {"workload": w.name, "L": w.L, "replicas": w.replicas, "sweeps": w.sweeps,
+                       "beta": f"linear {w.beta0}->{w.beta1}", "cache": "working set 4 MB, L2-resident"},
+            "roofline": roof, "gpu_launches": sum(v["launches"] for v in st.values()), "clocks": clk,
+            "eps": {"min": float(min(eps)), "median": float(sorted(eps)[len(eps) // 2]),
+                    "max": float(max(eps))}}
+
+
 # ---------------------------------------------------------------- GPU leg
 
 def main():
@@ -328,9 +436,10 @@ def main():
     ap.add_argument("--ref-sweeps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="pt", choices=["pt", "serving"],
+    ap.add_argument("--workload", default="pt", choices=["pt", "serving", "batched", "sa"],
                     help="pt: the PT throughput line (with a short serving leg); serving: the "
-                         "serving stream alone")
+                         "serving stream alone; batched: 512 uneven SA instances in one launch; "
+                         "sa: SA throughput at L=16 with 1024 replicas")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg of the pt line")
     ap.add_argument("--serve-seconds", type=float, default=None,
                     help="arrival window (default: 10 s in the pt line, the workload's 60 s alone)")
@@ -383,6 +492,14 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
+    if args.workload in ("batched", "sa"):
+        if rank == 0:
+            fn = batched_line if args.workload == "batched" else sa_line
+            print(json.dumps(fn(sg, args, torch, ClockSampler, local)), flush=True)
+        barrier()
+        if world > 1:
+            torch.distributed.destroy_process_group()
+        return
     if alone:
         if rank == 0:
             res = serving_leg(sg, args, wl.SERVING)

@@ -570,19 +570,38 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
     SG_TRY_CUDA(cudaStreamSynchronize(st));  // host arrays above are stack/heap temporaries
 
     const int blocks = blocks_for(WG);
+    // launch statistics: with timing on, the run launches directly and brackets the
+    // persistent sweep launch with events
+    const bool timed = stats_timing();
+    struct EventPair {
+        cudaEvent_t e[2] = {nullptr, nullptr};
+        ~EventPair()
+        {
+            for (cudaEvent_t x : e)
+                if (x) cudaEventDestroy(x);
+        }
+    } evp;
+    cudaEvent_t* ev = evp.e;
+    if (timed && (cudaEventCreate(&ev[0]) != cudaSuccess || cudaEventCreate(&ev[1]) != cudaSuccess)) {
+        cudaGetLastError();
+        set_error("cudaEventCreate failed");
+        return SG_ECUDA;
+    }
     auto device_work = [&](cudaStream_t s) -> int32_t {
         SG_TRY_CUDA(cudaMemsetAsync(d_next.p, 0, sizeof(unsigned), s));
         SG_TRY_CUDA(cudaMemsetAsync(d_E.p, 0, sizeof(unsigned long long) * (size_t)n * 4 * WG, s));
         SG_B(launch_planes_init(WG, static_cast<Plane*>(d_pl.p), n, s));
+        if (timed) SG_TRY_CUDA(cudaEventRecord(ev[0], s));
         SG_B(launch_sa_planes(WG, static_cast<Plane*>(d_pl.p), static_cast<int*>(d_ord.p), n,
                               static_cast<unsigned*>(d_next.p), unit, blocks, s));
+        if (timed) SG_TRY_CUDA(cudaEventRecord(ev[1], s));
         SG_B(launch_planes_energy(WG, static_cast<Plane*>(d_pl.p), n, static_cast<unsigned long long*>(d_E.p), s));
         SG_B(launch_planes_unpack(WG, static_cast<Plane*>(d_pl.p), n, static_cast<int8_t* const*>(d_outs.p), s));
         return SG_OK;
     };
     // the device part of the run is one CUDA graph (knob SG_BATCH_GRAPH=0 launches directly)
     const char* g = getenv("SG_BATCH_GRAPH");
-    const bool graph = !(g && atoi(g) == 0);
+    const bool graph = !(g && atoi(g) == 0) && !timed;
     if (used_graph) *used_graph = graph;
     if (graph) {
         cudaStream_t cs = nullptr;
@@ -618,6 +637,20 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
                                         cudaMemcpyDeviceToHost, st));
     }
     SG_TRY_CUDA(cudaStreamSynchronize(st));
+    {
+        int64_t attempts = 0, cells = 0;
+        for (int a = 0; a < I; ++a) {
+            const int64_t N = insts[members[a]]->N, R = ps[members[a]].replicas;
+            attempts += N * R * ps[members[a]].sweeps;
+            cells += N * R;
+        }
+        float ms = 0.f;
+        if (timed) cudaEventElapsedTime(&ms, ev[0], ev[1]);
+        stats_add(SG_KERNEL_INIT, 1, cells, 0.0);
+        stats_add(SG_KERNEL_SWEEP, 1, attempts, (double)ms);
+        stats_add(SG_KERNEL_ENERGY, 1, cells, 0.0);
+        stats_add(SG_KERNEL_OTHER, 1, cells, 0.0);
+    }
     for (int q = 0; q < n; ++q) {
         const Plane& pl = planes[q];
         const int a = pl.out;

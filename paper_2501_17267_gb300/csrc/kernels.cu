@@ -296,6 +296,77 @@ energy_kernel(const uint32_t* __restrict__ spins, const uint2* const* __restrict
     }
 }
 
+// Energy by rows (used when Wn divides the block size): every edge counted once, as a
+// forward bond (+x, +y, +z) of its lower site, with 32-bit indexing.  Thread t owns word
+// w = t % Wn of every (kBlock / Wn)-th site of a row, so its four byte sums belong to
+// fixed slots.  Per site and byte, sum_d J_d s_i s_{i+e_d} = m3 - W3, where m3 = sum_d |J_d|
+// and W3 adds 2|J_d| for every bond whose term J_d s_i s_j is negative; W3 <= 12 per byte,
+// so 21 sites add up in the four bytes of one word without carries before a fold.
+__global__ void __launch_bounds__(kBlock)
+energy_rows_kernel(const uint32_t* __restrict__ spins, const uint2* const* __restrict__ j6_ptrs, int L,
+                   int Wn, int rows_per_block, unsigned long long* __restrict__ E_out)
+{
+    __shared__ unsigned long long s_E[4 * kBlock];
+    const int inst = blockIdx.y;
+    const int LL = L * L, H = L >> 1;
+    const uint2* __restrict__ j6 = j6_ptrs[inst];
+    const uint32_t* __restrict__ s = spins + (size_t)inst * (size_t)LL * L * Wn;
+    for (int q = threadIdx.x; q < 4 * Wn; q += blockDim.x) s_E[q] = 0;
+    __syncthreads();
+    const int w = threadIdx.x % Wn, s0 = threadIdx.x / Wn, ds = kBlock / Wn;
+    long long m3sum = 0;
+    long long acc[4] = {0, 0, 0, 0};
+    uint32_t lanes = 0;
+    int nl = 0;
+    auto fold = [&]() {
+#pragma unroll
+        for (int b = 0; b < 4; ++b) acc[b] += (lanes >> (8 * b)) & 0xFFu;
+        lanes = 0;
+        nl = 0;
+    };
+    const int r0 = blockIdx.x * rows_per_block;
+    const int r1 = min(LL, r0 + rows_per_block);
+    for (int r = r0; r < r1; ++r) {
+        const int z = r / L, y = r - z * L;
+        const int ryp = z * L + (y + 1 == L ? 0 : y + 1);
+        const int rzp = (z + 1 == L ? 0 : z + 1) * L + y;
+        const uint32_t* __restrict__ row = s + (size_t)r * L * Wn;
+        const uint32_t* __restrict__ rowy = s + (size_t)ryp * L * Wn;
+        const uint32_t* __restrict__ rowz = s + (size_t)rzp * L * Wn;
+        for (int pos = s0; pos < L; pos += ds) {
+            // colour-split storage: position pos holds x = 2j + par
+            const int par = pos >= H ? 1 : 0;
+            const int j = pos - par * H;
+            const int x = 2 * j + par;
+            const int posx = par ? (j + 1 == H ? 0 : j + 1) : H + j;  // site x + 1
+            const uint2 rec = j6[r * L + x];
+            const int Jd[3] = {(int)(int8_t)(rec.x & 0xFFu), (int)(int8_t)((rec.x >> 16) & 0xFFu),
+                               (int)(int8_t)(rec.y & 0xFFu)};
+            const uint32_t me = row[pos * Wn + w];
+            const uint32_t nb[3] = {row[posx * Wn + w], rowy[pos * Wn + w], rowz[pos * Wn + w]};
+            uint32_t W3 = 0;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                const uint32_t differ = (me ^ nb[d]) & 0x02020202u;  // 0x02 where the spins differ
+                // negative term: J > 0 with different spins, J < 0 with equal spins
+                const uint32_t neg = Jd[d] > 0 ? differ : Jd[d] < 0 ? differ ^ 0x02020202u : 0u;
+                W3 += neg * (uint32_t)abs(Jd[d]);
+                m3sum += abs(Jd[d]);
+            }
+            lanes += W3;
+            if (++nl == 21) fold();
+        }
+    }
+    fold();
+#pragma unroll
+    for (int b = 0; b < 4; ++b)
+        if (m3sum - acc[b]) atomicAdd(&s_E[4 * w + b], (unsigned long long)(m3sum - acc[b]));
+    __syncthreads();
+    unsigned long long* Ei = E_out + (size_t)inst * 4 * Wn;
+    for (int q = threadIdx.x; q < 4 * Wn; q += blockDim.x)
+        if (s_E[q]) atomicAdd(&Ei[q], s_E[q]);
+}
+
 // ---------------------------------------------------------------- parallel tempering
 
 __global__ void pt_setup_kernel(const unsigned long long* __restrict__ E64, int32_t* __restrict__ E,
@@ -443,6 +514,19 @@ int32_t launch_init_spins(int8_t* spins, const RunKeys* keys_dev, int I, int L, 
 int32_t launch_energy(const int8_t* spins, const uint2* const* j6_ptrs, int I, int L, int Wn,
                       unsigned long long* E_out, cudaStream_t st)
 {
+    if (kBlock % Wn == 0) {
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int LL = L * L;
+        int gx = (8 * sms + I - 1) / I;  // about eight blocks per SM over all instances
+        if (gx > LL) gx = LL;
+        if (gx < 1) gx = 1;
+        const int rpb = (LL + gx - 1) / gx;
+        dim3 grid((LL + rpb - 1) / rpb, I);
+        energy_rows_kernel<<<grid, kBlock, 0, st>>>((const uint32_t*)spins, j6_ptrs, L, Wn, rpb, E_out);
+        return check_launch("energy_rows");
+    }
     const int64_t N = (int64_t)L * L * L;
     dim3 grid(sweep_grid_x(N * Wn, Wn), I);
     energy_kernel<<<grid, kBlock, 0, st>>>((const uint32_t*)spins, j6_ptrs, L, Wn, E_out);
