@@ -595,34 +595,24 @@ extern "C" int32_t sg_sa_run_batch(const sg_instance* const* insts, const sg_sa_
         groups[std::make_tuple(insts[a]->L, p.replicas, p.sweeps, p.beta0, p.beta1, p.schedule)]
             .push_back(a);
     }
-    // A batch of uneven shapes runs in one persistent launch (batch.cu); a batch of one
-    // shape uses the sweep kernels that spread each instance over many blocks.  Knob
+    // A batch of uneven shapes runs in one persistent launch (batch.cu), and so does a
+    // batch of small lattices whose half sweeps are too short to pay for a launch each
+    // (every plane then lives in shared memory for the whole run); other batches of one
+    // shape use the sweep kernels that spread each instance over many blocks.  Knob
     // SG_BATCH_PLANES = 1 / 0 forces one or the other.
+    bool small = n > 0;
+    int64_t half_sweep = 0;  // attempts per half sweep of the whole batch
+    for (int a = 0; a < n; ++a) {
+        small &= planes_smem_bytes(1, insts[a]->L) > 0;
+        half_sweep += insts[a]->N / 2 * (int64_t)ps[a].replicas;
+    }
+    small &= half_sweep <= (int64_t)1 << 24;
     const char* knob = getenv("SG_BATCH_PLANES");
-    const bool planes = knob ? atoi(knob) == 1 : groups.size() > 1;
+    const bool planes = knob ? atoi(knob) == 1 : (groups.size() > 1 || small);
     if (planes && n > 0) {
         std::vector<int> all(n);
         for (int a = 0; a < n; ++a) all[a] = a;
-        int64_t units = 0;
-        for (int a = 0; a < n; ++a) units += insts[a]->N * (int64_t)ps[a].replicas * ps[a].sweeps;
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        const bool timing = stats_timing();
-        if (timing) {
-            cudaEventCreate(&e0);
-            cudaEventCreate(&e1);
-            cudaEventRecord(e0, st);
-        }
-        const int32_t rc = run_sa_planes(all, insts, ps, outs, st, nullptr, nullptr);
-        float ms = 0.f;
-        if (timing) {
-            cudaEventRecord(e1, st);
-            cudaEventSynchronize(e1);
-            cudaEventElapsedTime(&ms, e0, e1);
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-        }
-        if (rc == SG_OK) stats_add(SG_KERNEL_SWEEP, 1, units, ms);
-        return rc;
+        return run_sa_planes(all, insts, ps, outs, st, nullptr, nullptr);  // records its launches
     }
     for (auto& g : groups)
         for (size_t at = 0; at < g.second.size(); at += kMaxGroup) {

@@ -36,12 +36,17 @@ namespace {
 
 __device__ __forceinline__ int div_magic(int v, uint32_t m) { return (int)__umulhi((uint32_t)v, m); }
 
-// Persistent sweep kernel.  `order` lists plane indices by decreasing work.
-template <int WG, bool UNITJ>
+// Persistent sweep kernel.  `order` lists plane indices by decreasing work.  SMEM: the
+// block copies its plane into shared memory (dynamic, [N][WG] words), runs all of the
+// plane's sweeps there, and writes it back -- no global traffic and no launches between
+// sweeps, for planes that fit.
+template <int WG, bool UNITJ, bool SMEM = false>
 __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict__ planes,
                                                         const int* __restrict__ order, int n_planes,
                                                         unsigned* __restrict__ next)
 {
+    constexpr int U = 4 / WG;
+    extern __shared__ __align__(16) uint32_t s_plane[];
     __shared__ int s_item;
     __shared__ uint32_t s_thr[kThrRow];
     const int tid = threadIdx.x, nthreads = blockDim.x;
@@ -51,7 +56,7 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
         const int it = s_item;
         if (it >= n_planes) break;
         const Plane p = planes[order[it]];
-        const int L = p.L, H = L >> 1, LL = L * L;
+        const int L = p.L, H = L >> 1, LL = L * L, N = LL * L;
         const int half = LL * H;  // sites of one colour
         const RunKeys key{p.k0, p.k1};
         uint32_t vmask[WG], acc[WG];
@@ -64,42 +69,74 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
             vmask[wi] = m;
             acc[wi] = 0;
         }
+        uint32_t* __restrict__ sp = p.spins;
+        if constexpr (SMEM) {
+            for (int q = tid; q < N; q += nthreads) {
+                uint32_t w[WG];
+                mp::load_words<WG>(p.spins + (size_t)q * WG, w);
+                mp::store_words<WG>(s_plane + (size_t)q * WG, w);
+            }
+            __syncthreads();
+            sp = s_plane;
+        }
         for (int sw = p.s_begin; sw < p.s_end; ++sw) {
             if (tid < kThrRow) s_thr[tid] = p.thr[(size_t)sw * kThrRow + tid];
             __syncthreads();
             for (int colour = 0; colour < 2; ++colour) {
-                for (int q = tid; q < half; q += nthreads) {
-                    const int row = div_magic(q, p.Hmagic);
-                    const int j = q - row * H;
-                    const int z = div_magic(row, p.Lmagic);
-                    const int y = row - z * L;
-                    const int par = (y + z + colour) & 1;
-                    const int rowoff = row * L;
-                    const int i = rowoff + 2 * j + par;  // logical site
-                    const int is = rowoff + par * H + j;  // storage position
-                    const int ho = rowoff + (1 - par) * H;
-                    const int jp = j + par == H ? 0 : j + par, jm = j + par == 0 ? H - 1 : j + par - 1;
-                    const int dyp = (y + 1 == L ? 1 - L : 1) * L, dym = (y == 0 ? L - 1 : -1) * L;
-                    const int dzp = (z + 1 == L ? 1 - L : 1) * LL, dzm = (z == 0 ? L - 1 : -1) * LL;
-                    const int nb[6] = {ho + jp, ho + jm, is + dyp, is + dym, is + dzp, is + dzm};
-                    const mp::Couplings cp = UNITJ ? mp::decode_unit(p.j1[i]) : mp::decode_general(p.j6[i]);
-                    uint32_t self[WG], P[WG];
-                    mp::load_words<WG>(p.spins + (size_t)is * WG, self);
+                // U = 4 / WG sites per thread at a time: all their loads, then all their
+                // updates and stores (sites of one colour never read one another), so the
+                // U Philox chains and load streams overlap
+                for (int q0 = tid; q0 < half; q0 += U * nthreads) {
+                    int is_[U], i_[U];
+                    bool live[U];
+                    mp::Couplings cp[U];
+                    uint32_t self[U][WG], P[U][WG];
 #pragma unroll
-                    for (int wi = 0; wi < WG; ++wi) P[wi] = 0;
+                    for (int u = 0; u < U; ++u) {
+                        live[u] = q0 + u * nthreads < half;
+                        const int q = live[u] ? q0 + u * nthreads : q0;  // an idle slot redoes q0, unstored
+                        const int row = H == 1 ? q : div_magic(q, p.Hmagic);  // ceil(2^32 / 1) does not fit
+                        const int j = q - row * H;
+                        const int z = div_magic(row, p.Lmagic);
+                        const int y = row - z * L;
+                        const int par = (y + z + colour) & 1;
+                        const int rowoff = row * L;
+                        i_[u] = rowoff + 2 * j + par;  // logical site
+                        is_[u] = rowoff + par * H + j;  // storage position
+                        const int ho = rowoff + (1 - par) * H;
+                        const int jp = j + par == H ? 0 : j + par, jm = j + par == 0 ? H - 1 : j + par - 1;
+                        const int dyp = (y + 1 == L ? 1 - L : 1) * L, dym = (y == 0 ? L - 1 : -1) * L;
+                        const int dzp = (z + 1 == L ? 1 - L : 1) * LL, dzm = (z == 0 ? L - 1 : -1) * LL;
+                        const int nb[6] = {ho + jp, ho + jm, is_[u] + dyp, is_[u] + dym, is_[u] + dzp, is_[u] + dzm};
+                        cp[u] = UNITJ ? mp::decode_unit(p.j1[i_[u]]) : mp::decode_general(p.j6[i_[u]]);
+                        mp::load_words<WG>(sp + (size_t)is_[u] * WG, self[u]);
 #pragma unroll
-                    for (int qq = 0; qq < 6; ++qq) {
-                        uint32_t n[WG];
-                        mp::load_words<WG>(p.spins + (size_t)nb[qq] * WG, n);
+                        for (int wi = 0; wi < WG; ++wi) P[u][wi] = 0;
 #pragma unroll
-                        for (int wi = 0; wi < WG; ++wi) P[wi] += mp::bond_term(n[wi], cp, qq);
+                        for (int qq = 0; qq < 6; ++qq) {
+                            uint32_t n[WG];
+                            mp::load_words<WG>(sp + (size_t)nb[qq] * WG, n);
+#pragma unroll
+                            for (int wi = 0; wi < WG; ++wi) P[u][wi] += mp::bond_term(n[wi], cp[u], qq);
+                        }
                     }
-                    if (mp::update_words<false, WG, 0, true>(self, P, vmask, cp.msum, (uint32_t)i,
-                                                             (uint32_t)sw, (uint32_t)p.w0, key, s_thr,
-                                                             acc))
-                        mp::store_words<WG>(p.spins + (size_t)is * WG, self);
+#pragma unroll
+                    for (int u = 0; u < U; ++u) {
+                        const bool flip = mp::update_words<false, WG, 0, true>(
+                            self[u], P[u], vmask, cp[u].msum, (uint32_t)i_[u], (uint32_t)sw, (uint32_t)p.w0, key,
+                            s_thr, acc);
+                        if (live[u] && flip) mp::store_words<WG>(sp + (size_t)is_[u] * WG, self[u]);
+                    }
                 }
                 __syncthreads();
+            }
+        }
+        if constexpr (SMEM) {
+            __syncthreads();
+            for (int q = tid; q < N; q += nthreads) {
+                uint32_t w[WG];
+                mp::load_words<WG>(s_plane + (size_t)q * WG, w);
+                mp::store_words<WG>(p.spins + (size_t)q * WG, w);
             }
         }
     }
@@ -200,41 +237,64 @@ int check(const char* what)
     return SG_OK;
 }
 
+// The instantiation for (WG, unit couplings, plane in shared memory).
 template <int WG>
-int32_t launch_planes(const Plane* d_planes, const int* d_order, int n, unsigned* d_next, bool unit,
-                      int blocks, cudaStream_t st)
+const void* planes_kernel_fn(bool unit, bool smem)
 {
-    if (unit)
-        sa_planes_kernel<WG, true><<<blocks, 256, 0, st>>>(d_planes, d_order, n, d_next);
-    else
-        sa_planes_kernel<WG, false><<<blocks, 256, 0, st>>>(d_planes, d_order, n, d_next);
-    return check("sa_planes_kernel");
+    if (smem)
+        return unit ? (const void*)sa_planes_kernel<WG, true, true> : (const void*)sa_planes_kernel<WG, false, true>;
+    return unit ? (const void*)sa_planes_kernel<WG, true, false> : (const void*)sa_planes_kernel<WG, false, false>;
+}
+
+const void* planes_kernel_fn(int WG, bool unit, bool smem)
+{
+    return WG == 4 ? planes_kernel_fn<4>(unit, smem) : WG == 2 ? planes_kernel_fn<2>(unit, smem)
+                                                              : planes_kernel_fn<1>(unit, smem);
+}
+
+// Tuning knob SG_PLANES_SMEM_KB: largest plane kept in shared memory (default 110 KB, so
+// that two blocks fit per SM; 0 keeps every plane in global memory).
+size_t planes_smem_limit()
+{
+    const char* e = getenv("SG_PLANES_SMEM_KB");
+    const long kb = e ? atol(e) : 110;
+    return kb > 0 ? (size_t)kb * 1024 : 0;
 }
 
 }  // namespace
 
-int32_t launch_sa_planes(int WG, const Plane* d_planes, const int* d_order, int n, unsigned* d_next,
-                         bool unit, int blocks, cudaStream_t st)
+size_t planes_smem_bytes(int WG, int max_L)
 {
-    switch (WG) {
-    case 4: return launch_planes<4>(d_planes, d_order, n, d_next, unit, blocks, st);
-    case 2: return launch_planes<2>(d_planes, d_order, n, d_next, unit, blocks, st);
-    default: return launch_planes<1>(d_planes, d_order, n, d_next, unit, blocks, st);
-    }
+    const size_t bytes = (size_t)max_L * max_L * max_L * WG * 4;
+    int dev = 0, per_block = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return bytes <= planes_smem_limit() && bytes + 1024 <= (size_t)per_block ? bytes : 0;
 }
 
-int planes_blocks(int WG, bool unit)
+int32_t launch_sa_planes(int WG, const Plane* d_planes, const int* d_order, int n, unsigned* d_next,
+                         bool unit, int blocks, cudaStream_t st, size_t smem)
+{
+    const void* fn = planes_kernel_fn(WG, unit, smem > 0);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    void* args[] = {(void*)&d_planes, (void*)&d_order, (void*)&n, (void*)&d_next};
+    cudaError_t e = cudaLaunchKernel(fn, dim3(blocks), dim3(256), args, smem, st);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("sa_planes_kernel: %s", cudaGetErrorString(e));
+        return SG_ECUDA;
+    }
+    return check("sa_planes_kernel");
+}
+
+int planes_blocks(int WG, bool unit, size_t smem)
 {
     int dev = 0, sms = 148, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaError_t e;
-    if (WG == 4)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unit ? sa_planes_kernel<4, true> : sa_planes_kernel<4, false>, 256, 0);
-    else if (WG == 2)
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unit ? sa_planes_kernel<2, true> : sa_planes_kernel<2, false>, 256, 0);
-    else
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, unit ? sa_planes_kernel<1, true> : sa_planes_kernel<1, false>, 256, 0);
+    const void* fn = planes_kernel_fn(WG, unit, smem > 0);
+    if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    const cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, 256, smem);
     if (e != cudaSuccess || per_sm < 1) {
         cudaGetLastError();
         per_sm = 1;
@@ -448,7 +508,11 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
         std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work[x] > work[y]; });
         return order;
     };
-    auto blocks_for = [&](int WG) { return planes_blocks(WG, unit); };
+    // planes of a launch sit in shared memory when the largest of them fits
+    int max_L = 0;
+    for (int a = 0; a < I; ++a) max_L = std::max(max_L, insts[members[a]]->L);
+    auto smem_for = [&](int WG) { return planes_smem_bytes(WG, max_L); };
+    auto blocks_for = [&](int WG) { return planes_blocks(WG, unit, smem_for(WG)); };
 
     // ---- autotune the words per plane: measured throughput on the batch itself, then the
     // makespan bound max(total / rate, largest plane / per-block rate) ----
@@ -462,7 +526,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
         cudaDeviceProp prop;
         cudaGetDeviceProperties(&prop, dev);
         std::ostringstream ks;
-        ks << prop.name << "/" << sms << "/" << (unit ? "u" : "g");
+        ks << prop.name << "/" << sms << "/" << (unit ? "u" : "g") << "/smem" << smem_for(1) / 1024 << "/t2";
         for (auto& m : mix)
             ks << "/" << std::get<0>(m.first) << "x" << std::get<1>(m.first) << "x" << std::get<2>(m.first) << "x" << m.second;
         key = ks.str();
@@ -489,8 +553,16 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
                 Buf d_sp, d_pl, d_ord, d_next;
                 SG_B(d_sp.alloc(words * 4, st));
                 make_planes(wg, static_cast<uint32_t*>(d_sp.p), &planes, &work, &words);
-                // trial: a few sweeps of every plane
-                const int trial_sweeps = 2;
+                // trial: a few sweeps of every plane, enough (up to 64) for about 1e9
+                // attempts, so that launch and copy costs do not decide small batches
+                double per_sweep = 0;
+                int s_min = 1 << 30;
+                for (auto& pl : planes) {
+                    per_sweep += (double)pl.L * pl.L * pl.L * 4 * wg;
+                    s_min = std::min(s_min, std::max(pl.S, 1));
+                }
+                const int trial_sweeps =
+                    std::max(2, std::min({64, s_min, (int)std::min(1e9 / std::max(per_sweep, 1.0), 1e6)}));
                 double trial_work = 0;
                 for (auto& pl : planes) {
                     pl.s_end = std::min(pl.S, trial_sweeps);
@@ -510,7 +582,8 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
                     SG_TRY_CUDA(cudaStreamSynchronize(st));
                     const auto t0 = std::chrono::steady_clock::now();
                     SG_B(launch_sa_planes(wg, static_cast<Plane*>(d_pl.p), static_cast<int*>(d_ord.p),
-                                          (int)planes.size(), static_cast<unsigned*>(d_next.p), unit, blocks, st));
+                                          (int)planes.size(), static_cast<unsigned*>(d_next.p), unit, blocks, st,
+                                          smem_for(wg)));
                     SG_TRY_CUDA(cudaStreamSynchronize(st));
                     t_best = std::min(t_best, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
                 }
@@ -593,7 +666,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
         SG_B(launch_planes_init(WG, static_cast<Plane*>(d_pl.p), n, s));
         if (timed) SG_TRY_CUDA(cudaEventRecord(ev[0], s));
         SG_B(launch_sa_planes(WG, static_cast<Plane*>(d_pl.p), static_cast<int*>(d_ord.p), n,
-                              static_cast<unsigned*>(d_next.p), unit, blocks, s));
+                              static_cast<unsigned*>(d_next.p), unit, blocks, s, smem_for(WG)));
         if (timed) SG_TRY_CUDA(cudaEventRecord(ev[1], s));
         SG_B(launch_planes_energy(WG, static_cast<Plane*>(d_pl.p), n, static_cast<unsigned long long*>(d_E.p), s));
         SG_B(launch_planes_unpack(WG, static_cast<Plane*>(d_pl.p), n, static_cast<int8_t* const*>(d_outs.p), s));

@@ -629,9 +629,14 @@ void launch_group(PlaneGroup& g, const std::vector<Request*>& act, int chunk)
                     cudaSuccess)))
         rc = SG_ECUDA;
     if (rc == SG_OK && nI) rc = launch_planes_init(g.WG, static_cast<Plane*>(g.init), nI, st);
-    if (rc == SG_OK)
-        rc = launch_sa_planes(g.WG, static_cast<Plane*>(g.pl), static_cast<int*>(g.ord), np,
-                              static_cast<unsigned*>(g.next), unit, planes_blocks(g.WG, unit), st);
+    {
+        int max_L = 0;
+        for (Request* q : g.reqs) max_L = std::max(max_L, q->L);
+        const size_t smem = planes_smem_bytes(g.WG, max_L);
+        if (rc == SG_OK)
+            rc = launch_sa_planes(g.WG, static_cast<Plane*>(g.pl), static_cast<int*>(g.ord), np,
+                                  static_cast<unsigned*>(g.next), unit, planes_blocks(g.WG, unit, smem), st, smem);
+    }
     if (rc == SG_OK) rc = launch_planes_energy(g.WG, static_cast<Plane*>(g.pl), np, static_cast<unsigned long long*>(g.E), st);
     if (rc == SG_OK && (cudaMemcpyAsync(g.hE, g.E, 8 * nE, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
                         cudaEventRecord(g.ev, st) != cudaSuccess))

@@ -118,12 +118,15 @@ struct Plane {
     uint32_t Lmagic, Hmagic;  // ceil(2^32 / L), ceil(2^32 / (L/2))
     int out;                // index of the instance in the batch
 };
+// smem > 0: each block keeps its plane in that many bytes of shared memory
+// (planes_smem_bytes gives the size for the largest side of the launch, 0 if it does not fit).
 int32_t launch_sa_planes(int WG, const Plane* d_planes, const int* d_order, int n, unsigned* d_next,
-                         bool unit, int blocks, cudaStream_t st);
+                         bool unit, int blocks, cudaStream_t st, size_t smem = 0);
+size_t planes_smem_bytes(int WG, int max_L);
 int32_t launch_planes_init(int WG, const Plane* d_planes, int n, cudaStream_t st);
 int32_t launch_planes_energy(int WG, const Plane* d_planes, int n, unsigned long long* E_out,
                              cudaStream_t st);
-int planes_blocks(int WG, bool unit);  // resident blocks of the plane kernel on this device
+int planes_blocks(int WG, bool unit, size_t smem = 0);  // resident blocks of the plane kernel
 // Runs members of a batch through one persistent plane kernel (device part captured as
 // one CUDA graph unless disabled); reports whether a graph was used and the words per
 // plane the autotuner chose.

@@ -327,3 +327,20 @@ def test_staged_equals_plain_loads(sg, monkeypatch, depth):
         assert np.array_equal(a["accepts"], b["accepts"])
     assert np.array_equal(sa_plain["spins"], sa_staged["spins"])
     assert np.array_equal(sa_plain["E"], sa_staged["E"])
+
+
+@pytest.mark.parametrize("L,R,S", [(16, 256, 20), (8, 64, 30), (24, 16, 10), (2, 12, 25), (2, 5, 40)])
+def test_planes_in_shared_memory_equal_global(sg, monkeypatch, L, R, S):
+    """Small lattices run with every plane held in shared memory for the whole run; the
+    same run with planes in global memory, the row kernels and the oracle agree."""
+    inst = sg.Instance.create(L, 7300 + L)
+    J3, _, egs = inst.get()
+    monkeypatch.setenv("SG_BATCH_PLANES", "1")
+    smem = sg.sa_run(inst, R, S, 0.1, 3.0, seed=4, spins="host")
+    monkeypatch.setenv("SG_PLANES_SMEM_KB", "0")
+    glob = sg.sa_run(inst, R, S, 0.1, 3.0, seed=4, spins="host")
+    monkeypatch.setenv("SG_BATCH_PLANES", "0")
+    rows = sg.sa_run(inst, R, S, 0.1, 3.0, seed=4, spins="host")
+    for other in (glob, rows):
+        assert np.array_equal(smem["spins"], other["spins"]) and np.array_equal(smem["E"], other["E"])
+    _sa_compare(sg, inst, J3, egs, R, S, 0.1, 3.0, seed=4, reps=[0, R // 2, R - 1])
