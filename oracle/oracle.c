@@ -22,7 +22,8 @@
  * frustrated faces (F22: two adjacent faces, F42: four faces with the two
  * unfrustrated ones opposite, F6: all six); the sum in Eq. 1 runs once over each
  * lattice edge; sites are swept in checkerboard order (colour 0, then colour 1);
- * the Metropolis draw is accepted when u < floor(2^32 exp(-beta dE)).
+ * the Metropolis draw is accepted when u < floor(2^32 exp(-beta dE)), with the
+ * 32-bit uniform u of an attempt assembled from two Philox blocks (metropolis_uniform).
  */
 #include "oracle.h"
 
@@ -342,6 +343,23 @@ int8_t or_init_spin(uint64_t seed, uint32_t instance_id, int64_t i, int rep)
     return (w >> 31) ? -1 : +1;
 }
 
+/* The 32-bit uniform of replica rep's attempt at site i in sweep `sweep` (our RNG
+ * contract; the paper fixes none).  Its leading byte is byte rep%4 of word (rep/4)%4 of
+ * the block at counter (i, sweep, rep/16, METROPOLIS), so one block serves sixteen
+ * replicas; its low 24 bits are the top 24 bits of word rep%4 of the block at counter
+ * (i, sweep, rep/4, TAIL).  The two blocks are independent and uniform, so u is uniform
+ * on [0, 2^32).  (A fast implementation needs the tail only when the leading byte
+ * equals the threshold's; the result is the same.) */
+static uint32_t metropolis_uniform(uint32_t k0, uint32_t k1, int64_t i, uint32_t sweep, int rep)
+{
+    uint32_t lead = philox_word(k0, k1, (uint32_t)i, sweep, (uint32_t)(rep / 16),
+                                OR_DOMAIN_METROPOLIS, (rep / 4) % 4);
+    uint32_t tail = philox_word(k0, k1, (uint32_t)i, sweep, (uint32_t)(rep / 4),
+                                OR_DOMAIN_TAIL, rep % 4);
+    uint32_t a = (lead >> (8 * (rep % 4))) & 0xFFu;
+    return (a << 24) | (tail >> 8);
+}
+
 /* One Metropolis attempt at site i of replica rep during sweep `sweep`.
  * x = s_i h_i; flipping changes E by -2x.  Accept when x >= 0, else when the
  * draw u is below the threshold for dE = -2x.  Returns the energy change. */
@@ -354,8 +372,7 @@ static int metropolis_attempt(int L, const int8_t* J3, int8_t* s, int64_t i,
     if (x >= 0) {
         accept = 1;
     } else {
-        uint32_t u = philox_word(k0, k1, (uint32_t)i, sweep, (uint32_t)(rep / 4),
-                                 OR_DOMAIN_METROPOLIS, rep % 4);
+        uint32_t u = metropolis_uniform(k0, k1, i, sweep, rep);
         accept = u < or_metropolis_threshold(beta, -2 * x);
     }
     if (!accept) return 0;

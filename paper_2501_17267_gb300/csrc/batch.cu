@@ -46,10 +46,16 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
                                                         unsigned* __restrict__ next)
 {
     constexpr int U = 4 / WG;
+    constexpr int kTieCap = 32;  // queued tied draws per warp
     extern __shared__ __align__(16) uint32_t s_plane[];
     __shared__ int s_item;
     __shared__ uint32_t s_thr[kThrRow];
+    __shared__ uint4 s_ties[8 * kTieCap];
+    __shared__ int s_tie_n[8];
     const int tid = threadIdx.x, nthreads = blockDim.x;
+    const int warp = tid >> 5, lane = tid & 31;
+    const mp::TieList ties{s_ties + warp * kTieCap, &s_tie_n[warp], kTieCap};
+    if (tid < 8) s_tie_n[tid] = 0;
     for (;;) {
         if (tid == 0) s_item = (int)atomicAdd(next, 1u);
         __syncthreads();
@@ -82,11 +88,31 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
         for (int sw = p.s_begin; sw < p.s_end; ++sw) {
             if (tid < kThrRow) s_thr[tid] = p.thr[(size_t)sw * kThrRow + tid];
             __syncthreads();
+            const uint4 lead = UNITJ ? mp::lead_record(s_thr, s_thr, s_thr, s_thr) : make_uint4(0, 0, 0, 0);
+            // Deferred ties of this warp, decided by all its lanes together (every lane
+            // runs the same iterations of the site loop below).
+            auto resolve_list = [&]() {
+                __syncwarp();
+                const int n = min(*ties.count, kTieCap);
+                for (int e = lane; e < n; e += 32) {
+                    const uint4 t = ties.entries[e];
+                    const uint32_t w = t.z & 0xFFFFu, nib = t.z >> 16;
+                    const uint32_t tie =
+                        ((nib & 1u) << 7) | ((nib & 2u) << 14) | ((nib & 4u) << 21) | ((nib & 8u) << 28);
+                    const uint32_t acc_t = mp::resolve_ties(tie, t.w, s_thr, 0, t.x, (uint32_t)sw, w, key.k0, key.k1);
+                    if (acc_t) sp[(size_t)t.y * WG + (w - (uint32_t)p.w0)] ^= mp::prmt(acc_t, 0u, 0xBA98u) & 0xFEFEFEFEu;
+                }
+                __syncwarp();
+                if (lane == 0) *ties.count = 0;
+                __syncwarp();
+            };
             for (int colour = 0; colour < 2; ++colour) {
                 // U = 4 / WG sites per thread at a time: all their loads, then all their
                 // updates and stores (sites of one colour never read one another), so the
-                // U Philox chains and load streams overlap
-                for (int q0 = tid; q0 < half; q0 += U * nthreads) {
+                // U Philox chains and load streams overlap.  The loop bound depends only on
+                // the warp, so the warp stays converged; slots past the end are idle.
+                for (int qb = tid - lane; qb < half; qb += U * nthreads) {
+                    const int q0 = qb + lane;
                     int is_[U], i_[U];
                     bool live[U];
                     mp::Couplings cp[U];
@@ -94,7 +120,7 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         live[u] = q0 + u * nthreads < half;
-                        const int q = live[u] ? q0 + u * nthreads : q0;  // an idle slot redoes q0, unstored
+                        const int q = live[u] ? q0 + u * nthreads : 0;  // an idle slot reads site 0, unstored
                         const int row = H == 1 ? q : div_magic(q, p.Hmagic);  // ceil(2^32 / 1) does not fit
                         const int j = q - row * H;
                         const int z = div_magic(row, p.Lmagic);
@@ -122,12 +148,18 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
                     }
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        const bool flip = mp::update_words<false, WG, 0, true>(
-                            self[u], P[u], vmask, cp[u].msum, (uint32_t)i_[u], (uint32_t)sw, (uint32_t)p.w0, key,
-                            s_thr, acc);
+                        uint32_t vm[WG];  // an idle slot has no replicas: no flips, no ties
+#pragma unroll
+                        for (int wi = 0; wi < WG; ++wi) vm[wi] = live[u] ? vmask[wi] : 0u;
+                        const bool flip = mp::update_words<false, UNITJ, WG, 0, true>(
+                            self[u], P[u], vm, cp[u].msum, (uint32_t)i_[u], (uint32_t)sw, (uint32_t)p.w0, key,
+                            s_thr, &lead, acc, &ties, (uint32_t)is_[u]);
                         if (live[u] && flip) mp::store_words<WG>(sp + (size_t)is_[u] * WG, self[u]);
                     }
+                    __syncwarp();
+                    if (*ties.count >= kTieCap / 2) resolve_list();
                 }
+                resolve_list();  // the next colour reads these sites
                 __syncthreads();
             }
         }

@@ -211,13 +211,24 @@ half_sweep_kernel(uint32_t* __restrict__ spins, const uint2* const* __restrict__
             }
         }
         if (need) {
-            const Philox4 u = philox4x32_10((uint32_t)g.i, sweep, (uint32_t)w, kDomainMetropolis,
+            // the draw of replica 4w + b: leading byte b of word w mod 4 of the block at
+            // (site, sweep, w / 4, 0); its low 24 bits (word b of the block at
+            // (site, sweep, w, 4), top 24 bits) only when the leading bytes tie
+            const Philox4 u = philox4x32_10((uint32_t)g.i, sweep, (uint32_t)w >> 2, kDomainMetropolis,
                                             key.k0, key.k1);
+            const int wm = w & 3;
+            const uint32_t lead = wm == 0 ? u.v[0] : wm == 1 ? u.v[1] : wm == 2 ? u.v[2] : u.v[3];
 #pragma unroll
             for (int b = 0; b < 4; ++b) {
                 if (!((valid >> b) & 1) || kb[b] <= 0) continue;
                 const uint32_t th = MODE_PT ? s_thr[(4 * w + b) * kThrRow + kb[b]] : s_thr[kb[b]];
-                if (u.v[b] < th) {
+                const uint32_t a8 = (lead >> (8 * b)) & 0xFFu, t8 = th >> 24;
+                bool accept = a8 < t8;
+                if (a8 == t8 && (th & 0xFFFFFFu)) {
+                    const Philox4 t = philox4x32_10((uint32_t)g.i, sweep, (uint32_t)w, kDomainTail, key.k0, key.k1);
+                    accept = (t.v[b] >> 8) < (th & 0xFFFFFFu);
+                }
+                if (accept) {
                     flip |= 0xFEu << (8 * b);
                     dE[b] += 2 * kb[b];
                 }

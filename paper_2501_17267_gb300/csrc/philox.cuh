@@ -66,6 +66,7 @@ constexpr uint32_t kDomainMetropolis = 0;
 constexpr uint32_t kDomainExchange = 1;
 constexpr uint32_t kDomainGenerate = 2;
 constexpr uint32_t kDomainGauge = 3;
+constexpr uint32_t kDomainTail = 4;  // low 24 bits of a Metropolis draw, counter (site, sweep, word, 4)
 constexpr uint32_t kSweepInit = 0xFFFFFFFFu;
 
 }  // namespace sg

@@ -34,6 +34,7 @@ namespace sg {
 namespace {
 
 constexpr int kThrStride = 17;   // per-slot threshold row stride in shared memory (bank spread)
+constexpr int kTieCap = 32;      // queued tied draws per warp
 
 // Words of the staged PT variant's threshold table in dynamic shared memory (Rp slots),
 // rounded so that the row buffers after it stay 128-byte aligned.
@@ -73,6 +74,9 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
     __shared__ int s_dE[PT ? 256 : 1];
     extern __shared__ __align__(128) uint32_t s_stage[];  // NST > 0: [thr][TY][NST][6][segw]
     __shared__ uint64_t s_bar[NST > 0 ? 8 * NST : 1];
+    __shared__ uint4 s_lead[PT ? 64 : 1];  // PT: leading threshold bytes per word (unit couplings)
+    __shared__ uint4 s_ties[8 * kTieCap];  // per warp: draws whose leading byte tied
+    __shared__ int s_tie_n[8];
 
     const int inst = blockIdx.y;
     const int L = a.L, Wn = a.Wn, G = a.G;
@@ -104,7 +108,20 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
             ac::mbar_fence_init();
         }
     }
+    if (tid < 8) s_tie_n[tid] = 0;
     __syncthreads();
+    uint4 lead_sa = make_uint4(0, 0, 0, 0);  // SA: one record for every word
+    if (UNITJ) {
+        if (PT) {
+            for (int q = tid; q < Wn; q += nthreads) {
+                const uint32_t* t0 = s_thr + 4 * q * kThrStride;
+                s_lead[q] = mp::lead_record(t0, t0 + kThrStride, t0 + 2 * kThrStride, t0 + 3 * kThrStride);
+            }
+            __syncthreads();
+        } else {
+            lead_sa = mp::lead_record(s_thr, s_thr, s_thr, s_thr);
+        }
+    }
 
     const int g = threadIdx.x % G;
     const int j0 = threadIdx.x / G;
@@ -155,6 +172,37 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
             }
     };
     int items = 0;  // site updates folded into the 8-bit lanes since the last flush
+
+    // Deferred ties of this thread's warp.  resolve_list() is called by every live lane of
+    // the warp at a convergent point: the lanes share the queued entries, decide each from
+    // the low 24 bits of its draws, and flip the accepted bytes in global memory (the
+    // warp's own earlier stores to those words are ordered before by __syncwarp).
+    const int warp = tid >> 5, lane32 = tid & 31;
+    const mp::TieList ties{s_ties + warp * kTieCap, &s_tie_n[warp], kTieCap};
+    const int warp_lanes = min(32, nthreads - 32 * warp);  // the block's last warp may be partial
+    const unsigned wm = warp_lanes == 32 ? 0xFFFFFFFFu : (1u << warp_lanes) - 1u;
+    auto resolve_list = [&]() {
+        __syncwarp(wm);
+        const int n = min(*ties.count, kTieCap);
+        const int lanes = __popc(wm), rank = __popc(wm & ((1u << lane32) - 1u));
+        for (int e = rank; e < n; e += lanes) {
+            const uint4 t = ties.entries[e];
+            const uint32_t w = t.z & 0xFFFFu, nib = t.z >> 16;
+            const uint32_t tie = ((nib & 1u) << 7) | ((nib & 2u) << 14) | ((nib & 4u) << 21) | ((nib & 8u) << 28);
+            const uint32_t* row = PT ? s_thr + 4 * w * kThrStride : s_thr;
+            const uint32_t acc_t = mp::resolve_ties(tie, t.w, row, PT ? kThrStride : 0, t.x, sweep, w, key.k0, key.k1);
+            if (acc_t) {
+                const uint32_t ff = mp::prmt(acc_t, 0u, 0xBA98u);
+                s[(size_t)t.y * Wn + w] ^= ff & 0xFEFEFEFEu;
+                if (PT)
+                    for (int b = 0; b < 4; ++b)
+                        if ((acc_t >> (8 * b + 7)) & 1u) atomicAdd(&s_dE[4 * w + b], 2 * (int)((t.w >> (8 * b)) & 0xFFu));
+            }
+        }
+        __syncwarp(wm);
+        if (rank == 0) *ties.count = 0;
+        __syncwarp(wm);
+    };
 
     if constexpr (NST > 0) {
         // rows c = 0, 1, ... of this warp: (c * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y
@@ -219,8 +267,10 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
                     for (int wi = 0; wi < WG; ++wi) P[wi] += mp::bond_term(n[wi], cp, q);
                 }
                 const uint32_t* thr = PT ? s_thr + 4 * w0 * kThrStride : s_thr;
-                if (mp::update_words<PT, WG, kThrStride, DRAW>(self, P, vmask[ch], cp.msum, (uint32_t)i,
-                                                               sweep, (uint32_t)w0, key, thr, acc[ch]))
+                if (mp::update_words<PT, UNITJ, WG, kThrStride, true>(self, P, vmask[ch], cp.msum, (uint32_t)i,
+                                                                     sweep, (uint32_t)w0, key, thr,
+                                                                     PT ? s_lead + w0 : &lead_sa, acc[ch],
+                                                                     &ties, (uint32_t)is))
                     mp::store_words<WG>(s + (size_t)is * Wn + w0, self);
             }
             if (PT && ++items == mp::kLaneCapacity<KMAX>) {
@@ -228,6 +278,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
                 items = 0;
             }
             __syncwarp();  // every lane is done with slot c % NST
+            if (*ties.count >= kTieCap / 2) resolve_list();
             if (lane == 0 && c + NST < a.rows_per_thread && row_of(c + NST) < LL) {
                 ac::fence_proxy_async();
                 issue(c + NST);
@@ -278,8 +329,10 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
                         for (int wi = 0; wi < WG; ++wi) P[wi] += mp::bond_term(n[wi], cp, q);
                     }
                     const uint32_t* thr = PT ? s_thr + 4 * w0 * kThrStride : s_thr;
-                    if (mp::update_words<PT, WG, kThrStride, DRAW>(self, P, vmask[ch], cp.msum, (uint32_t)i,
-                                                             sweep, (uint32_t)w0, key, thr, acc[ch]))
+                    if (mp::update_words<PT, UNITJ, WG, kThrStride, true>(self, P, vmask[ch], cp.msum,
+                                                                         (uint32_t)i, sweep, (uint32_t)w0, key,
+                                                                         thr, PT ? s_lead + w0 : &lead_sa,
+                                                                         acc[ch], &ties, (uint32_t)is))
                         mp::store_words<WG>(s + (size_t)is * Wn + w0, self);
                 }
                 if (PT && ++items == mp::kLaneCapacity<KMAX>) {
@@ -291,6 +344,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
 
     }
 
+    resolve_list();
     if (PT) {
         flush();
         __syncthreads();
@@ -394,7 +448,7 @@ SweepShape sweep_shape(int I, int L, int Wn, bool pt, bool pad)
         const int nst = stage_depth();
         const size_t ring = (size_t)TY * nst * 6 * (size_t)(H * Wn) * 4;
         const size_t thr = pt ? (size_t)staged_thr_words(4 * Wn) * 4 : 0;
-        const size_t fixed = pt ? 256 * 4 + 8 * 8 * 3 + 64 : kThrRow * 4 + 8 * 8 * 3 + 64;
+        const size_t fixed = (pt ? 256 * 4 + 64 * 16 : kThrRow * 4 + 16) + 8 * 8 * 3 + 8 * kTieCap * 16 + 32 + 64;
         const size_t need = ring + thr;
         const long long fit = (long long)per_sm / (long long)(need + fixed + 1024);
         if ((long long)need <= per_block && fit >= 1) {

@@ -53,6 +53,7 @@ __global__ void __launch_bounds__(256, 2) sweep_tile_kernel(const TileArgs a)
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ uint64_t bars[kRing];
     __shared__ uint32_t s_thr[PT ? 256 * kThrStrideT : kThrRow];
+    __shared__ uint4 s_lead[PT ? 64 : 1];  // PT: leading threshold bytes per word (unit couplings)
     __shared__ int s_dE[PT ? 256 : 1];
     __shared__ int s_abort;
 
@@ -87,6 +88,18 @@ __global__ void __launch_bounds__(256, 2) sweep_tile_kernel(const TileArgs a)
         for (int q = tid; q < kThrRow; q += nthreads) s_thr[q] = a.thr[q];
     }
     __syncthreads();
+    uint4 lead_sa = make_uint4(0, 0, 0, 0);  // SA: one record for every word
+    if (UNITJ) {
+        if (PT) {
+            for (int q = tid; q < Wn; q += nthreads) {
+                const uint32_t* t0 = s_thr + 4 * q * kThrStrideT;
+                s_lead[q] = mp::lead_record(t0, t0 + kThrStrideT, t0 + 2 * kThrStrideT, t0 + 3 * kThrStrideT);
+            }
+            __syncthreads();
+        } else {
+            lead_sa = mp::lead_record(s_thr, s_thr, s_thr, s_thr);
+        }
+    }
 
     // slab k (k = -1 .. ZC) of the unit lives in ring buffer (k+1) % kRing, as that
     // buffer's ((k+1)/kRing)-th fill
@@ -209,9 +222,9 @@ __global__ void __launch_bounds__(256, 2) sweep_tile_kernel(const TileArgs a)
                         for (int wi = 0; wi < WG; ++wi) P[wi] += mp::bond_term(n[wi], cp, q);
                     }
                     const uint32_t* thr = PT ? s_thr + 4 * w0 * kThrStrideT : s_thr;
-                    if (mp::update_words<PT, WG, kThrStrideT>(self, P, vmask[ch], cp.msum, (uint32_t)i,
-                                                              a.sweep, (uint32_t)w0, key, thr,
-                                                              acc[ch]))
+                    if (mp::update_words<PT, UNITJ, WG, kThrStrideT>(self, P, vmask[ch], cp.msum, (uint32_t)i,
+                                                                     a.sweep, (uint32_t)w0, key, thr,
+                                                                     PT ? s_lead + w0 : &lead_sa, acc[ch]))
                         mp::store_words<WG>(s + ((size_t)(z * L + y) * L + px) * Wn + w0, self);
                 }
             }
