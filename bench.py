@@ -47,12 +47,29 @@ def _peaks():
         return 6800.0, "fallback", 2070.0
 
 
-# Integer roof of one attempt: every attempt consumes one 32-bit Philox4x32-10 word, and
-# a Philox call (4 words) makes 20 32x32->64-bit multiplies, i.e. 5 per attempt.  The SM
-# executes 32 such multiplies per clock (64 IMAD lanes, two IMADs -- high and low half --
-# per product), so the multiply pipe alone caps a GB300 at SMs * 32 / 5 attempts per clock.
-MULS_PER_ATTEMPT = 5
+# Roofs of one attempt.  HBM: 1 B of spin read and 1 B written per sweep plus 3/R B of
+# couplings (bytes_per_attempt).  Integer: an attempt's leading draw byte is a quarter of
+# a Philox4x32-10 word, and a Philox block (16 bytes) costs 20 32x32->64-bit multiplies,
+# i.e. 1.25 per attempt (the low 24 bits are drawn for 1/256 of the draws); the SM runs 32
+# such multiplies per clock, so the multiply pipe caps a GB300 at SMs * 32 / 1.25
+# attempts per clock -- above the HBM roof, which therefore binds.
+MULS_PER_ATTEMPT = 1.25
 WIDE_MULS_PER_SM_CLOCK = 32
+
+
+def _roof(rate, bytes_per_attempt, sms, sm_mhz, peak, peak_kind, **extra):
+    """The roofline object: HBM bound (algorithmic bytes / s against the measured copy
+    bandwidth), with the integer-multiply view beside it."""
+    gbs = rate * bytes_per_attempt / 1e9
+    alu_peak = sms * WIDE_MULS_PER_SM_CLOCK / MULS_PER_ATTEMPT * sm_mhz * 1e6
+    r = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+         "peak_source": peak_kind, "bytes_per_attempt": bytes_per_attempt,
+         "attempts_per_s": rate,
+         "alu": {"achieved": rate, "peak": alu_peak, "unit": "attempts/s", "frac": rate / alu_peak,
+                 "peak_source": f"derived: {sms} SMs x {WIDE_MULS_PER_SM_CLOCK} 32x32->64 multiplies per "
+                                f"clock / {MULS_PER_ATTEMPT} per attempt at {sm_mhz:.0f} MHz"}}
+    r.update(extra)
+    return r
 
 
 def _traffic_record():
@@ -350,16 +367,11 @@ def batched_line(sg, args, torch, clocks_cls, local):
     sw = st["sweep"]
     peak, peak_kind, sm_mhz = _peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak = sms * WIDE_MULS_PER_SM_CLOCK / MULS_PER_ATTEMPT * sm_mhz * 1e6
-    bpa = 2.0 + 3.0 / w.replicas
     roof = None
     if sw["device_ms"] > 0:
-        rate = sw["units"] / (sw["device_ms"] / 1000.0)
-        roof = {"bound": "alu", "achieved": rate, "peak": alu_peak, "unit": "attempts/s",
-                "frac": rate / alu_peak, "traffic": None, "kernel": "sa_planes_kernel",
-                "launch_ms": sw["device_ms"] / max(sw["launches"], 1),
-                "hbm": {"achieved": rate * bpa / 1e9, "peak": peak, "unit": "GB/s",
-                        "frac": rate * bpa / 1e9 / peak, "peak_source": peak_kind}}
+        roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), 2.0 + 3.0 / w.replicas, sms, sm_mhz, peak,
+                     peak_kind, traffic=None, kernel="sa_planes_kernel",
+                     launch_ms=sw["device_ms"] / max(sw["launches"], 1))
     value = attempts * args.steps / (ms / 1000.0)
     eps = [float(e) for o in out for e in o["eps"][:4]]
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -402,14 +414,13 @@ def sa_line(sg, args, torch, clocks_cls, local):
     sw = st["sweep"]
     peak, peak_kind, sm_mhz = _peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak = sms * WIDE_MULS_PER_SM_CLOCK / MULS_PER_ATTEMPT * sm_mhz * 1e6
     roof = None
     if sw["launches"] and sw["device_ms"] > 0:
-        rate = sw["units"] / (sw["device_ms"] / 1000.0)
-        roof = {"bound": "alu", "achieved": rate, "peak": alu_peak, "unit": "attempts/s",
-                "frac": rate / alu_peak, "traffic": None, "kernel": "sweep_rows_kernel<SA>",
-                "launch_ms": sw["device_ms"] / sw["launches"],
-                "share_of_step": sw["device_ms"] / ms}
+        roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), 2.0 + 3.0 / w.replicas, sms, sm_mhz, peak,
+                     peak_kind, traffic=None,
+                     kernel="sa_planes_kernel" if sw["launches"] <= 4 * steps else "sweep_rows_kernel<SA>",
+                     launch_ms=sw["device_ms"] / sw["launches"], share_of_step=sw["device_ms"] / ms,
+                     note="working set 4 MB: L2- or shared-memory-resident, so HBM is not what limits it")
     eps = out["eps"]
     return {"metric": METRIC, "value": attempts * steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1,
             "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / steps,
@@ -560,27 +571,17 @@ def main():
     sw = st["sweep"]
     peak, peak_kind, sm_mhz = _peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
-    alu_peak = sms * WIDE_MULS_PER_SM_CLOCK / MULS_PER_ATTEMPT * sm_mhz * 1e6
     roof = None
     if sw["launches"] and sw["device_ms"] > 0:
         per_launch_s = sw["device_ms"] / 1000.0 / sw["launches"]
         attempts_per_launch = sw["units"] / sw["launches"]
-        bytes_per_launch = attempts_per_launch * BYTES_PER_ATTEMPT
-        gbs = bytes_per_launch / per_launch_s / 1e9
-        rate = attempts_per_launch / per_launch_s
         rec = _traffic_record()
-        roof = {"bound": "alu", "achieved": rate, "peak": alu_peak, "unit": "attempts/s",
-                "frac": rate / alu_peak,
-                "traffic": rec["traffic_bytes_per_launch"] if rec else None,
-                "traffic_unit": "DRAM bytes per launch (ncu)",
-                "algorithmic_bytes_per_launch": bytes_per_launch,
-                "peak_source": f"derived: {sms} SMs x {WIDE_MULS_PER_SM_CLOCK} 32x32->64 multiplies "
-                               f"per clock / {MULS_PER_ATTEMPT} per attempt at {sm_mhz:.0f} MHz",
-                "hbm": {"achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-                        "peak_source": peak_kind},
-                "kernel": "sweep_rows_kernel<PT>", "launch_ms": 1000 * per_launch_s,
-                "attempts_per_launch": attempts_per_launch,
-                "share_of_step": sw["device_ms"] / ms}
+        roof = _roof(attempts_per_launch / per_launch_s, BYTES_PER_ATTEMPT, sms, sm_mhz, peak, peak_kind,
+                     traffic=rec["traffic_bytes_per_launch"] if rec else None,
+                     traffic_unit="DRAM bytes per launch (ncu)",
+                     algorithmic_bytes_per_launch=attempts_per_launch * BYTES_PER_ATTEMPT,
+                     kernel="sweep_rows_kernel<PT>", launch_ms=1000 * per_launch_s,
+                     attempts_per_launch=attempts_per_launch, share_of_step=sw["device_ms"] / ms)
 
     # end to end: host couplings in, results out, inside the timed region
     e2e = None
