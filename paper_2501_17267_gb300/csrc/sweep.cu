@@ -213,25 +213,30 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
         const int lane = threadIdx.x;
         auto row_of = [&](int c) { return (c * (int)gridDim.x + (int)blockIdx.x) * (int)blockDim.y + (int)threadIdx.y; };
         // lane 0: the six half rows of row c into ring slot c % NST
+        // the whole warp: the six half rows of row c into ring slot c % NST, lane k < 6
+        // issuing copy k after lane 0 has announced the bytes
         auto issue = [&](int c) {
-            const int row = row_of(c);
-            const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
-            const int y = row - z * L;
-            const int par = (y + z + a.colour) & 1;
-            const int src[6] = {row, row, row + (y + 1 == L ? 1 - L : 1), row + (y == 0 ? L - 1 : -1),
-                                row + (z + 1 == L ? 1 - L : 1) * L, row + (z == 0 ? L - 1 : -1) * L};
-            uint32_t* dst = ring + (size_t)(c % NST) * 6 * segw;
             uint64_t* bar = &bars[c % NST];
-            ac::mbar_expect_tx(bar, 6u * seg_bytes);
-#pragma unroll
-            for (int k = 0; k < 6; ++k) {
-                const int half = k == 1 ? 1 - par : par;  // x neighbours sit in the other half
-                ac::bulk_g2s(dst + (size_t)k * segw, s + ((size_t)src[k] * L + (size_t)half * H) * Wn, seg_bytes, bar);
+            if (lane == 0) ac::mbar_expect_tx(bar, 6u * seg_bytes);
+            __syncwarp();
+            if (lane < 6) {
+                const int row = row_of(c);
+                const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
+                const int y = row - z * L;
+                const int par = (y + z + a.colour) & 1;
+                const int src = lane < 2    ? row
+                                : lane == 2 ? row + (y + 1 == L ? 1 - L : 1)
+                                : lane == 3 ? row + (y == 0 ? L - 1 : -1)
+                                : lane == 4 ? row + (z + 1 == L ? 1 - L : 1) * L
+                                            : row + (z == 0 ? L - 1 : -1) * L;
+                const int half = lane == 1 ? 1 - par : par;  // x neighbours sit in the other half
+                ac::fence_proxy_async();  // this slot's earlier reads come before the refill
+                ac::bulk_g2s(ring + (size_t)(c % NST) * 6 * segw + (size_t)lane * segw,
+                             s + ((size_t)src * L + (size_t)half * H) * Wn, seg_bytes, bar);
             }
         };
-        if (lane == 0)
-            for (int c = 0; c < NST && c < a.rows_per_thread; ++c)
-                if (row_of(c) < LL) issue(c);
+        for (int c = 0; c < NST && c < a.rows_per_thread; ++c)
+            if (row_of(c) < LL) issue(c);
         bool ok = true;
         int c = 0;
         for (; c < a.rows_per_thread; ++c) {
@@ -279,10 +284,7 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
             }
             __syncwarp();  // every lane is done with slot c % NST
             if (*ties.count >= kTieCap / 2) resolve_list();
-            if (lane == 0 && c + NST < a.rows_per_thread && row_of(c + NST) < LL) {
-                ac::fence_proxy_async();
-                issue(c + NST);
-            }
+            if (c + NST < a.rows_per_thread && row_of(c + NST) < LL) issue(c + NST);
         }
         if (!ok) {
             // a copy did not arrive: report it, then wait (bounded) for the copies this
