@@ -282,7 +282,7 @@ int32_t sg_server_destroy(sg_server* srv);
  *   E_dev      device int64 [n_configs], written
  * No cudaMalloc, cudaFree or allocating library routine is called.  All scratch lives
  * in one fixed array of SG_NOALLOC_SCRATCH_BYTES per device; a request that needs more
- * (about 8*L^3 + L^3 * 4*ceil(n_configs/4) bytes) fails with SG_EINVAL and a message.
+ * (about 9*L^3 + L^3 * 4*ceil(n_configs/32) bytes) fails with SG_EINVAL and a message.
  * The first call on a device looks up the array's device address (with that device
  * current); make that first call before any stream capture.  Every call shares the
  * array and it keeps the last call's contents (the call clears what must start at

@@ -344,19 +344,25 @@ int8_t or_init_spin(uint64_t seed, uint32_t instance_id, int64_t i, int rep)
 }
 
 /* The 32-bit uniform of replica rep's attempt at site i in sweep `sweep` (our RNG
- * contract; the paper fixes none).  Its leading byte is byte rep%4 of word (rep/4)%4 of
- * the block at counter (i, sweep, rep/16, METROPOLIS), so one block serves sixteen
- * replicas; its low 24 bits are the top 24 bits of word rep%4 of the block at counter
- * (i, sweep, rep/4, TAIL).  The two blocks are independent and uniform, so u is uniform
- * on [0, 2^32).  (A fast implementation needs the tail only when the leading byte
- * equals the threshold's; the result is the same.) */
+ * contract; the paper fixes none).  Replicas come in groups of 32 (g = rep / 32, bit
+ * b = rep % 32).  The leading byte A of the draw has, for j = 0..7, bit j equal to bit b
+ * of word j % 4 of the block at counter (i, sweep, 2g + j / 4, METROPOLIS): two blocks
+ * give the eight bit planes of the leading bytes of all 32 replicas of a group.  Its low
+ * 24 bits are the top 24 bits of word rep % 4 of the block at counter
+ * (i, sweep, rep / 4, TAIL).  The blocks are independent and uniform, so u is uniform on
+ * [0, 2^32).  (A fast implementation needs the tail only when A equals the threshold's
+ * leading byte; the result is the same.) */
 static uint32_t metropolis_uniform(uint32_t k0, uint32_t k1, int64_t i, uint32_t sweep, int rep)
 {
-    uint32_t lead = philox_word(k0, k1, (uint32_t)i, sweep, (uint32_t)(rep / 16),
-                                OR_DOMAIN_METROPOLIS, (rep / 4) % 4);
+    int g = rep / 32, b = rep % 32;
+    uint32_t a = 0;
+    for (int j = 0; j < 8; ++j) {
+        uint32_t plane = philox_word(k0, k1, (uint32_t)i, sweep, (uint32_t)(2 * g + j / 4),
+                                     OR_DOMAIN_METROPOLIS, j % 4);
+        a |= ((plane >> b) & 1u) << j;
+    }
     uint32_t tail = philox_word(k0, k1, (uint32_t)i, sweep, (uint32_t)(rep / 4),
                                 OR_DOMAIN_TAIL, rep % 4);
-    uint32_t a = (lead >> (8 * (rep % 4))) & 0xFFu;
     return (a << 24) | (tail >> 8);
 }
 

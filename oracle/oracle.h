@@ -15,7 +15,7 @@ extern "C" {
 
 enum { OR_CLASS_F22 = 0, OR_CLASS_F42 = 1, OR_CLASS_F6 = 2 };
 enum {
-    OR_DOMAIN_METROPOLIS = 0, /* init: (site, 0xFFFFFFFF, replica/4, 0); draws: (site, sweep, replica/16, 0) */
+    OR_DOMAIN_METROPOLIS = 0, /* init: (site, 0xFFFFFFFF, replica/4, 0); draws: (site, sweep, 2*(replica/32) + j/4, 0) */
     OR_DOMAIN_EXCHANGE = 1,   /* counter (rung pair k, sweep, 0, 1)  */
     OR_DOMAIN_GENERATE = 2,   /* counter (tile, 0, 0, 2)              */
     OR_DOMAIN_GAUGE = 3,      /* counter (site, 0, 0, 3)              */

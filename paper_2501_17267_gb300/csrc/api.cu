@@ -283,7 +283,7 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
     const int L = first->L;
     const int64_t N = first->N;
     const int R = p.replicas;
-    const int Wn = (R + 3) / 4, Rp = 4 * Wn;
+    const int Wn = words_for(R), Rp = 32 * Wn;
     const int S = p.sweeps;
 
     std::vector<double> beta((size_t)std::max(S, 1));
@@ -306,7 +306,7 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
     bool unit_j = true;  // every coupling of the group has |J| = 1
     for (int a = 0; a < I; ++a) unit_j &= insts[members[a]]->unit_couplings;
     DevBuf d_spins, d_E, d_E64, d_thr, d_keys, d_j6, d_flag, d_stage;
-    SG_RET(d_spins.alloc((size_t)I * N * Rp, st));
+    SG_RET(d_spins.alloc((size_t)I * N * Wn * 4, st));
     SG_RET(d_E.alloc(sizeof(int32_t) * (size_t)I * Rp, st));
     SG_RET(d_E64.alloc(sizeof(unsigned long long) * (size_t)I * Rp, st));
     SG_RET(d_thr.alloc(sizeof(uint32_t) * thr.size(), st));
@@ -390,7 +390,7 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     const int L = first->L;
     const int64_t N = first->N;
     const int K = p.temps;
-    const int Wn = (K + 3) / 4, Rp = 4 * Wn;
+    const int Wn = words_for(K), Rp = 32 * Wn;
     const int S = p.sweeps;
 
     std::vector<double> ladder(K);
@@ -418,7 +418,7 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     for (int a = 0; a < I; ++a) unit_j &= insts[members[a]]->unit_couplings;
     DevBuf d_spins, d_E, d_E64, d_thr, d_keys, d_j6, d_flag, d_stage, d_perm, d_inv, d_acc, d_min,
         d_xtab, d_xoff, d_xlen, d_xtail, d_done;
-    SG_RET(d_spins.alloc((size_t)I * N * Rp, st));
+    SG_RET(d_spins.alloc((size_t)I * N * Wn * 4, st));
     SG_RET(d_E.alloc(sizeof(int32_t) * (size_t)I * Rp, st));
     SG_RET(d_E64.alloc(sizeof(unsigned long long) * (size_t)I * Rp, st));
     SG_RET(d_thr.alloc(sizeof(uint32_t) * thr.size(), st));
@@ -676,7 +676,7 @@ extern "C" int32_t sg_energy(const sg_instance* inst_c, const int8_t* spins, int
     sg_instance* inst = const_cast<sg_instance*>(inst_c);
     cudaStream_t st = (cudaStream_t)stream;
     const int64_t N = inst->N;
-    const int R = n_configs, Wn = (R + 3) / 4, Rp = 4 * Wn;
+    const int R = n_configs, Wn = words_for(R), Rp = 32 * Wn;
     const uint2* j6 = nullptr;
     SG_RET(instance_device_j6(inst, st, &j6, nullptr));
     DevBuf d_in, d_packed, d_E64, d_j6, d_bad;
@@ -686,7 +686,7 @@ extern "C" int32_t sg_energy(const sg_instance* inst_c, const int8_t* spins, int
         SG_TRY_CUDA(cudaMemcpyAsync(d_in.as<void>(), spins, (size_t)R * N, cudaMemcpyHostToDevice, st));
         src = d_in.as<int8_t>();
     }
-    SG_RET(d_packed.alloc((size_t)Rp * N, st));
+    SG_RET(d_packed.alloc((size_t)Wn * 4 * N, st));
     SG_RET(d_E64.alloc(sizeof(unsigned long long) * Rp, st));
     SG_RET(d_j6.alloc(sizeof(uint2*), st));
     SG_RET(d_bad.alloc(sizeof(int), st));

@@ -3,8 +3,8 @@
 //
 // Annealing chains are independent: replicas never interact.  A batch is cut into
 // "planes", one per (instance, group of WG consecutive replica words); a plane holds
-// its chain's spins for every site, [N][WG] words in storage order, so the threads of
-// a block read consecutive 4*WG-byte records.  One persistent kernel runs every plane
+// its chain's spins for every site, [N][WG] words (32 replicas a word) in storage order,
+// so the threads of a block read consecutive 4*WG-byte records.  One persistent kernel runs every plane
 // from the first sweep to the last: each block takes the next plane from an atomic
 // counter (planes are ordered by decreasing work, largest first), sweeps it colour
 // by colour with only block barriers in between -- no other block touches its
@@ -36,25 +36,54 @@ namespace {
 
 __device__ __forceinline__ int div_magic(int v, uint32_t m) { return (int)__umulhi((uint32_t)v, m); }
 
+template <int WG>
+__device__ __forceinline__ void load_plane_words(const uint32_t* p, uint32_t (&w)[WG])
+{
+    if constexpr (WG == 4) {
+        const uint4 v = *reinterpret_cast<const uint4*>(p);
+        w[0] = v.x, w[1] = v.y, w[2] = v.z, w[3] = v.w;
+    } else if constexpr (WG == 2) {
+        const uint2 v = *reinterpret_cast<const uint2*>(p);
+        w[0] = v.x, w[1] = v.y;
+    } else {
+        w[0] = *p;
+    }
+}
+
+template <int WG>
+__device__ __forceinline__ void store_plane_words(uint32_t* p, const uint32_t (&w)[WG])
+{
+    if constexpr (WG == 4) *reinterpret_cast<uint4*>(p) = make_uint4(w[0], w[1], w[2], w[3]);
+    else if constexpr (WG == 2) *reinterpret_cast<uint2*>(p) = make_uint2(w[0], w[1]);
+    else *p = w[0];
+}
+
+// Replicas of word w (of the instance) that exist.
+__device__ __forceinline__ uint32_t plane_valid_bits(int R, int w)
+{
+    const int left = R - 32 * w;
+    return left >= 32 ? 0xFFFFFFFFu : left <= 0 ? 0u : (1u << left) - 1u;
+}
+
 // Persistent sweep kernel.  `order` lists plane indices by decreasing work.  SMEM: the
 // block copies its plane into shared memory (dynamic, [N][WG] words), runs all of the
 // plane's sweeps there, and writes it back -- no global traffic and no launches between
-// sweeps, for planes that fit.
+// sweeps, for planes that fit.  Every word update is the bit-sliced one of metropolis.cuh.
 template <int WG, bool UNITJ, bool SMEM = false>
 __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict__ planes,
                                                         const int* __restrict__ order, int n_planes,
                                                         unsigned* __restrict__ next)
 {
     constexpr int U = 4 / WG;
-    constexpr int kTieCap = 32;  // queued tied draws per warp
+    constexpr int kTieCap = 16;  // queued tie entries per warp
     extern __shared__ __align__(16) uint32_t s_plane[];
     __shared__ int s_item;
     __shared__ uint32_t s_thr[kThrRow];
-    __shared__ uint4 s_ties[8 * kTieCap];
+    __shared__ uint4 s_ties[8 * kTieCap * 2];  // per warp: {site, storage, word, tie}, {c0, c1, -, -}
     __shared__ int s_tie_n[8];
     const int tid = threadIdx.x, nthreads = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const mp::TieList ties{s_ties + warp * kTieCap, &s_tie_n[warp], kTieCap};
+    uint4* ties = s_ties + warp * kTieCap * 2;
     if (tid < 8) s_tie_n[tid] = 0;
     for (;;) {
         if (tid == 0) s_item = (int)atomicAdd(next, 1u);
@@ -65,22 +94,15 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
         const int L = p.L, H = L >> 1, LL = L * L, N = LL * L;
         const int half = LL * H;  // sites of one colour
         const RunKeys key{p.k0, p.k1};
-        uint32_t vmask[WG], acc[WG];
+        uint32_t vmask[WG];
 #pragma unroll
-        for (int wi = 0; wi < WG; ++wi) {
-            uint32_t m = 0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if (4 * (p.w0 + wi) + b < p.R) m |= 0x80u << (8 * b);
-            vmask[wi] = m;
-            acc[wi] = 0;
-        }
+        for (int wi = 0; wi < WG; ++wi) vmask[wi] = plane_valid_bits(p.R, p.w0 + wi);
         uint32_t* __restrict__ sp = p.spins;
         if constexpr (SMEM) {
             for (int q = tid; q < N; q += nthreads) {
                 uint32_t w[WG];
-                mp::load_words<WG>(p.spins + (size_t)q * WG, w);
-                mp::store_words<WG>(s_plane + (size_t)q * WG, w);
+                load_plane_words<WG>(p.spins + (size_t)q * WG, w);
+                store_plane_words<WG>(s_plane + (size_t)q * WG, w);
             }
             __syncthreads();
             sp = s_plane;
@@ -88,22 +110,24 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
         for (int sw = p.s_begin; sw < p.s_end; ++sw) {
             if (tid < kThrRow) s_thr[tid] = p.thr[(size_t)sw * kThrRow + tid];
             __syncthreads();
-            const uint4 lead = UNITJ ? mp::lead_record(s_thr, s_thr, s_thr, s_thr) : make_uint4(0, 0, 0, 0);
+            uint32_t tp[24];  // threshold planes of the sweep (the same for every replica)
+            if (UNITJ) {
+#pragma unroll
+                for (int m = 0; m < 24; ++m) tp[m] = mp::threshold_plane_bit(s_thr[2 + 2 * (m / 8)], m % 8) ? ~0u : 0u;
+            }
             // Deferred ties of this warp, decided by all its lanes together (every lane
             // runs the same iterations of the site loop below).
             auto resolve_list = [&]() {
                 __syncwarp();
-                const int n = min(*ties.count, kTieCap);
+                const int n = min(s_tie_n[warp], kTieCap);
                 for (int e = lane; e < n; e += 32) {
-                    const uint4 t = ties.entries[e];
-                    const uint32_t w = t.z & 0xFFFFu, nib = t.z >> 16;
-                    const uint32_t tie =
-                        ((nib & 1u) << 7) | ((nib & 2u) << 14) | ((nib & 4u) << 21) | ((nib & 8u) << 28);
-                    const uint32_t acc_t = mp::resolve_ties(tie, t.w, s_thr, 0, t.x, (uint32_t)sw, w, key.k0, key.k1);
-                    if (acc_t) sp[(size_t)t.y * WG + (w - (uint32_t)p.w0)] ^= mp::prmt(acc_t, 0u, 0xBA98u) & 0xFEFEFEFEu;
+                    const uint4 t = ties[2 * e], u = ties[2 * e + 1];
+                    const uint32_t acc =
+                        mp::resolve_tie_bits(t.w, u.x, u.y, s_thr, 0, t.x, (uint32_t)sw, t.z, key.k0, key.k1);
+                    if (acc) sp[(size_t)t.y * WG + (t.z - (uint32_t)p.w0)] ^= acc;
                 }
                 __syncwarp();
-                if (lane == 0) *ties.count = 0;
+                if (lane == 0) s_tie_n[warp] = 0;
                 __syncwarp();
             };
             for (int colour = 0; colour < 2; ++colour) {
@@ -115,8 +139,9 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
                     const int q0 = qb + lane;
                     int is_[U], i_[U];
                     bool live[U];
-                    mp::Couplings cp[U];
-                    uint32_t self[U][WG], P[U][WG];
+                    uint32_t S[U][6];
+                    int J[U][6];
+                    uint32_t self[U][WG], n[U][6][WG];
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
                         live[u] = q0 + u * nthreads < half;
@@ -134,30 +159,56 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
                         const int dyp = (y + 1 == L ? 1 - L : 1) * L, dym = (y == 0 ? L - 1 : -1) * L;
                         const int dzp = (z + 1 == L ? 1 - L : 1) * LL, dzm = (z == 0 ? L - 1 : -1) * LL;
                         const int nb[6] = {ho + jp, ho + jm, is_[u] + dyp, is_[u] + dym, is_[u] + dzp, is_[u] + dzm};
-                        cp[u] = UNITJ ? mp::decode_unit(p.j1[i_[u]]) : mp::decode_general(p.j6[i_[u]]);
-                        mp::load_words<WG>(sp + (size_t)is_[u] * WG, self[u]);
+                        if (UNITJ) {
+                            mp::unit_signs(p.j1[i_[u]], S[u]);
+                        } else {
+                            const uint2 r = p.j6[i_[u]];
 #pragma unroll
-                        for (int wi = 0; wi < WG; ++wi) P[u][wi] = 0;
-#pragma unroll
-                        for (int qq = 0; qq < 6; ++qq) {
-                            uint32_t n[WG];
-                            mp::load_words<WG>(sp + (size_t)nb[qq] * WG, n);
-#pragma unroll
-                            for (int wi = 0; wi < WG; ++wi) P[u][wi] += mp::bond_term(n[wi], cp[u], qq);
+                            for (int qq = 0; qq < 6; ++qq)
+                                J[u][qq] = (int)(int8_t)(((qq < 4 ? r.x : r.y) >> (8 * (qq & 3))) & 0xFFu);
                         }
+                        load_plane_words<WG>(sp + (size_t)is_[u] * WG, self[u]);
+#pragma unroll
+                        for (int qq = 0; qq < 6; ++qq) load_plane_words<WG>(sp + (size_t)nb[qq] * WG, n[u][qq]);
                     }
 #pragma unroll
                     for (int u = 0; u < U; ++u) {
-                        uint32_t vm[WG];  // an idle slot has no replicas: no flips, no ties
+                        uint32_t out[WG];
+                        bool any = false;
 #pragma unroll
-                        for (int wi = 0; wi < WG; ++wi) vm[wi] = live[u] ? vmask[wi] : 0u;
-                        const bool flip = mp::update_words<false, UNITJ, WG, 0, true>(
-                            self[u], P[u], vm, cp[u].msum, (uint32_t)i_[u], (uint32_t)sw, (uint32_t)p.w0, key,
-                            s_thr, &lead, acc, &ties, (uint32_t)is_[u]);
-                        if (live[u] && flip) mp::store_words<WG>(sp + (size_t)is_[u] * WG, self[u]);
+                        for (int wi = 0; wi < WG; ++wi) {
+                            const uint32_t w = (uint32_t)(p.w0 + wi);
+                            const uint32_t valid = live[u] ? vmask[wi] : 0u;  // an idle slot flips nothing
+                            uint32_t nw[6];
+#pragma unroll
+                            for (int qq = 0; qq < 6; ++qq) nw[qq] = n[u][qq][wi];
+                            uint32_t A[8];
+                            mp::lead_planes((uint32_t)i_[u], (uint32_t)sw, w, key, A);
+                            uint32_t flip;
+                            if (UNITJ) {
+                                uint32_t tie, c0, c1, c2;
+                                mp::update_word_unit(self[u][wi], nw, S[u], valid, tp, A, &flip, &tie, &c0, &c1, &c2);
+                                if (tie) {
+                                    const int pos = atomicAdd(&s_tie_n[warp], 1);
+                                    if (pos < kTieCap) {
+                                        ties[2 * pos] = make_uint4((uint32_t)i_[u], (uint32_t)is_[u], w, tie);
+                                        ties[2 * pos + 1] = make_uint4(c0, c1, 0u, 0u);
+                                    } else {  // list full: decide here
+                                        flip |= mp::resolve_tie_bits(tie, c0, c1, s_thr, 0, (uint32_t)i_[u],
+                                                                     (uint32_t)sw, w, key.k0, key.k1);
+                                    }
+                                }
+                            } else {
+                                flip = mp::update_word_general(self[u][wi], nw, J[u], valid, s_thr, 0, A,
+                                                               (uint32_t)i_[u], (uint32_t)sw, w, key);
+                            }
+                            out[wi] = self[u][wi] ^ flip;
+                            any |= flip != 0u;
+                        }
+                        if (any) store_plane_words<WG>(sp + (size_t)is_[u] * WG, out);
                     }
                     __syncwarp();
-                    if (*ties.count >= kTieCap / 2) resolve_list();
+                    if (s_tie_n[warp] >= kTieCap / 2) resolve_list();
                 }
                 resolve_list();  // the next colour reads these sites
                 __syncthreads();
@@ -167,14 +218,15 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
             __syncthreads();
             for (int q = tid; q < N; q += nthreads) {
                 uint32_t w[WG];
-                mp::load_words<WG>(s_plane + (size_t)q * WG, w);
-                mp::store_words<WG>(p.spins + (size_t)q * WG, w);
+                load_plane_words<WG>(s_plane + (size_t)q * WG, w);
+                store_plane_words<WG>(p.spins + (size_t)q * WG, w);
             }
         }
     }
 }
 
-// Initial spins of every plane (grid.y = plane).
+// Initial spins of every plane (grid.y = plane): replica r of site i starts at -1 when
+// bit 31 of word r % 4 of Philox(i, kSweepInit, r / 4, 0) is set.
 template <int WG>
 __global__ void planes_init_kernel(const Plane* __restrict__ planes)
 {
@@ -185,59 +237,52 @@ __global__ void planes_init_kernel(const Plane* __restrict__ planes)
         uint32_t words[WG];
 #pragma unroll
         for (int wi = 0; wi < WG; ++wi) {
-            const Philox4 r = philox4x32_10(i, kSweepInit, (uint32_t)(p.w0 + wi), kDomainMetropolis, p.k0, p.k1);
+            const int w = p.w0 + wi;
             uint32_t word = 0;
+            for (int q = 0; q < 8; ++q) {
+                if (32 * w + 4 * q >= p.R) break;
+                const Philox4 r = philox4x32_10(i, kSweepInit, (uint32_t)(8 * w + q), kDomainMetropolis, p.k0, p.k1);
 #pragma unroll
-            for (int b = 0; b < 4; ++b) {
-                const bool down = (4 * (p.w0 + wi) + b < p.R) && (r.v[b] >> 31);
-                word |= (down ? 0xFFu : 0x01u) << (8 * b);
+                for (int m = 0; m < 4; ++m)
+                    if (32 * w + 4 * q + m < p.R && (r.v[m] >> 31)) word |= 1u << (4 * q + m);
             }
             words[wi] = word;
         }
-        mp::store_words<WG>(p.spins + (size_t)is * WG, words);
+        store_plane_words<WG>(p.spins + (size_t)is * WG, words);
     }
 }
 
-// Energies (Eq. 1) of every replica of every plane: E_out[plane][4*WG] (grid.y = plane).
+// Energies (Eq. 1) of every replica of every plane: E_out[plane][32*WG] (grid.y = plane).
+// One warp per (row, word) item; lane b sums replica bit b along the row (forward bonds).
 template <int WG>
 __global__ void planes_energy_kernel(const Plane* __restrict__ planes, unsigned long long* __restrict__ E_out)
 {
-    __shared__ long long s_E[4 * WG];
     const Plane p = planes[blockIdx.y];
-    const int L = p.L, N = L * L * L;
-    if (threadIdx.x < 4 * WG) s_E[threadIdx.x] = 0;
-    __syncthreads();
-    long long acc[4 * WG];
+    const int L = p.L, LL = L * L, H = L >> 1;
+    const int lane = threadIdx.x & 31, warps = blockDim.x >> 5;
+    for (int t = blockIdx.x * warps + (threadIdx.x >> 5); t < LL * WG; t += gridDim.x * warps) {
+        const int r = t / WG, wi = t % WG;
+        const int z = r / L, y = r - z * L;
+        const int ryp = z * L + (y + 1 == L ? 0 : y + 1);
+        const int rzp = (z + 1 == L ? 0 : z + 1) * L + y;
+        const uint32_t* __restrict__ row = p.spins + (size_t)r * L * WG + wi;
+        const uint32_t* __restrict__ rowy = p.spins + (size_t)ryp * L * WG + wi;
+        const uint32_t* __restrict__ rowz = p.spins + (size_t)rzp * L * WG + wi;
+        long long e = 0;
+        for (int x = 0; x < L; ++x) {
+            const int pos = (x & 1) * H + (x >> 1);
+            const int xp = x + 1 == L ? 0 : x + 1;
+            const int posx = (xp & 1) * H + (xp >> 1);
+            const uint2 rec = p.j6[r * L + x];
+            const int J[3] = {(int)(int8_t)(rec.x & 0xFFu), (int)(int8_t)((rec.x >> 16) & 0xFFu),
+                              (int)(int8_t)(rec.y & 0xFFu)};
+            const uint32_t me = row[pos * WG];
+            const uint32_t nb[3] = {row[posx * WG], rowy[pos * WG], rowz[pos * WG]};
 #pragma unroll
-    for (int q = 0; q < 4 * WG; ++q) acc[q] = 0;
-    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < N; i += gridDim.x * blockDim.x) {
-        const int x = i % L, y = (i / L) % L, z = i / (L * L);
-        const uint2 r = p.j6[i];
-        const int J[3] = {(int)(int8_t)(r.x & 0xFF), (int)(int8_t)((r.x >> 16) & 0xFF),
-                          (int)(int8_t)(r.y & 0xFF)};
-        const int64_t fwd[3] = {storage_of(L, (x + 1 == L ? 0 : x + 1) + L * (y + L * z)),
-                                storage_of(L, x + L * ((y + 1 == L ? 0 : y + 1) + L * z)),
-                                storage_of(L, x + L * (y + L * (z + 1 == L ? 0 : z + 1)))};
-        uint32_t me[WG];
-        mp::load_words<WG>(p.spins + (size_t)storage_of(L, i) * WG, me);
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-            uint32_t nb[WG];
-            mp::load_words<WG>(p.spins + (size_t)fwd[d] * WG, nb);
-#pragma unroll
-            for (int wi = 0; wi < WG; ++wi)
-#pragma unroll
-                for (int b = 0; b < 4; ++b)
-                    acc[4 * wi + b] += J[d] * (int)(int8_t)((me[wi] >> (8 * b)) & 0xFF) *
-                                       (int)(int8_t)((nb[wi] >> (8 * b)) & 0xFF);
+            for (int d = 0; d < 3; ++d) e += J[d] * (1 - 2 * (int)(((me ^ nb[d]) >> lane) & 1u));
         }
+        if (e) atomicAdd(&E_out[(size_t)blockIdx.y * 32 * WG + 32 * wi + lane], (unsigned long long)e);
     }
-#pragma unroll
-    for (int q = 0; q < 4 * WG; ++q)
-        if (acc[q]) atomicAdd((unsigned long long*)&s_E[q], (unsigned long long)acc[q]);
-    __syncthreads();
-    if (threadIdx.x < 4 * WG && s_E[threadIdx.x])
-        atomicAdd(&E_out[(size_t)blockIdx.y * 4 * WG + threadIdx.x], (unsigned long long)s_E[threadIdx.x]);
 }
 
 // Spins of one plane into the instance's [R][N] output (grid.y = plane).
@@ -249,13 +294,15 @@ __global__ void planes_unpack_kernel(const Plane* __restrict__ planes, int8_t* c
     if (!out) return;
     const int L = p.L;
     const int64_t N = (int64_t)L * L * L;
-    const int8_t* src = reinterpret_cast<const int8_t*>(p.spins);
-    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * 4 * WG;
+    for (int64_t q = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; q < N * 32 * WG;
          q += (int64_t)gridDim.x * blockDim.x) {
         const int rb = (int)(q / N);            // replica within the plane
         const int64_t i = q - (int64_t)rb * N;  // logical site
-        const int r = 4 * p.w0 + rb;
-        if (r < p.R) out[(int64_t)r * N + i] = src[storage_of(L, i) * 4 * WG + rb];
+        const int r = 32 * p.w0 + rb;
+        if (r < p.R) {
+            const uint32_t word = p.spins[storage_of(L, i) * WG + (rb >> 5)];
+            out[(int64_t)r * N + i] = ((word >> (rb & 31)) & 1u) ? (int8_t)-1 : (int8_t)1;
+        }
     }
 }
 
@@ -465,7 +512,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
     // words per plane: a common divisor of every instance's word count
     int wg_max = 4;
     for (int a = 0; a < I; ++a) {
-        const int Wn = (ps[members[a]].replicas + 3) / 4;
+        const int Wn = words_for(ps[members[a]].replicas);
         while (Wn % wg_max) wg_max >>= 1;
     }
 
@@ -508,7 +555,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
         for (int a = 0; a < I; ++a) {
             const sg_instance* in = insts[members[a]];
             const sg_sa_params& p = ps[members[a]];
-            const int Wn = (p.replicas + 3) / 4;
+            const int Wn = words_for(p.replicas);
             for (int w0 = 0; w0 < Wn; w0 += WG) {
                 Plane pl{};
                 pl.spins = spins_base ? spins_base + wo : nullptr;
@@ -528,7 +575,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
                 pl.Hmagic = magic(in->L / 2);
                 pl.out = a;
                 planes->push_back(pl);
-                work->push_back((double)in->N * 4 * WG * std::max(p.sweeps, 1));
+                work->push_back((double)in->N * 32 * WG * std::max(p.sweeps, 1));
                 wo += (size_t)in->N * WG;
             }
         }
@@ -558,7 +605,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
         cudaDeviceProp prop;
         cudaGetDeviceProperties(&prop, dev);
         std::ostringstream ks;
-        ks << prop.name << "/" << sms << "/" << (unit ? "u" : "g") << "/smem" << smem_for(1) / 1024 << "/t2";
+        ks << prop.name << "/" << sms << "/" << (unit ? "u" : "g") << "/smem" << smem_for(1) / 1024 << "/t3";
         for (auto& m : mix)
             ks << "/" << std::get<0>(m.first) << "x" << std::get<1>(m.first) << "x" << std::get<2>(m.first) << "x" << m.second;
         key = ks.str();
@@ -590,7 +637,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
                 double per_sweep = 0;
                 int s_min = 1 << 30;
                 for (auto& pl : planes) {
-                    per_sweep += (double)pl.L * pl.L * pl.L * 4 * wg;
+                    per_sweep += (double)pl.L * pl.L * pl.L * 32 * wg;
                     s_min = std::min(s_min, std::max(pl.S, 1));
                 }
                 const int trial_sweeps =
@@ -598,7 +645,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
                 double trial_work = 0;
                 for (auto& pl : planes) {
                     pl.s_end = std::min(pl.S, trial_sweeps);
-                    trial_work += (double)pl.L * pl.L * pl.L * 4 * wg * pl.s_end;
+                    trial_work += (double)pl.L * pl.L * pl.L * 32 * wg * pl.s_end;
                 }
                 const std::vector<int> order = lpt_order(work);
                 SG_B(d_pl.alloc(sizeof(Plane) * planes.size(), st));
@@ -650,7 +697,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
     SG_B(d_pl.alloc(sizeof(Plane) * n, st));
     SG_B(d_ord.alloc(sizeof(int) * n, st));
     SG_B(d_next.alloc(sizeof(unsigned), st));
-    SG_B(d_E.alloc(sizeof(unsigned long long) * (size_t)n * 4 * WG, st));
+    SG_B(d_E.alloc(sizeof(unsigned long long) * (size_t)n * 32 * WG, st));
     // spin outputs: device targets directly, host targets through one staging area
     std::vector<int8_t*> outp(I, nullptr);
     size_t stage_bytes = 0;
@@ -694,7 +741,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
     }
     auto device_work = [&](cudaStream_t s) -> int32_t {
         SG_TRY_CUDA(cudaMemsetAsync(d_next.p, 0, sizeof(unsigned), s));
-        SG_TRY_CUDA(cudaMemsetAsync(d_E.p, 0, sizeof(unsigned long long) * (size_t)n * 4 * WG, s));
+        SG_TRY_CUDA(cudaMemsetAsync(d_E.p, 0, sizeof(unsigned long long) * (size_t)n * 32 * WG, s));
         SG_B(launch_planes_init(WG, static_cast<Plane*>(d_pl.p), n, s));
         if (timed) SG_TRY_CUDA(cudaEventRecord(ev[0], s));
         SG_B(launch_sa_planes(WG, static_cast<Plane*>(d_pl.p), static_cast<int*>(d_ord.p), n,
@@ -732,7 +779,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
         SG_B(device_work(st));
     }
 
-    std::vector<unsigned long long> E((size_t)n * 4 * WG);
+    std::vector<unsigned long long> E((size_t)n * 32 * WG);
     SG_TRY_CUDA(cudaMemcpyAsync(E.data(), d_E.p, sizeof(unsigned long long) * E.size(), cudaMemcpyDeviceToHost, st));
     for (int a = 0; a < I; ++a) {
         const sg_sa_result& o = outs[members[a]];
@@ -761,10 +808,10 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
         const int a = pl.out;
         const sg_sa_result& o = outs[members[a]];
         const int64_t egs = insts[members[a]]->e_gs;
-        for (int rb = 0; rb < 4 * WG; ++rb) {
-            const int r = 4 * pl.w0 + rb;
+        for (int rb = 0; rb < 32 * WG; ++rb) {
+            const int r = 32 * pl.w0 + rb;
             if (r >= pl.R) continue;
-            o.E[r] = (int64_t)(long long)E[(size_t)q * 4 * WG + rb];
+            o.E[r] = (int64_t)(long long)E[(size_t)q * 32 * WG + rb];
             if (o.eps) o.eps[r] = (double)(o.E[r] - egs) / (double)(-egs);
         }
     }

@@ -64,16 +64,16 @@ extern "C" int32_t sg_energy_noalloc(int32_t L, const int8_t* J3_dev, const int8
     }
     cudaStream_t st = (cudaStream_t)stream;
     const size_t N = (size_t)L * L * L;
-    const int Wn = (n_configs + 3) / 4, Rp = 4 * Wn;
+    const int Wn = words_for(n_configs), Rp = 32 * Wn;
     // scratch layout: [E sums: 8 * Rp][status: 16][j6 pointer: 16][coupling records: 8 * N]
-    //                 [sign bytes: N][packed spins: N * Rp]
+    //                 [sign bytes: N][packed spins: N * Wn 32-bit words]
     const size_t off_E = 0;
     const size_t off_bad = round_up(off_E + 8 * (size_t)Rp, 256);
     const size_t off_ptr = off_bad + 16;
     const size_t off_j6 = round_up(off_ptr + 16, 256);
     const size_t off_j1 = round_up(off_j6 + 8 * N, 256);
     const size_t off_sp = round_up(off_j1 + N, 256);
-    const size_t need = off_sp + N * (size_t)Rp;
+    const size_t need = off_sp + N * (size_t)Wn * 4;
     if (need > (size_t)SG_NOALLOC_SCRATCH_BYTES) {
         set_error("sg_energy_noalloc: L=%d with %d configurations needs %zu bytes of scratch, "
                   "more than the fixed %u", L, n_configs, need, (unsigned)SG_NOALLOC_SCRATCH_BYTES);

@@ -137,7 +137,7 @@ Layout layout_of(const Request& q)
     y.j6 = take(8 * N);
     y.j1 = take(N);
     y.J3 = take(3 * N);
-    y.spins = take(N * Rp);
+    y.spins = take(N * (Rp / 32) * 4);  // bit-packed words
     if (q.mode == kPlanes) {
         y.thr = take(4 * q.thr->size());
     } else if (q.mode == kRowsSA) {
@@ -292,8 +292,8 @@ int32_t prepare_request(ScheduleCache& cache, Request* q)
     q->inst.reset(inst);
     q->L = inst->L;
     q->N = inst->N;
-    q->Wn = (r.width + 3) / 4;
-    q->Rp = 4 * q->Wn;
+    q->Wn = words_for(r.width);
+    q->Rp = 32 * q->Wn;
     q->WG = largest_wg(q->Wn);
     q->result.e_gs = inst->e_gs;
     const int64_t abs_gs = inst->e_gs < 0 ? -inst->e_gs : inst->e_gs;
@@ -561,9 +561,9 @@ bool grow_group(PlaneGroup& g, size_t np)
     if (g.hE) cudaFreeHost(g.hE), g.hE = nullptr;
     g.cap_planes = 0;
     if (cudaMalloc(&g.pl, sizeof(Plane) * cap) != cudaSuccess || cudaMalloc(&g.ord, sizeof(int) * cap) != cudaSuccess ||
-        cudaMalloc(&g.next, 16) != cudaSuccess || cudaMalloc(&g.E, 8 * 16 * cap) != cudaSuccess ||
+        cudaMalloc(&g.next, 16) != cudaSuccess || cudaMalloc(&g.E, 8 * 128 * cap) != cudaSuccess ||
         cudaMalloc(&g.init, sizeof(Plane) * cap) != cudaSuccess ||
-        cudaMallocHost(&g.hE, 8 * 16 * cap) != cudaSuccess) {
+        cudaMallocHost(&g.hE, 8 * 128 * cap) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
@@ -615,7 +615,7 @@ void launch_group(PlaneGroup& g, const std::vector<Request*>& act, int chunk)
         return (double)p.L * p.L * p.L * (p.s_end - p.s_begin);
     };
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return work(x) > work(y); });  // longest first
-    const size_t nE = (size_t)np * 4 * g.WG;
+    const size_t nE = (size_t)np * 32 * g.WG;
     cudaStream_t st = g.st;
     int32_t rc = grow_group(g, (size_t)np) ? SG_OK : SG_ENOMEM;
     // uploads of newly admitted requests ran on their own streams
@@ -670,9 +670,9 @@ bool poll_group(PlaneGroup& g)
         Request* q = g.reqs[a];
         int64_t m = INT64_MAX;
         for (int k = g.first[a]; k < g.first[a + 1]; ++k)
-            for (int rb = 0; rb < 4 * g.WG; ++rb)
-                if (4 * g.planes[k].w0 + rb < q->req.width)
-                    m = std::min<int64_t>(m, (int64_t)(long long)g.hE[(size_t)k * 4 * g.WG + rb]);
+            for (int rb = 0; rb < 32 * g.WG; ++rb)
+                if (32 * g.planes[k].w0 + rb < q->req.width)
+                    m = std::min<int64_t>(m, (int64_t)(long long)g.hE[(size_t)k * 32 * g.WG + rb]);
         finish_chunk(q, m);
     }
     return true;

@@ -81,6 +81,12 @@ int32_t build_exchange_tables(const std::vector<double>& ladder, int64_t dmax,
 int32_t instance_device_j6(sg_instance* inst, cudaStream_t stream, const uint2** j6,
                            const uint8_t** j1);
 
+// ---- spin words ----
+// Spins are bit-packed 32 replicas to a 32-bit word (bit b of word w is replica 32w + b,
+// set meaning -1); a run of R replicas keeps Wn = words_for(R) words per site and
+// Rp = 32 * Wn replica slots.
+inline int words_for(int replicas) { return (replicas + 31) / 32; }
+
 // ---- spin storage order ----
 // Within every row (y, z) of the lattice the L/2 sites with even x are stored first,
 // then the L/2 sites with odd x, so that the sites of one checkerboard colour in a row
@@ -149,7 +155,7 @@ int32_t launch_prepare_j6(const int8_t* J3_dev, uint2* j6_dev, uint8_t* j1_dev, 
 int32_t launch_init_spins(int8_t* spins, const RunKeys* keys_dev, int I, int L, int Wn, int R,
                           cudaStream_t st);
 int32_t launch_energy(const int8_t* spins, const uint2* const* j6_ptrs, int I, int L, int Wn,
-                      unsigned long long* E_out /* [I][Wn*4] */, cudaStream_t st);
+                      unsigned long long* E_out /* [I][32*Wn], added to */, cudaStream_t st);
 int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_row /* kThrRow */, int32_t* E, int* status,
@@ -158,13 +164,13 @@ int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs,
 int32_t launch_half_sweep_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs /* [K][kThrRow] */,
-                             const uint8_t* rung_of_slot /* [I][Wn*4] */, int32_t* E, int* status,
+                             const uint8_t* rung_of_slot /* [I][32*Wn] */, int32_t* E, int* status,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
                              const ExchangeArgs* xch, unsigned* done, bool* fused,
                              cudaStream_t st);
-// sweep.cu: row-mapped sweep kernel (used whenever it supports the word count)
+// sweep.cu: the bit-sliced sweep kernel, one launch per colour
 bool rows_kernel_supports(int Wn);
-// SA variant keeps no incremental energies (the run recomputes them at the end);
+// SA variant keeps no energies (the run recomputes them at the end);
 // unit_j: every coupling of the group has |J| = 1.  With sweep_base the sweep index is
 // *sweep_base + sweep, read on the device, and thr_row is the whole [S][kThrRow] table.
 int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
@@ -172,21 +178,16 @@ int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint32_t* thr_row, bool unit_j, int I, int L, int Wn, int R,
                              uint32_t sweep, int colour, cudaStream_t st,
                              const uint32_t* sweep_base = nullptr, int* status = nullptr);
-// xch != nullptr: the launch may also perform the PT exchange (last block per instance);
-// *fused reports whether it did.  done: [I] zeroed counters.  status (optional): set to
-// SG_ETIMEOUT when a bounded wait of the staged variant gives up.
+// PT: the colour-0 launch clears E [I][32*Wn] and the colour-1 launch sums every slot's
+// energy afresh.  xch != nullptr: the colour-1 launch also performs the exchange (last
+// block per instance); *fused reports whether it did.  done: [I] zeroed counters.
+// status: unused (no launch of this kernel waits).
 int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
                              const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st,
                              const uint32_t* sweep_base = nullptr, int* status = nullptr);
-// tile.cu: shared-memory streaming sweep (used when it supports the shape)
-bool tile_kernel_supports(int I, int L, int Wn);
-int32_t launch_sweep_tile(int8_t* spins, const uint2* const* j6_ptrs, const uint8_t* const* j1_ptrs,
-                          const RunKeys* keys, const uint32_t* thr, const uint8_t* rung_of_slot,
-                          int32_t* E, int* status, bool pt, bool unit_j, int I, int L, int Wn,
-                          int Rvalid, uint32_t sweep, int colour, cudaStream_t st);
 int32_t launch_pt_exchange(const ExchangeArgs& x, int I, uint32_t sweep, cudaStream_t st);
 int32_t launch_pt_setup(const unsigned long long* E64, int32_t* E, uint8_t* rung_of_slot,
                         uint8_t* slot_of_rung, unsigned long long* accepts, int32_t* minE,
@@ -195,6 +196,7 @@ int32_t launch_check_energy(const unsigned long long* E64, const int32_t* E, int
                             int R, int* mismatch, cudaStream_t st);
 int32_t launch_copy_energies(const unsigned long long* E64, int64_t* E, int n, cudaStream_t st);
 int32_t launch_narrow_energy(const unsigned long long* E64, int32_t* E, int64_t n, cudaStream_t st);
+// Rp = 32 * Wn; the int8 side is [R][N] in logical site order
 int32_t launch_unpack_spins(const int8_t* spins, int8_t* out, int L, int Rp, int R,
                             int I_index, cudaStream_t st);
 int32_t launch_pack_spins(const int8_t* in, int8_t* spins, int L, int Rp, int R, int* bad,

@@ -1,31 +1,31 @@
-// sweep.cu -- the Metropolis half-sweep kernel: the hot path (App. D.1, App. D.2).
+// sweep.cu -- one Metropolis half sweep (one checkerboard colour) of every replica of a
+// group of instances, spins bit-packed 32 replicas to a word (App. D.1 / D.2).
 //
-// One launch updates every site of one checkerboard colour, for every replica of a
-// group of instances.  Thread mapping (no division except one multiply-high per row):
-//   blockIdx.y        instance
-//   blockIdx.x, ty    rows (y, z) of the lattice, dealt out grid-stride: thread (bx, ty)
-//                     takes rows (c * gridDim.x + bx) * blockDim.y + ty, c < rows_per_thread
-//   tx = j * G + g    site j of the colour inside the row, word group g
-// A word holds four replicas (one byte each).  Thread g of a site owns CH chunks of
-// WG consecutive words, so it updates 4*WG*CH replicas with one decode of the site's
-// couplings, and one Philox4x32-10 call per word (the counter (site, sweep, word, 0)
-// names exactly that word's four replicas).
+// Work layout:
+//   blockIdx.y         instance
+//   blockIdx.x, ty     lattice rows (y, z), dealt out grid-stride: thread (bx, ty) takes
+//                      rows (c * gridDim.x + bx) * blockDim.y + ty, c < rows_per_thread, so
+//                      the blocks of an instance move through the lattice together and the
+//                      +-z neighbour rows they read are still in L2
+//   tx = j * G + g     site j of the row's colour (colour-split storage: the sites of one
+//                      colour in a row are contiguous) and its words g, g + G, ...
+// Each (site, word) item loads its own word and the six neighbour words, counts the
+// satisfied bonds of all 32 replicas with a bit-sliced adder, compares the leading draw
+// bytes with the threshold bytes plane by plane (metropolis.cuh), and stores the word
+// back when a replica flipped.  Draws whose leading byte ties with the threshold's are
+// queued per warp and decided later, together: sites of one colour never read one
+// another within a half sweep, so a late flip changes nothing else.
 //
-// Per word (bit layout in kernels.cu):
-//   P  = sum_q ((n_q ^ S_q) & M_q)                 2|J| for each negative bond term
-//   W  = s_i == +1 ? P : 2*sum|J| - P                2 * (weight of unsatisfied bonds)
-//   k  = W - sum|J|  (= -x; flipping raises E by 2k)
-// Bytes with k <= 0 flip unconditionally; the others flip when their Philox word is
-// below thr[k].  "k > 0" is found for four bytes by one borrow-free subtraction; the
-// draws are taken only when some lane of the warp needs one (a warp-uniform branch,
-// so the WG Philox chains of a chunk interleave), and the byte decisions are
-// branch-free.  For parallel tempering the energy change of every slot is summed in
-// 8-bit lanes (at most 10 updates per thread, each adding <= 24) and reduced once per
-// thread with warp reductions.
+// Parallel tempering: the colour-1 launch also sums every slot's energy afresh: each bond
+// joins a colour-0 and a colour-1 site, so E = sum over colour-1 sites of
+// s_i sum_q J_q s_q, which for |J| = 1 is 6 - 2c with c the satisfied count after the
+// update (kept in bit-sliced vertical counters, reduced through a warp bit transpose).
+// The colour-0 launch clears E; the block that finishes the colour-1 launch last for an
+// instance performs that instance's replica exchange (exchange.cuh).
+#include <stdint.h>
 #include <stdlib.h>
 
 #include "exchange.cuh"
-#include "async_copy.cuh"
 #include "metropolis.cuh"
 #include "philox.cuh"
 #include "sg_internal.h"
@@ -33,21 +33,19 @@
 namespace sg {
 namespace {
 
-constexpr int kThrStride = 17;   // per-slot threshold row stride in shared memory (bank spread)
-constexpr int kTieCap = 32;      // queued tied draws per warp
-
-// Words of the staged PT variant's threshold table in dynamic shared memory (Rp slots),
-// rounded so that the row buffers after it stay 128-byte aligned.
-__host__ __device__ constexpr int staged_thr_words(int Rp) { return (Rp * kThrStride + 31) & ~31; }
+constexpr int kThrStride = 17;  // per-slot threshold row stride in shared memory (bank spread)
+constexpr int kTieCap = 16;     // queued tie entries per warp
+constexpr int kVBits = 10;      // planes of the per-thread energy counters
+constexpr int kVItems = ((1 << kVBits) - 1) / 6;  // items a counter holds before a fold
 
 struct SweepArgs {
-    uint32_t* spins;
+    uint32_t* spins;                 // [I][N][Wn] words, storage order
     const uint2* const* j6_ptrs;     // per instance: [N] records of the six int8 couplings
     const uint8_t* const* j1_ptrs;   // per instance: [N] sign bits (used when all |J| = 1)
     const RunKeys* keys;
     const uint32_t* thr;          // SA: one row of kThrRow ([S][kThrRow] with sweep_base); PT: [K][kThrRow]
     const uint8_t* rung_of_slot;  // PT: [I][Rp]
-    int32_t* E;                   // PT: [I][Rp] energies, updated
+    int32_t* E;                   // PT: [I][Rp] energies, recomputed by colour 1
     int L, Wn, Rvalid, G, rows_per_thread;
     uint32_t Lmagic;              // ceil(2^32 / L): row / L by multiply-high
     uint32_t sweep;
@@ -55,32 +53,26 @@ struct SweepArgs {
     ExchangeArgs x;               // PT exchange performed by the last block of each instance
     unsigned* done;               // [I] blocks finished in this launch (reset by the last one)
     const uint32_t* sweep_base;   // if set, the sweep index is *sweep_base + sweep
-    int* status;                  // staged variant: set to SG_ETIMEOUT when a copy wait gives up
-    int segw;                     // staged variant: words of one half row, (L/2) * Wn
 };
 
-// NST > 0: the staged variant.  Each warp owns one row at a time (blockDim.x == 32, one
-// site per thread) and keeps NST rows in flight: for row (y, z) the six half rows it
-// reads -- its own sites, their x neighbours, and the matching halves of rows y+-1 and
-// z+-1 -- arrive in shared memory by bulk asynchronous copies that complete on the
-// warp's mbarrier for that ring slot, issued NST rows ahead of use.  The updated spins
-// go straight back to global memory; a half sweep never reads what it writes.
-template <bool PT, bool UNITJ, int WG, int CH, bool PAD, int MINB = 2, bool DRAW = false,
-          bool XCH = false, int NST = 0>
-__global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a)
+__device__ __forceinline__ uint32_t valid_bits(int Rvalid, int w)
 {
-    // staged PT: the slot thresholds live at the start of the dynamic array, sized to Rp
-    __shared__ uint32_t s_thr_fixed[PT ? (NST > 0 ? 1 : 256 * kThrStride) : kThrRow];
-    __shared__ int s_dE[PT ? 256 : 1];
-    extern __shared__ __align__(128) uint32_t s_stage[];  // NST > 0: [thr][TY][NST][6][segw]
-    __shared__ uint64_t s_bar[NST > 0 ? 8 * NST : 1];
-    __shared__ uint4 s_lead[PT ? 64 : 1];  // PT: leading threshold bytes per word (unit couplings)
-    __shared__ uint4 s_ties[8 * kTieCap];  // per warp: draws whose leading byte tied
+    const int left = Rvalid - 32 * w;
+    return left >= 32 ? 0xFFFFFFFFu : left <= 0 ? 0u : (1u << left) - 1u;
+}
+
+template <bool PT, bool UNITJ, bool XCH>
+__global__ void __launch_bounds__(256, 2) sweep_bits_kernel(const SweepArgs a)
+{
+    __shared__ uint32_t s_thr[PT ? 256 * kThrStride : kThrRow];
+    __shared__ uint32_t s_tp[(PT ? 8 : 1) * 24];  // threshold planes per word (unit couplings)
+    __shared__ int s_E[PT ? 256 : 1];
+    __shared__ uint4 s_ties[8 * kTieCap * 2];      // per warp: {site, storage, word, tie}, {c0, c1, -, -}
     __shared__ int s_tie_n[8];
 
     const int inst = blockIdx.y;
     const int L = a.L, Wn = a.Wn, G = a.G;
-    const int Rp = 4 * Wn;
+    const int Rp = 32 * Wn;
     const int H = L >> 1;
     const int LL = L * L;
     const RunKeys key = a.keys[inst];
@@ -88,271 +80,201 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
     uint32_t* __restrict__ s = a.spins + (size_t)inst * (size_t)LL * L * Wn;
     const int nthreads = blockDim.x * blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    uint32_t* s_thr = (PT && NST > 0) ? s_stage : s_thr_fixed;
-    const int thr_words = (PT && NST > 0) ? staged_thr_words(Rp) : 0;
+    const bool energy = PT && a.colour == 1;
 
     if (PT) {
         for (int q = tid; q < Rp * kThrRow; q += nthreads) {
             const int slot = q / kThrRow, k = q % kThrRow;
             s_thr[slot * kThrStride + k] = a.thr[a.rung_of_slot[(size_t)inst * Rp + slot] * kThrRow + k];
         }
-        for (int q = tid; q < Rp; q += nthreads) s_dE[q] = 0;
+        for (int q = tid; q < Rp; q += nthreads) s_E[q] = 0;
+        // colour 1 of this sweep sums the energies afresh
+        if (a.colour == 0 && blockIdx.x == 0)
+            for (int q = tid; q < Rp; q += nthreads) a.E[(size_t)inst * Rp + q] = 0;
     } else {
         // with a device sweep index, thr is the run's [S][kThrRow] schedule table
         const uint32_t* row = a.sweep_base ? a.thr + (size_t)sweep * kThrRow : a.thr;
         for (int q = tid; q < kThrRow; q += nthreads) s_thr[q] = row[q];
     }
-    if constexpr (NST > 0) {
-        if (threadIdx.x == 0) {
-            for (int k = 0; k < NST; ++k) ac::mbar_init(&s_bar[threadIdx.y * NST + k], 1);
-            ac::mbar_fence_init();
-        }
-    }
     if (tid < 8) s_tie_n[tid] = 0;
     __syncthreads();
-    uint4 lead_sa = make_uint4(0, 0, 0, 0);  // SA: one record for every word
     if (UNITJ) {
-        if (PT) {
-            for (int q = tid; q < Wn; q += nthreads) {
-                const uint32_t* t0 = s_thr + 4 * q * kThrStride;
-                s_lead[q] = mp::lead_record(t0, t0 + kThrStride, t0 + 2 * kThrStride, t0 + 3 * kThrStride);
+        const int nw = PT ? Wn : 1;
+        for (int q = tid; q < nw * 24; q += nthreads) {
+            const int w = q / 24, m = (q % 24) / 8, j = q % 8, k = 2 + 2 * m;
+            uint32_t plane = 0;
+            for (int b = 0; b < 32; ++b) {
+                const uint32_t th = PT ? s_thr[(32 * w + b) * kThrStride + k] : s_thr[k];
+                plane |= mp::threshold_plane_bit(th, j) << b;
             }
-            __syncthreads();
-        } else {
-            lead_sa = mp::lead_record(s_thr, s_thr, s_thr, s_thr);
+            s_tp[q] = plane;
         }
+        __syncthreads();
     }
 
     const int g = threadIdx.x % G;
     const int j0 = threadIdx.x / G;
     const int JX = blockDim.x / G;
-    const int wbase = g * CH * WG;  // first word owned by this thread
-
-    uint32_t vmask[CH][WG];  // bit 7 of each byte that is a real replica (not padding)
-    uint32_t acc[CH][WG];
+    uint32_t tp[24];
+    if (UNITJ) {
 #pragma unroll
-    for (int ch = 0; ch < CH; ++ch)
-#pragma unroll
-        for (int wi = 0; wi < WG; ++wi) {
-            uint32_t m = 0;
-#pragma unroll
-            for (int b = 0; b < 4; ++b)
-                if (4 * (wbase + ch * WG + wi) + b < a.Rvalid) m |= 0x80u << (8 * b);
-            vmask[ch][wi] = PAD ? m : 0x80808080u;
-            acc[ch][wi] = 0;
-        }
-
-    constexpr int KMAX = UNITJ ? 6 : 12;  // largest |k| of one flip
-    // Folds the 8-bit energy lanes into the block's per-slot sums.  Called by whole
-    // warps at the same point of the row loop.
-    auto flush = [&]() {
-        const int lane = tid & 31;
-        const bool full = __activemask() == 0xFFFFFFFFu;
-        const bool full_warp_same = full && (G == 1);
-        const bool shuffle_same = full && G < 32 && (32 % G) == 0;
-#pragma unroll
-        for (int ch = 0; ch < CH; ++ch)
-#pragma unroll
-            for (int wi = 0; wi < WG; ++wi) {
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int slot = 4 * (wbase + ch * WG + wi) + b;
-                    int d = 2 * mp::lane_sum(acc[ch][wi], b);
-                    if (full_warp_same) {
-                        d = __reduce_add_sync(0xFFFFFFFFu, d);
-                        if (lane == 0 && d) atomicAdd(&s_dE[slot], d);
-                    } else if (shuffle_same) {
-                        for (int off = G; off < 32; off <<= 1) d += __shfl_xor_sync(0xFFFFFFFFu, d, off);
-                        if (lane < G && d) atomicAdd(&s_dE[slot], d);
-                    } else if (d) {
-                        atomicAdd(&s_dE[slot], d);
-                    }
-                }
-                acc[ch][wi] = 0;
-            }
-    };
-    int items = 0;  // site updates folded into the 8-bit lanes since the last flush
-
-    // Deferred ties of this thread's warp.  resolve_list() is called by every live lane of
-    // the warp at a convergent point: the lanes share the queued entries, decide each from
-    // the low 24 bits of its draws, and flip the accepted bytes in global memory (the
-    // warp's own earlier stores to those words are ordered before by __syncwarp).
-    const int warp = tid >> 5, lane32 = tid & 31;
-    const mp::TieList ties{s_ties + warp * kTieCap, &s_tie_n[warp], kTieCap};
-    const int warp_lanes = min(32, nthreads - 32 * warp);  // the block's last warp may be partial
-    const unsigned wm = warp_lanes == 32 ? 0xFFFFFFFFu : (1u << warp_lanes) - 1u;
-    auto resolve_list = [&]() {
-        __syncwarp(wm);
-        const int n = min(*ties.count, kTieCap);
-        const int lanes = __popc(wm), rank = __popc(wm & ((1u << lane32) - 1u));
-        for (int e = rank; e < n; e += lanes) {
-            const uint4 t = ties.entries[e];
-            const uint32_t w = t.z & 0xFFFFu, nib = t.z >> 16;
-            const uint32_t tie = ((nib & 1u) << 7) | ((nib & 2u) << 14) | ((nib & 4u) << 21) | ((nib & 8u) << 28);
-            const uint32_t* row = PT ? s_thr + 4 * w * kThrStride : s_thr;
-            const uint32_t acc_t = mp::resolve_ties(tie, t.w, row, PT ? kThrStride : 0, t.x, sweep, w, key.k0, key.k1);
-            if (acc_t) {
-                const uint32_t ff = mp::prmt(acc_t, 0u, 0xBA98u);
-                s[(size_t)t.y * Wn + w] ^= ff & 0xFEFEFEFEu;
-                if (PT)
-                    for (int b = 0; b < 4; ++b)
-                        if ((acc_t >> (8 * b + 7)) & 1u) atomicAdd(&s_dE[4 * w + b], 2 * (int)((t.w >> (8 * b)) & 0xFFu));
-            }
-        }
-        __syncwarp(wm);
-        if (rank == 0) *ties.count = 0;
-        __syncwarp(wm);
-    };
-
-    if constexpr (NST > 0) {
-        // rows c = 0, 1, ... of this warp: (c * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y
-        const int segw = a.segw;
-        const uint32_t seg_bytes = (uint32_t)segw * 4u;
-        uint32_t* ring = s_stage + thr_words + (size_t)threadIdx.y * NST * 6 * segw;
-        uint64_t* bars = s_bar + threadIdx.y * NST;
-        const int lane = threadIdx.x;
-        auto row_of = [&](int c) { return (c * (int)gridDim.x + (int)blockIdx.x) * (int)blockDim.y + (int)threadIdx.y; };
-        // lane 0: the six half rows of row c into ring slot c % NST
-        // the whole warp: the six half rows of row c into ring slot c % NST, lane k < 6
-        // issuing copy k after lane 0 has announced the bytes
-        auto issue = [&](int c) {
-            uint64_t* bar = &bars[c % NST];
-            if (lane == 0) ac::mbar_expect_tx(bar, 6u * seg_bytes);
-            __syncwarp();
-            if (lane < 6) {
-                const int row = row_of(c);
-                const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
-                const int y = row - z * L;
-                const int par = (y + z + a.colour) & 1;
-                const int src = lane < 2    ? row
-                                : lane == 2 ? row + (y + 1 == L ? 1 - L : 1)
-                                : lane == 3 ? row + (y == 0 ? L - 1 : -1)
-                                : lane == 4 ? row + (z + 1 == L ? 1 - L : 1) * L
-                                            : row + (z == 0 ? L - 1 : -1) * L;
-                const int half = lane == 1 ? 1 - par : par;  // x neighbours sit in the other half
-                ac::fence_proxy_async();  // this slot's earlier reads come before the refill
-                ac::bulk_g2s(ring + (size_t)(c % NST) * 6 * segw + (size_t)lane * segw,
-                             s + ((size_t)src * L + (size_t)half * H) * Wn, seg_bytes, bar);
-            }
-        };
-        for (int c = 0; c < NST && c < a.rows_per_thread; ++c)
-            if (row_of(c) < LL) issue(c);
-        bool ok = true;
-        int c = 0;
-        for (; c < a.rows_per_thread; ++c) {
-            const int row = row_of(c);
-            if (row >= LL) break;
-            ok = __all_sync(0xFFFFFFFFu, ac::mbar_wait(&bars[c % NST], (uint32_t)((c / NST) & 1)));
-            if (!ok) break;
-            const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
-            const int y = row - z * L;
-            const int par = (y + z + a.colour) & 1;
-            const int rowoff = row * L;
-            const int j = j0;  // one site per thread: blockDim.x == G * H
-            const int i = rowoff + 2 * j + par;  // logical site (counters, couplings)
-            const int is = rowoff + par * H + j;  // storage position
-            const int jp = j + par == H ? 0 : j + par, jm = j + par == 0 ? H - 1 : j + par - 1;
-            const uint32_t* buf = ring + (size_t)(c % NST) * 6 * segw;
-            const mp::Couplings cp = UNITJ ? mp::decode_unit(a.j1_ptrs[inst][i])
-                                           : mp::decode_general(a.j6_ptrs[inst][i]);
-#pragma unroll
-            for (int ch = 0; ch < CH; ++ch) {
-                const int w0 = wbase + ch * WG;
-                uint32_t self[WG], P[WG];
-                mp::load_words<WG>(buf + j * Wn + w0, self);
-#pragma unroll
-                for (int wi = 0; wi < WG; ++wi) P[wi] = 0;
-#pragma unroll
-                for (int q = 0; q < 6; ++q) {
-                    // q = +x, -x, +y, -y, +z, -z: half row 1 (at jp, jm), then rows 2..5 at j
-                    const int at = q == 0 ? segw + jp * Wn : q == 1 ? segw + jm * Wn : (q) * segw + j * Wn;
-                    uint32_t n[WG];
-                    mp::load_words<WG>(buf + at + w0, n);
-#pragma unroll
-                    for (int wi = 0; wi < WG; ++wi) P[wi] += mp::bond_term(n[wi], cp, q);
-                }
-                const uint32_t* thr = PT ? s_thr + 4 * w0 * kThrStride : s_thr;
-                if (mp::update_words<PT, UNITJ, WG, kThrStride, true>(self, P, vmask[ch], cp.msum, (uint32_t)i,
-                                                                     sweep, (uint32_t)w0, key, thr,
-                                                                     PT ? s_lead + w0 : &lead_sa, acc[ch],
-                                                                     &ties, (uint32_t)is))
-                    mp::store_words<WG>(s + (size_t)is * Wn + w0, self);
-            }
-            if (PT && ++items == mp::kLaneCapacity<KMAX>) {
-                flush();
-                items = 0;
-            }
-            __syncwarp();  // every lane is done with slot c % NST
-            if (*ties.count >= kTieCap / 2) resolve_list();
-            if (c + NST < a.rows_per_thread && row_of(c + NST) < LL) issue(c + NST);
-        }
-        if (!ok) {
-            // a copy did not arrive: report it, then wait (bounded) for the copies this
-            // warp still has in flight before the block may exit
-            if (lane == 0 && a.status) atomicExch(a.status, SG_ETIMEOUT);
-            for (int k = c; k < c + NST && k < a.rows_per_thread; ++k)
-                if (row_of(k) < LL) ac::mbar_wait(&bars[k % NST], (uint32_t)((k / NST) & 1));
-        }
-    } else {
-        // rows are dealt out grid-stride, so the blocks of an instance advance together
-        // through the lattice and the +-z neighbour rows they read are still in L2
-        for (int c = 0; c < a.rows_per_thread; ++c) {
-            const int row = (c * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y;
-            if (row >= LL) break;
-            const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
-            const int y = row - z * L;
-            const int par = (y + z + a.colour) & 1;
-            const int dyp = (y + 1 == L ? 1 - L : 1) * L, dym = (y == 0 ? L - 1 : -1) * L;
-            const int dzp = (z + 1 == L ? 1 - L : 1) * LL, dzm = (z == 0 ? L - 1 : -1) * LL;
-            const int rowoff = row * L;
-            for (int j = j0; j < H; j += JX) {
-                const int x = 2 * j + par;
-                const int i = rowoff + x;  // logical site (counters, couplings)
-                // storage positions (colour-split rows): this site is entry j of half `par`;
-                // its x neighbours are entries j + par and j + par - 1 of the other half
-                const int is = rowoff + par * H + j;
-                const int ho = rowoff + (1 - par) * H;
-                const int jp = j + par == H ? 0 : j + par, jm = j + par == 0 ? H - 1 : j + par - 1;
-                const int nb[6] = {ho + jp, ho + jm, is + dyp, is + dym, is + dzp, is + dzm};
-                const mp::Couplings cp = UNITJ ? mp::decode_unit(a.j1_ptrs[inst][i])
-                                               : mp::decode_general(a.j6_ptrs[inst][i]);
-    #pragma unroll
-                for (int ch = 0; ch < CH; ++ch) {
-                    const int w0 = wbase + ch * WG;
-                    uint32_t self[WG], P[WG];
-                    mp::load_words<WG>(s + (size_t)is * Wn + w0, self);
-    #pragma unroll
-                    for (int wi = 0; wi < WG; ++wi) P[wi] = 0;
-    #pragma unroll
-                    for (int q = 0; q < 6; ++q) {
-                        uint32_t n[WG];
-                        mp::load_words<WG>(s + (size_t)nb[q] * Wn + w0, n);
-    #pragma unroll
-                        for (int wi = 0; wi < WG; ++wi) P[wi] += mp::bond_term(n[wi], cp, q);
-                    }
-                    const uint32_t* thr = PT ? s_thr + 4 * w0 * kThrStride : s_thr;
-                    if (mp::update_words<PT, UNITJ, WG, kThrStride, true>(self, P, vmask[ch], cp.msum,
-                                                                         (uint32_t)i, sweep, (uint32_t)w0, key,
-                                                                         thr, PT ? s_lead + w0 : &lead_sa,
-                                                                         acc[ch], &ties, (uint32_t)is))
-                        mp::store_words<WG>(s + (size_t)is * Wn + w0, self);
-                }
-                if (PT && ++items == mp::kLaneCapacity<KMAX>) {
-                    flush();
-                    items = 0;
-                }
-            }
-        }
-
+        for (int m = 0; m < 24; ++m) tp[m] = s_tp[(PT ? g : 0) * 24 + m];
     }
 
+    // ---- deferred ties of this thread's warp ----
+    const int warp = tid >> 5, lane = tid & 31;
+    const int warp_lanes = min(32, nthreads - 32 * warp);  // the block's last warp may be partial
+    const unsigned wm = warp_lanes == 32 ? 0xFFFFFFFFu : (1u << warp_lanes) - 1u;
+    uint4* ties = s_ties + warp * kTieCap * 2;
+    auto thr_row = [&](uint32_t w) -> const uint32_t* { return PT ? s_thr + 32 * w * kThrStride : s_thr; };
+    // applies the decided ties of one word (and, in a colour-1 PT launch, their energy
+    // change 2k to the slots' sums)
+    auto apply_ties = [&](uint32_t is, uint32_t w, uint32_t acc, uint32_t c0, uint32_t c1) {
+        if (!acc) return;
+        s[(size_t)is * Wn + w] ^= acc;
+        if (energy)
+            for (uint32_t m = acc; m; m &= m - 1u) {
+                const int b = __ffs(m) - 1;
+                const int c = 4 + (int)((c0 >> b) & 1u) + 2 * (int)((c1 >> b) & 1u);
+                atomicAdd(&s_E[32 * w + b], 2 * (2 * c - 6));
+            }
+    };
+    auto resolve_list = [&]() {
+        __syncwarp(wm);
+        const int n = min(s_tie_n[warp], kTieCap);
+        const int rank = __popc(wm & ((1u << lane) - 1u));
+        for (int e = rank; e < n; e += warp_lanes) {
+            const uint4 t = ties[2 * e], u = ties[2 * e + 1];
+            const uint32_t acc = mp::resolve_tie_bits(t.w, u.x, u.y, thr_row(t.z), PT ? kThrStride : 0, t.x, sweep,
+                                                      t.z, key.k0, key.k1);
+            apply_ties(t.y, t.z, acc, u.x, u.y);
+        }
+        __syncwarp(wm);
+        if (rank == 0) s_tie_n[warp] = 0;
+        __syncwarp(wm);
+    };
+    // queues the ties of one word; when the list is full they are decided here instead and
+    // the accepted ones returned, to join the word's flips
+    auto queue_tie = [&](uint32_t i, uint32_t is, uint32_t w, uint32_t tie, uint32_t c0, uint32_t c1) -> uint32_t {
+        const int pos = atomicAdd(&s_tie_n[warp], 1);
+        if (pos < kTieCap) {
+            ties[2 * pos] = make_uint4(i, is, w, tie);
+            ties[2 * pos + 1] = make_uint4(c0, c1, 0u, 0u);
+            return 0u;
+        }
+        return mp::resolve_tie_bits(tie, c0, c1, thr_row(w), PT ? kThrStride : 0, i, sweep, w, key.k0, key.k1);
+    };
+
+    // ---- energy counters (colour-1 PT launches) ----
+    uint32_t V[kVBits];
+#pragma unroll
+    for (int j = 0; j < kVBits; ++j) V[j] = 0;
+    int nitems = 0;
+    auto fold_thread = [&]() {  // this thread's counters into the block sums (any time)
+        for (int b = 0; b < 32; ++b) {
+            const int e = 6 * nitems - 2 * mp::vcount(V, b);
+            if (e) atomicAdd(&s_E[32 * g + b], e);
+        }
+#pragma unroll
+        for (int j = 0; j < kVBits; ++j) V[j] = 0;
+        nitems = 0;
+    };
+
+    // a warp stays converged through a row when it lies in one row of threads, every
+    // thread of it has the same number of sites in the row, and of words per site
+    const bool uniform_rows = blockDim.x % 32 == 0 && H % JX == 0 && Wn % G == 0;
+
+    for (int c = 0; c < a.rows_per_thread; ++c) {
+        const int row = (c * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y;
+        if (row >= LL) break;
+        const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
+        const int y = row - z * L;
+        const int par = (y + z + a.colour) & 1;
+        const int dyp = (y + 1 == L ? 1 - L : 1) * L, dym = (y == 0 ? L - 1 : -1) * L;
+        const int dzp = (z + 1 == L ? 1 - L : 1) * LL, dzm = (z == 0 ? L - 1 : -1) * LL;
+        const int rowoff = row * L;
+        for (int j = j0; j < H; j += JX) {
+            const int i = rowoff + 2 * j + par;   // logical site (counters, couplings)
+            const int is = rowoff + par * H + j;  // storage position
+            const int ho = rowoff + (1 - par) * H;
+            const int jp = j + par == H ? 0 : j + par, jm = j + par == 0 ? H - 1 : j + par - 1;
+            const int nb[6] = {ho + jp, ho + jm, is + dyp, is + dym, is + dzp, is + dzm};
+            uint32_t S[6];
+            int J[6];
+            if (UNITJ) {
+                mp::unit_signs(a.j1_ptrs[inst][i], S);
+            } else {
+                const uint2 r = a.j6_ptrs[inst][i];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) J[q] = (int)(int8_t)(((q < 4 ? r.x : r.y) >> (8 * (q & 3))) & 0xFFu);
+            }
+            for (int w = g; w < Wn; w += G) {
+                const uint32_t self = s[(size_t)is * Wn + w];
+                uint32_t n[6];
+#pragma unroll
+                for (int q = 0; q < 6; ++q) n[q] = s[(size_t)nb[q] * Wn + w];
+                const uint32_t valid = valid_bits(a.Rvalid, w);
+                uint32_t A[8];
+                mp::lead_planes((uint32_t)i, sweep, (uint32_t)w, key, A);
+                uint32_t flip;
+                if (UNITJ) {
+                    uint32_t tie, c0, c1, c2;
+                    mp::update_word_unit(self, n, S, valid, tp, A, &flip, &tie, &c0, &c1, &c2);
+                    if (tie) flip |= queue_tie((uint32_t)i, (uint32_t)is, (uint32_t)w, tie, c0, c1);
+                    if (energy) {
+                        mp::count_after_flip(flip, c0, c1, c2);
+                        mp::vadd3(V, c0, c1, c2);
+                        if (++nitems == kVItems) fold_thread();
+                    }
+                } else {
+                    flip = mp::update_word_general(self, n, J, valid, thr_row((uint32_t)w), PT ? kThrStride : 0, A,
+                                                   (uint32_t)i, sweep, (uint32_t)w, key);
+                    if (energy) {  // slow path: each replica's s_i sum_q J_q s_q after the update
+                        const uint32_t after = self ^ flip;
+                        for (int b = 0; b < 32; ++b) {
+                            int h = 0;
+#pragma unroll
+                            for (int q = 0; q < 6; ++q) h += J[q] * (((n[q] >> b) & 1u) ? -1 : 1);
+                            const int e = ((after >> b) & 1u) ? -h : h;
+                            if (e) atomicAdd(&s_E[32 * w + b], e);
+                        }
+                    }
+                }
+                if (flip) s[(size_t)is * Wn + w] = self ^ flip;
+            }
+        }
+        if (uniform_rows) {
+            __syncwarp(wm);
+            if (s_tie_n[warp] >= kTieCap / 2) resolve_list();
+        }
+    }
     resolve_list();
-    if (PT) {
-        flush();
+
+    if (energy) {
+        if (UNITJ) {
+            if (warp_lanes == 32) {
+                // lane r collects replica r of every lane through a bit transpose per plane
+                uint32_t T[kVBits];
+#pragma unroll
+                for (int jb = 0; jb < kVBits; ++jb) T[jb] = mp::warp_transpose(V[jb], lane);
+                for (int w = 0; w < Wn; ++w) {
+                    const unsigned m = __ballot_sync(0xFFFFFFFFu, g == w);
+                    if (!m) continue;
+                    const int items = __reduce_add_sync(0xFFFFFFFFu, g == w ? nitems : 0);
+                    int cnt = 0;
+#pragma unroll
+                    for (int jb = 0; jb < kVBits; ++jb) cnt += __popc(T[jb] & m) << jb;
+                    const int e = 6 * items - 2 * cnt;
+                    if (e) atomicAdd(&s_E[32 * w + lane], e);
+                }
+            } else {
+                fold_thread();
+            }
+        }
         __syncthreads();
         int32_t* Ei = a.E + (size_t)inst * Rp;
         for (int q = tid; q < Rp; q += nthreads)
-            if (s_dE[q]) atomicAdd(&Ei[q], s_dE[q]);
+            if (s_E[q]) atomicAdd(&Ei[q], s_E[q]);
         if (XCH) {
             // The block that finishes last for this instance performs the exchange: every
             // block publishes its energy sums, then counts itself done; no block waits.
@@ -371,62 +293,15 @@ __global__ void __launch_bounds__(256, MINB) sweep_rows_kernel(const SweepArgs a
     }
 }
 
-// Tuning knob SG_DRAW_ALWAYS (default 1): compute the draws unconditionally in the
-// padding-free variants (0: only when some lane of the warp needs one).
-bool draw_always()
-{
-    static const bool v = [] {
-        const char* e = getenv("SG_DRAW_ALWAYS");
-        return !(e && atoi(e) == 0);
-    }();
-    return v;
-}
-
 struct SweepShape {
     dim3 block, grid;
-    int G, CH, WG, rows_per_thread;
-    int nst = 0;      // staged variant: rows in flight per warp (0: plain loads)
-    size_t smem = 0;  // staged variant: dynamic shared memory per block
+    int G, rows_per_thread;
 };
 
-// Tuning knob SG_ROWS_STAGE: rows in flight per warp in the staged variant, 2 (default)
-// or 3; 0 turns the staged variant off.  Read at every launch.
-int stage_depth()
-{
-    const char* e = getenv("SG_ROWS_STAGE");
-    const int d = e ? atoi(e) : 2;
-    return (d == 0 || d == 3) ? d : 2;
-}
-
-// Tuning knob: largest number of 4-word chunks per thread (1 or 2), from the
-// environment variable SG_SWEEP_MAX_CH (default 2).
-int max_chunks()
-{
-    static const int v = [] {
-        const char* e = getenv("SG_SWEEP_MAX_CH");
-        return (e && atoi(e) == 1) ? 1 : 2;
-    }();
-    return v;
-}
-
-// Tuning knob SG_ROWS_MINB (2, 3 or 4): resident blocks per SM the register budget is
-// cut for, for the padding-free four-word variants.
-int rows_min_blocks()
-{
-    static const int v = [] {
-        const char* e = getenv("SG_ROWS_MINB");
-        const int m = e ? atoi(e) : 0;
-        return (m == 3 || m == 4) ? m : 2;
-    }();
-    return v;
-}
-
-SweepShape sweep_shape(int I, int L, int Wn, bool pt, bool pad)
+SweepShape sweep_shape(int I, int L, int Wn)
 {
     SweepShape sh;
-    sh.WG = (Wn % 4 == 0) ? 4 : (Wn % 2 == 0) ? 2 : 1;
-    sh.CH = (sh.WG == 4 && (Wn / 4) % 2 == 0 && max_chunks() == 2) ? 2 : 1;
-    sh.G = Wn / (sh.WG * sh.CH);
+    sh.G = Wn < 256 ? Wn : 256;
     const int H = L / 2;
     int JX = 256 / sh.G;
     if (JX < 1) JX = 1;
@@ -439,28 +314,9 @@ SweepShape sweep_shape(int I, int L, int Wn, bool pt, bool pad)
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    long long bps = rows_min_blocks();
-    // staged variant: one warp per row (a half row is exactly 32 threads' sites), rows
-    // whose halves are whole 16-byte units, and room for the ring in shared memory
-    if (stage_depth() > 0 && !pad && sh.WG == 4 && TX == 32 && sh.G * H == 32 && (H * Wn) % 4 == 0 &&
-        rows_min_blocks() == 2 && draw_always()) {
-        int per_sm = 0, per_block = 0;
-        cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
-        cudaDeviceGetAttribute(&per_block, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-        const int nst = stage_depth();
-        const size_t ring = (size_t)TY * nst * 6 * (size_t)(H * Wn) * 4;
-        const size_t thr = pt ? (size_t)staged_thr_words(4 * Wn) * 4 : 0;
-        const size_t fixed = (pt ? 256 * 4 + 64 * 16 : kThrRow * 4 + 16) + 8 * 8 * 3 + 8 * kTieCap * 16 + 32 + 64;
-        const size_t need = ring + thr;
-        const long long fit = (long long)per_sm / (long long)(need + fixed + 1024);
-        if ((long long)need <= per_block && fit >= 1) {
-            sh.nst = nst;
-            sh.smem = need;
-            bps = fit < 2 ? fit : 2;
-        }
-    }
-    // rows per thread: enough blocks for about two per SM, so that each block fills
-    // its threshold table and reduces its energies once for many rows
+    // rows per thread: enough blocks for about two per SM, so that each block fills its
+    // threshold tables and reduces its energies once for many rows
+    const long long bps = 2;
     long long rpt = ((long long)LL * I + (long long)TY * bps * sms - 1) / ((long long)TY * bps * sms);
     if (rpt < 1) rpt = 1;
     const char* e = getenv("SG_ROWS_RPT");  // tuning knob: rows per thread
@@ -471,84 +327,21 @@ SweepShape sweep_shape(int I, int L, int Wn, bool pt, bool pad)
     return sh;
 }
 
-// Launches one instantiation with the shape's dynamic shared memory (raising the
-// kernel's limit when the staged ring needs more than the default 48 KB).
-template <typename K>
-void launch_with_smem(K kernel, const SweepShape& sh, const SweepArgs& a, cudaStream_t st)
-{
-    if (sh.smem > 48 * 1024)
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sh.smem);
-    kernel<<<sh.grid, sh.block, sh.smem, st>>>(a);
-}
-
-template <bool PT, bool UNITJ, int CH>
-void launch_nopad(const SweepShape& sh, const SweepArgs& a, bool xch, cudaStream_t st)
-{
-    if (sh.nst == 2 || sh.nst == 3) {
-        if (PT && xch)
-            launch_with_smem(sh.nst == 2 ? sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2, true, true, 2>
-                                         : sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2, true, true, 3>,
-                             sh, a, st);
-        else
-            launch_with_smem(sh.nst == 2 ? sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2, true, false, 2>
-                                         : sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2, true, false, 3>,
-                             sh, a, st);
-        return;
-    }
-    if (draw_always() && rows_min_blocks() == 2) {
-        if (PT && xch)
-            sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2, true, true><<<sh.grid, sh.block, 0, st>>>(a);
-        else
-            sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2, true><<<sh.grid, sh.block, 0, st>>>(a);
-        return;
-    }
-    switch (rows_min_blocks()) {
-    case 4:
-        sweep_rows_kernel<PT, UNITJ, 4, CH, false, 4><<<sh.grid, sh.block, 0, st>>>(a);
-        break;
-    case 3:
-        sweep_rows_kernel<PT, UNITJ, 4, CH, false, 3><<<sh.grid, sh.block, 0, st>>>(a);
-        break;
-    default:
-        sweep_rows_kernel<PT, UNITJ, 4, CH, false, 2><<<sh.grid, sh.block, 0, st>>>(a);
-    }
-}
-
-// Launches the variant for the shape; returns true when it also performed the exchange.
-template <bool PT, bool UNITJ>
-bool launch_variant(const SweepShape& sh, const SweepArgs& a, bool pad, bool xch, cudaStream_t st)
-{
-    const bool fused = xch && !pad && draw_always() && rows_min_blocks() == 2 && sh.WG == 4;
-    if (sh.WG == 4 && sh.CH == 2) {
-        if (pad)
-            sweep_rows_kernel<PT, UNITJ, 4, 2, true><<<sh.grid, sh.block, 0, st>>>(a);
-        else
-            launch_nopad<PT, UNITJ, 2>(sh, a, fused, st);
-    } else if (sh.WG == 4) {
-        if (pad)
-            sweep_rows_kernel<PT, UNITJ, 4, 1, true><<<sh.grid, sh.block, 0, st>>>(a);
-        else
-            launch_nopad<PT, UNITJ, 1>(sh, a, fused, st);
-    } else if (sh.WG == 2) {
-        sweep_rows_kernel<PT, UNITJ, 2, 1, true><<<sh.grid, sh.block, 0, st>>>(a);
-    } else {
-        sweep_rows_kernel<PT, UNITJ, 1, 1, true><<<sh.grid, sh.block, 0, st>>>(a);
-    }
-    return fused;
-}
-
 template <bool PT>
 int32_t launch_rows(SweepArgs a, int I, bool unit_j, bool xch, bool* fused, cudaStream_t st)
 {
-    const bool pad = a.Rvalid != 4 * a.Wn;  // padding replicas in the last word
-    const SweepShape sh = sweep_shape(I, a.L, a.Wn, PT, pad);
+    const SweepShape sh = sweep_shape(I, a.L, a.Wn);
     a.G = sh.G;
     a.rows_per_thread = sh.rows_per_thread;
     a.Lmagic = (uint32_t)((0x100000000ull + (uint64_t)a.L - 1) / (uint64_t)a.L);
-    a.segw = (a.L / 2) * a.Wn;
-    const bool f = unit_j ? launch_variant<PT, true>(sh, a, pad, xch, st)
-                          : launch_variant<PT, false>(sh, a, pad, xch, st);
-    if (fused) *fused = f;
+    if (PT && xch) {
+        if (unit_j) sweep_bits_kernel<PT, true, true><<<sh.grid, sh.block, 0, st>>>(a);
+        else sweep_bits_kernel<PT, false, true><<<sh.grid, sh.block, 0, st>>>(a);
+    } else {
+        if (unit_j) sweep_bits_kernel<PT, true, false><<<sh.grid, sh.block, 0, st>>>(a);
+        else sweep_bits_kernel<PT, false, false><<<sh.grid, sh.block, 0, st>>>(a);
+    }
+    if (fused) *fused = PT && xch;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("sweep launch failed: %s", cudaGetErrorString(e));
@@ -559,18 +352,13 @@ int32_t launch_rows(SweepArgs a, int I, bool unit_j, bool xch, bool* fused, cuda
 
 }  // namespace
 
-bool rows_kernel_supports(int Wn)
-{
-    const int WG = (Wn % 4 == 0) ? 4 : (Wn % 2 == 0) ? 2 : 1;
-    const int CH = (WG == 4 && (Wn / 4) % 2 == 0 && max_chunks() == 2) ? 2 : 1;
-    return Wn / (WG * CH) <= 256;
-}
+bool rows_kernel_supports(int Wn) { return Wn >= 1; }
 
 int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_row, bool unit_j, int I, int L, int Wn, int R,
                              uint32_t sweep, int colour, cudaStream_t st, const uint32_t* sweep_base,
-                             int* status)
+                             int* /*status*/)
 {
     SweepArgs a{};
     a.spins = reinterpret_cast<uint32_t*>(spins);
@@ -584,7 +372,6 @@ int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
     a.sweep = sweep;
     a.colour = colour;
     a.sweep_base = sweep_base;
-    a.status = status;
     return launch_rows<false>(a, I, unit_j, false, nullptr, st);
 }
 
@@ -593,7 +380,7 @@ int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
                              const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st,
-                             const uint32_t* sweep_base, int* status)
+                             const uint32_t* sweep_base, int* /*status*/)
 {
     SweepArgs a{};
     a.spins = reinterpret_cast<uint32_t*>(spins);
@@ -611,8 +398,7 @@ int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
     if (xch) a.x = *xch;
     a.done = done;
     a.sweep_base = sweep_base;
-    a.status = status;
-    return launch_rows<true>(a, I, unit_j, xch != nullptr, fused, st);
+    return launch_rows<true>(a, I, unit_j, xch != nullptr && colour == 1, fused, st);
 }
 
 }  // namespace sg

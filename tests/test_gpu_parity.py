@@ -47,11 +47,11 @@ def test_sa_L4_R8_S1000_full(sg):
 
 def test_sa_L16_R1024_S1000_sampled(sg):
     """Workload: L=16, 1024 replicas, 1000 sweeps -- full run on the GPU, replicas sampled
-    across every 4-replica word position and both ends checked against the oracle."""
+    across bit positions of several 32-replica words and both ends checked against the oracle."""
     w = wl.SA_L16
     inst = sg.Instance.create(w.L, w.instance_seed(0), w.class_prob, True)
     J3, _, egs = inst.get()
-    reps = [0, 1, 2, 3, 257, 514, 771, 1020, 1021, 1022, 1023]
+    reps = [0, 1, 31, 32, 257, 514, 771, 1020, 1021, 1022, 1023]
     res = _sa_compare(sg, inst, J3, egs, w.replicas, w.sweeps, w.beta0, w.beta1, reps=reps)
     assert (res["E"] >= egs).all()
     # every replica's reported energy equals a recompute of its spins
@@ -61,7 +61,7 @@ def test_sa_L16_R1024_S1000_sampled(sg):
 @pytest.mark.parametrize("L,R,S,geo", [(2, 5, 40, False), (6, 13, 30, True), (10, 7, 25, False),
                                        (12, 4, 20, True), (8, 1, 60, False)])
 def test_sa_ragged_shapes(sg, L, R, S, geo):
-    """Ragged replica counts (R not a multiple of 4), L=2 multi-edges, several tiles."""
+    """Ragged replica counts (R not a multiple of 32), L=2 multi-edges, several row blocks."""
     inst = sg.Instance.create(L, 1000 + L, wl.UNIFORM, True)
     J3, _, egs = inst.get()
     _sa_compare(sg, inst, J3, egs, R, S, 0.2, 2.5, geometric=geo, seed=77 + L, iid=L)
@@ -182,44 +182,44 @@ def test_energy_device_input_and_validation(sg):
     assert e.value.code == sg.SG_EINVAL
 
 
-@pytest.mark.parametrize("zc", ["1", "16", "32"])
-def test_pt_tile_kernel_zranges(sg, monkeypatch, zc):
-    """Shared-memory streaming kernel with slab ranges of 1, 16 and 32 (longer than the
-    8-bit energy lanes hold, so the periodic fold is exercised)."""
-    monkeypatch.setenv("SG_SWEEP_KERNEL", "2")
-    monkeypatch.setenv("SG_TILE_ZC", zc)
-    inst = sg.Instance.create(32, 77)
-    J3, _, egs = inst.get()
-    _pt_compare(sg, inst, J3, egs, 8, 6, 0.2, 3.0, seed=4, iid=2)
-
-
-def test_sweep_kernels_agree(sg, monkeypatch):
-    """The row kernel and the shared-memory kernel give the same bytes."""
-    insts = [sg.Instance.create(32, 900 + k) for k in range(3)]
-    params = [dict(temps=32, sweeps=12, beta_min=0.2, beta_max=3.0, seed=8, instance_id=k)
-              for k in range(3)]
-    monkeypatch.setenv("SG_SWEEP_KERNEL", "1")
-    rows = sg.pt_run_batch(insts, params, spins="host")
-    monkeypatch.setenv("SG_SWEEP_KERNEL", "2")
-    tile = sg.pt_run_batch(insts, params, spins="host")
-    for a, b in zip(rows, tile):
-        assert np.array_equal(a["spins"], b["spins"]) and np.array_equal(a["E"], b["E"])
-        assert a["minE"] == b["minE"] and np.array_equal(a["perm"], b["perm"])
-    sa_rows = None
-    monkeypatch.setenv("SG_SWEEP_KERNEL", "1")
-    sa_rows = sg.sa_run(insts[0], 36, 15, 0.1, 3.0, seed=2, spins="host")
-    monkeypatch.setenv("SG_SWEEP_KERNEL", "2")
-    sa_tile = sg.sa_run(insts[0], 36, 15, 0.1, 3.0, seed=2, spins="host")
-    assert np.array_equal(sa_rows["spins"], sa_tile["spins"])
-
-
-@pytest.mark.parametrize("kernel", ["1", "2"])
-@pytest.mark.parametrize("L,R", [(16, 32), (32, 64), (48, 8)])
-def test_sa_kernel_shapes(sg, monkeypatch, kernel, L, R):
-    monkeypatch.setenv("SG_SWEEP_KERNEL", kernel)
+@pytest.mark.parametrize("L,R", [(16, 32), (32, 64), (48, 8), (8, 31), (8, 33), (6, 65), (10, 100)])
+def test_sa_word_shapes(sg, L, R):
+    """Replica counts below, at and above whole 32-replica words (ragged last words)."""
     inst = sg.Instance.create(L, 40 + L)
     J3, _, egs = inst.get()
-    _sa_compare(sg, inst, J3, egs, R, 12, 0.1, 3.0, seed=6, reps=[0, 5, R - 1])
+    reps = sorted({0, 5 % R, R // 2, R - 1})
+    _sa_compare(sg, inst, J3, egs, R, 12, 0.1, 3.0, seed=6, reps=reps)
+
+
+@pytest.mark.parametrize("L,K,S", [(8, 40, 6), (6, 64, 8), (10, 100, 4), (4, 33, 12)])
+def test_pt_several_words(sg, L, K, S):
+    """Temperature ladders spanning two to four spin words, ragged and whole."""
+    inst = sg.Instance.create(L, 7400 + L)
+    J3, _, egs = inst.get()
+    _pt_compare(sg, inst, J3, egs, K, S, 0.2, 3.0, seed=13, iid=1)
+
+
+def test_pt_general_couplings(sg):
+    """Couplings with |J| = 2 and zeros take the replica-by-replica path, energies included."""
+    L = 6
+    J3 = wl.random_couplings(21, L, jmax=2)
+    inst = sg.Instance.from_couplings(L, J3)
+    res = sg.pt_run(inst, 12, 10, 0.2, 1.5, seed=7, instance_id=2, spins="host")
+    ref = o.pt_run(L, J3, 7, 2, 12, 10, 0.2, 1.5)
+    assert np.array_equal(res["spins"], ref["spins"])
+    assert np.array_equal(res["E"], ref["E"])
+    assert np.array_equal(res["perm"], ref["perm"])
+    assert np.array_equal(res["accepts"], ref["accepts"])
+    assert res["minE"] == ref["minE"]
+
+
+def test_pt_long_thread_runs_fold_energy_counters(sg, monkeypatch):
+    """Every thread walks 400 rows (more sites than its energy counters hold before a
+    fold), so the colour-1 energy sums fold mid-run and at the end."""
+    monkeypatch.setenv("SG_ROWS_RPT", "400")
+    inst = sg.Instance.create(32, 7500)
+    J3, _, egs = inst.get()
+    _pt_compare(sg, inst, J3, egs, 32, 3, 0.2, 3.0, seed=5, iid=4)
 
 
 # --------------------------------------------------------------------------- uneven batches
@@ -291,42 +291,21 @@ def test_uneven_batch_any_plane_width(sg, monkeypatch, wg, graph):
         assert np.array_equal(a["E"], b["E"])
 
 
-# --------------------------------------------------------------------------- staged rows
+# --------------------------------------------------------------------------- wide shapes
 
-# Shapes whose half row is exactly one warp's sites (the staged variant: bulk copies of
-# the six half rows into shared memory, NST rows ahead).
+# Shapes from one word of replicas on a large lattice to eight words on a small one.
 @pytest.mark.parametrize("L,K,S", [(64, 16, 2), (32, 64, 2), (16, 128, 3), (8, 256, 4)])
-def test_pt_staged_shapes_match_oracle(sg, L, K, S):
+def test_pt_wide_shapes_match_oracle(sg, L, K, S):
     inst = sg.Instance.create(L, 7000 + L)
     J3, _, egs = inst.get()
     _pt_compare(sg, inst, J3, egs, K, S, 0.2, 3.0, seed=21, iid=3)
 
 
 @pytest.mark.parametrize("L,R,S", [(64, 32, 2), (32, 64, 3), (16, 128, 4), (8, 256, 5), (2, 1024, 6)])
-def test_sa_staged_shapes_match_oracle(sg, L, R, S):
+def test_sa_wide_shapes_match_oracle(sg, L, R, S):
     inst = sg.Instance.create(L, 7100 + L)
     J3, _, egs = inst.get()
     _sa_compare(sg, inst, J3, egs, R, S, 0.1, 3.0, seed=5, iid=1)
-
-
-@pytest.mark.parametrize("depth", ["2", "3"])
-def test_staged_equals_plain_loads(sg, monkeypatch, depth):
-    """The staged variant (either ring depth) and the plain-load variant give the same bytes."""
-    insts = [sg.Instance.create(64, 7200 + k) for k in range(3)]
-    params = [dict(temps=32, sweeps=12, beta_min=0.2, beta_max=3.0, seed=8, instance_id=k)
-              for k in range(3)]
-    monkeypatch.setenv("SG_ROWS_STAGE", "0")
-    plain = sg.pt_run_batch(insts, params, spins="host")
-    sa_plain = sg.sa_run(insts[0], 32, 10, 0.1, 3.0, seed=2, spins="host")
-    monkeypatch.setenv("SG_ROWS_STAGE", depth)
-    staged = sg.pt_run_batch(insts, params, spins="host")
-    sa_staged = sg.sa_run(insts[0], 32, 10, 0.1, 3.0, seed=2, spins="host")
-    for a, b in zip(plain, staged):
-        assert np.array_equal(a["spins"], b["spins"]) and np.array_equal(a["E"], b["E"])
-        assert a["minE"] == b["minE"] and np.array_equal(a["perm"], b["perm"])
-        assert np.array_equal(a["accepts"], b["accepts"])
-    assert np.array_equal(sa_plain["spins"], sa_staged["spins"])
-    assert np.array_equal(sa_plain["E"], sa_staged["E"])
 
 
 @pytest.mark.parametrize("L,R,S", [(16, 256, 20), (8, 64, 30), (24, 16, 10), (2, 12, 25), (2, 5, 40)])
