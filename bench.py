@@ -34,7 +34,8 @@ from paper_2501_17267_gb300 import workloads as wl  # noqa: E402
 WORK = wl.PT_L64
 METRIC = "Metropolis spin-flip attempts/s"
 UNIT = "attempts/s"
-BYTES_PER_ATTEMPT = 2.0 + 3.0 / WORK.temps  # spin byte read + written once per sweep, 3 J bytes per site
+# spin bit read + written once per sweep (2/8 B), 3 coupling bytes per site shared by R replicas
+BYTES_PER_ATTEMPT = 2.0 / 8.0 + 3.0 / WORK.temps
 
 
 def _peaks():
@@ -47,29 +48,54 @@ def _peaks():
         return 6800.0, "fallback", 2070.0
 
 
-# Roofs of one attempt.  HBM: 1 B of spin read and 1 B written per sweep plus 3/R B of
-# couplings (bytes_per_attempt).  Integer: an attempt's leading draw byte is a quarter of
-# a Philox4x32-10 word, and a Philox block (16 bytes) costs 20 32x32->64-bit multiplies,
-# i.e. 1.25 per attempt (the low 24 bits are drawn for 1/256 of the draws); the SM runs 32
-# such multiplies per clock, so the multiply pipe caps a GB300 at SMs * 32 / 1.25
-# attempts per clock -- above the HBM roof, which therefore binds.
+# Roofs of one attempt.  HBM: one spin bit read and one written per sweep plus 3/R B of
+# couplings (bytes_per_attempt).  Integer: the eight leading-byte bit planes of a word of
+# 32 replicas come from two Philox4x32-10 blocks of 20 32x32->64-bit multiplies each,
+# i.e. 1.25 multiplies per attempt (the low 24 bits are drawn for 1/256 of the draws);
+# the SM runs 32 such multiplies per clock.  With bit-packed spins the multiply roof,
+# SMs * 32 / 1.25 attempts per clock, lies below the HBM roof and binds.
 MULS_PER_ATTEMPT = 1.25
 WIDE_MULS_PER_SM_CLOCK = 32
 
 
 def _roof(rate, bytes_per_attempt, sms, sm_mhz, peak, peak_kind, **extra):
-    """The roofline object: HBM bound (algorithmic bytes / s against the measured copy
-    bandwidth), with the integer-multiply view beside it."""
+    """The roofline object for a kernel running `rate` attempts/s: bound by whichever of
+    the two roofs allows fewer attempts per second -- the multiply pipe (Philox draws;
+    derived from the SM count and clock) or HBM (algorithmic bytes against the measured
+    copy bandwidth) -- with the other roof beside it."""
     gbs = rate * bytes_per_attempt / 1e9
-    alu_peak = sms * WIDE_MULS_PER_SM_CLOCK / MULS_PER_ATTEMPT * sm_mhz * 1e6
-    r = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-         "peak_source": peak_kind, "bytes_per_attempt": bytes_per_attempt,
-         "attempts_per_s": rate,
-         "alu": {"achieved": rate, "peak": alu_peak, "unit": "attempts/s", "frac": rate / alu_peak,
-                 "peak_source": f"derived: {sms} SMs x {WIDE_MULS_PER_SM_CLOCK} 32x32->64 multiplies per "
-                                f"clock / {MULS_PER_ATTEMPT} per attempt at {sm_mhz:.0f} MHz"}}
+    tmul = rate * MULS_PER_ATTEMPT / 1e12
+    mul_peak = sms * WIDE_MULS_PER_SM_CLOCK * sm_mhz * 1e6 / 1e12
+    hbm = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
+           "peak_source": peak_kind, "bytes_per_attempt": bytes_per_attempt}
+    alu = {"bound": "alu", "achieved": tmul, "peak": mul_peak, "unit": "T 32x32->64-bit multiplies/s",
+           "frac": tmul / mul_peak, "muls_per_attempt": MULS_PER_ATTEMPT,
+           "peak_source": f"derived: {sms} SMs x {WIDE_MULS_PER_SM_CLOCK} multiplies per clock "
+                          f"at {sm_mhz:.0f} MHz"}
+    alu_attempts = mul_peak * 1e12 / MULS_PER_ATTEMPT
+    hbm_attempts = peak * 1e9 / bytes_per_attempt
+    main, other = (alu, hbm) if alu_attempts <= hbm_attempts else (hbm, alu)
+    r = dict(main)
+    r["other_roof"] = other
+    r["attempts_per_s"] = rate
     r.update(extra)
     return r
+
+
+L2_FLUSH_BYTES = 256 << 20  # twice the 129 MB L2
+
+
+def _l2_flusher(torch):
+    """A callable that overwrites a buffer larger than L2 on the current stream; the
+    timed loops call it before every step (its time counts in the step)."""
+    buf = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    state = {"k": 0}
+
+    def flush():
+        state["k"] = (state["k"] + 1) & 0xFF
+        buf.fill_(state["k"])
+
+    return flush
 
 
 def _traffic_record():
@@ -153,7 +179,7 @@ def run_reference(args, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * sum(walls) / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": _config(),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": workers, "kind": "oracle",
                              "sample": f"each step: all {WORK.instances} instances, first "
@@ -167,12 +193,17 @@ def _config():
     return {"workload": WORK.name, "L": WORK.L, "instances": WORK.instances, "temps": WORK.temps,
             "sweeps": WORK.sweeps, "beta": f"geometric {WORK.beta_min}->{WORK.beta_max}",
             "exchange": "every sweep", "tiles": "uniform F22/F42/F6, gauged",
-            "cache": "inputs larger than L2: 134 MB of spins + 34 MB of couplings per step"}
+            "cache": "L2 flushed (256 MB written) before every timed step; the step's 17 MB of spins and "
+                     "38 MB of coupling records then stay in L2 across its sweeps"}
 
 
 # ---------------------------------------------------------------- clocks
 
 class ClockSampler:
+    """nvidia-smi sampling every 200 ms.  start() launches it and waits for its first
+    sample, so that its start-up (NVML initialisation, which can stall the GPU on a
+    freshly booted box) happens before the warm-up; mark() opens the timed window and
+    stop() keeps the samples that arrived inside it (plus the one that closes it)."""
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
@@ -180,8 +211,13 @@ class ClockSampler:
     def __init__(self, gpu: int):
         self.gpu = gpu
         self.proc = None
+        self.lines = []
+        self.t0 = None
+        self.reader = None
 
     def start(self):
+        import threading
+        first = threading.Event()
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
@@ -189,15 +225,34 @@ class ClockSampler:
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
         except Exception:
             self.proc = None
+            return
+
+        def read():
+            for line in self.proc.stdout:
+                self.lines.append((time.time(), line))
+                first.set()
+            first.set()
+
+        self.reader = threading.Thread(target=read, daemon=True)
+        self.reader.start()
+        first.wait(timeout=30)
+
+    def mark(self):
+        self.t0 = time.time()
 
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        t1 = time.time()
+        time.sleep(0.25)  # the sample that closes the window
         self.proc.terminate()
-        out, _ = self.proc.communicate(timeout=10)
+        self.proc.wait(timeout=10)
+        self.reader.join(timeout=10)
+        t0 = self.t0 if self.t0 is not None else 0.0
+        window = [line for t, line in self.lines if t0 <= t <= t1 + 0.25]
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in out.strip().splitlines():
+        for line in window:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -344,14 +399,18 @@ def batched_line(sg, args, torch, clocks_cls, local):
                    instance_id=k) for k, (L, S) in enumerate(shapes)]
     attempts = sum(L ** 3 * w.replicas * S for L, S in shapes)
     stream = torch.cuda.current_stream()
-    for _ in range(args.warmup):
-        out = sg.sa_run_batch(insts, params)
     clocks = clocks_cls(local)
     clocks.start()
+    flush = _l2_flusher(torch)
+    for _ in range(args.warmup):
+        flush()
+        out = sg.sa_run_batch(insts, params)
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark()
     ev0.record(stream)
     for _ in range(args.steps):
+        flush()
         out = sg.sa_run_batch(insts, params)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -369,17 +428,18 @@ def batched_line(sg, args, torch, clocks_cls, local):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     roof = None
     if sw["device_ms"] > 0:
-        roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), 2.0 + 3.0 / w.replicas, sms, sm_mhz, peak,
+        roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), 2.0 / 8.0 + 3.0 / w.replicas, sms, sm_mhz, peak,
                      peak_kind, traffic=None, kernel="sa_planes_kernel",
                      launch_ms=sw["device_ms"] / max(sw["launches"], 1))
     value = attempts * args.steps / (ms / 1000.0)
     eps = [float(e) for o in out for e in o["eps"][:4]]
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": {"workload": w.name, "instances": w.instances, "L": list(w.L_choices),
                        "replicas": w.replicas, "sweeps": list(w.sweep_choices),
-                       "attempts_per_step": attempts, "beta": f"linear {w.beta0}->{w.beta1}"},
+                       "attempts_per_step": attempts, "beta": f"linear {w.beta0}->{w.beta1}",
+                       "cache": "L2 flushed (256 MB written) before every timed step"},
             "roofline": roof, "gpu_launches": sum(v["launches"] for v in st.values()),
             "clocks": clk, "eps_mean_sample": sum(eps) / len(eps)}
 
@@ -394,16 +454,20 @@ def sa_line(sg, args, torch, clocks_cls, local):
     attempts = w.L ** 3 * w.replicas * w.sweeps
     stream = torch.cuda.current_stream()
     steps = max(args.steps, 20)
+    clocks = clocks_cls(local)
+    clocks.start()
+    flush = _l2_flusher(torch)
     for _ in range(max(args.warmup, 3)):
+        flush()
         out = sg.sa_run(inst, w.replicas, w.sweeps, w.beta0, w.beta1, "linear", w.run_seed, 0)
     sg.stats_read(reset=True)
     sg.stats_enable(True)
-    clocks = clocks_cls(local)
-    clocks.start()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark()
     ev0.record(stream)
     for _ in range(steps):
+        flush()
         out = sg.sa_run(inst, w.replicas, w.sweeps, w.beta0, w.beta1, "linear", w.run_seed, 0)
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -416,18 +480,19 @@ def sa_line(sg, args, torch, clocks_cls, local):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     roof = None
     if sw["launches"] and sw["device_ms"] > 0:
-        roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), 2.0 + 3.0 / w.replicas, sms, sm_mhz, peak,
+        roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), 2.0 / 8.0 + 3.0 / w.replicas, sms, sm_mhz, peak,
                      peak_kind, traffic=None,
-                     kernel="sa_planes_kernel" if sw["launches"] <= 4 * steps else "sweep_rows_kernel<SA>",
+                     kernel="sa_planes_kernel" if sw["launches"] <= 4 * steps else "sweep_bits_kernel<SA>",
                      launch_ms=sw["device_ms"] / sw["launches"], share_of_step=sw["device_ms"] / ms,
                      note="working set 4 MB: L2- or shared-memory-resident, so HBM is not what limits it")
     eps = out["eps"]
     return {"metric": METRIC, "value": attempts * steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1,
             "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
             "config": {"workload": w.name, "L": w.L, "replicas": w.replicas, "sweeps": w.sweeps,
-                       "beta": f"linear {w.beta0}->{w.beta1}", "cache": "working set 4 MB, L2-resident"},
+                       "beta": f"linear {w.beta0}->{w.beta1}", "cache": "L2 flushed (256 MB written) before every timed step; the 0.5 MB of spins "
+                                "stay in L2 across the step's sweeps"},
             "roofline": roof, "gpu_launches": sum(v["launches"] for v in st.values()), "clocks": clk,
             "eps": {"min": float(min(eps)), "median": float(sorted(eps)[len(eps) // 2]),
                     "max": float(max(eps))}}
@@ -517,7 +582,7 @@ def main():
             sv = res["served"]
             line = {"metric": "served TTe at eps <= 1% (p50)", "value": sv["tte_s"]["p50"], "unit": "s",
                     "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak",
-                    "vs_baseline": None, "dtype": "int8", "data": "synthetic",
+                    "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                     "config": {"workload": wl.SERVING.name, "rate_per_s": wl.SERVING.rate_per_s,
                                "window_s": args.serve_seconds},
                     "serving": res}
@@ -538,17 +603,21 @@ def main():
     def step():
         return sg.pt_run_batch(insts, params)
 
+    clocks = ClockSampler(local)
+    clocks.start()
+    flush = _l2_flusher(torch)
     for _ in range(args.warmup):
+        flush()
         out = step()
     sg.stats_read(reset=True)
     sg.stats_enable(True)
-    clocks = ClockSampler(local)
-    clocks.start()
     barrier()
     torch.cuda.synchronize()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark()
     ev0.record(stream)
     for _ in range(args.steps):
+        flush()
         out = step()
     ev1.record(stream)
     torch.cuda.synchronize()
@@ -580,7 +649,7 @@ def main():
                      traffic=rec["traffic_bytes_per_launch"] if rec else None,
                      traffic_unit="DRAM bytes per launch (ncu)",
                      algorithmic_bytes_per_launch=attempts_per_launch * BYTES_PER_ATTEMPT,
-                     kernel="sweep_rows_kernel<PT>", launch_ms=1000 * per_launch_s,
+                     kernel="sweep_bits_kernel<PT>", launch_ms=1000 * per_launch_s,
                      attempts_per_launch=attempts_per_launch, share_of_step=sw["device_ms"] / ms)
 
     # end to end: host couplings in, results out, inside the timed region
@@ -622,8 +691,7 @@ def main():
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
                 "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-                "dtype": "int8", "data": "synthetic", "config": _config(),
-                "pct_hbm_roofline": (value * BYTES_PER_ATTEMPT / 1e9) / peak,
+                "dtype": "u32", "data": "synthetic", "config": _config(),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "min_eps_mean": float(np.mean(mins)),
                 "kernel_stats": st, "serving": serving}

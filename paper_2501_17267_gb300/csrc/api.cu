@@ -5,6 +5,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <functional>
 #include <map>
 #include <tuple>
 
@@ -68,8 +69,9 @@ class LaunchLog {
         timing_ = stats().timing;
     }
     ~LaunchLog() { release(); }
+    // launches: kernels the call enqueues (a graph launch enqueues many)
     template <class F>
-    int32_t run(int kind, int64_t units, cudaStream_t st, F&& launch)
+    int32_t run(int kind, int64_t units, cudaStream_t st, F&& launch, int64_t launches = 1)
     {
         cudaEvent_t a = nullptr, b = nullptr;
         if (timing_) {
@@ -87,7 +89,7 @@ class LaunchLog {
         }
         {
             std::lock_guard<std::mutex> g(stats().mu);
-            stats().totals.launches[kind] += 1;
+            stats().totals.launches[kind] += launches;
             stats().totals.units[kind] += units;
         }
         return rc;
@@ -185,6 +187,70 @@ class DevBuf {
         int32_t _rc = (expr);           \
         if (_rc != SG_OK) return _rc;   \
     } while (0)
+
+__global__ void advance_sweep_base(uint32_t* base, uint32_t by) { *base += by; }
+
+// Runs sweeps 0 .. S-1 as CUDA graphs of up to kGraphSweeps sweeps each, so that the host
+// issues one launch per chunk instead of two or three per sweep and a slow host cannot
+// leave the GPU idle between sweeps.  enqueue(cs, c) puts sweep c of a chunk on stream cs
+// with the sweep index read on the device as *base + c; every chunk ends by advancing
+// *base.  per_sweep_launches and units_per_sweep feed the launch statistics.
+constexpr int kGraphSweeps = 100;
+
+int32_t run_sweep_graphs(int S, uint32_t* base, cudaStream_t st, LaunchLog& log, int per_sweep_launches,
+                         int64_t units_per_sweep, const std::function<int32_t(cudaStream_t, int)>& enqueue)
+{
+    SG_TRY_CUDA(cudaMemsetAsync(base, 0, sizeof(uint32_t), st));
+    struct Graphs {
+        cudaStream_t cs = nullptr;
+        std::map<int, cudaGraphExec_t> ex;
+        ~Graphs()
+        {
+            for (auto& kv : ex) cudaGraphExecDestroy(kv.second);
+            if (cs) cudaStreamDestroy(cs);
+        }
+    } g;
+    SG_TRY_CUDA(cudaStreamCreateWithFlags(&g.cs, cudaStreamNonBlocking));
+    auto capture = [&](int n) -> int32_t {
+        SG_TRY_CUDA(cudaStreamBeginCapture(g.cs, cudaStreamCaptureModeThreadLocal));
+        int32_t rc = SG_OK;
+        for (int c = 0; c < n && rc == SG_OK; ++c) rc = enqueue(g.cs, c);
+        if (rc == SG_OK) {
+            advance_sweep_base<<<1, 1, 0, g.cs>>>(base, (uint32_t)n);
+            if (cudaGetLastError() != cudaSuccess) rc = SG_ECUDA;
+        }
+        cudaGraph_t gr = nullptr;
+        const cudaError_t e = cudaStreamEndCapture(g.cs, &gr);
+        cudaGraphExec_t ge = nullptr;
+        if (rc == SG_OK && (e != cudaSuccess || cudaGraphInstantiate(&ge, gr, 0) != cudaSuccess)) rc = SG_ECUDA;
+        if (gr) cudaGraphDestroy(gr);
+        if (rc != SG_OK) {
+            cudaGetLastError();
+            if (!*sg_last_error_string()) set_error("capturing a graph of %d sweeps failed", n);
+            return rc;
+        }
+        g.ex[n] = ge;
+        return SG_OK;
+    };
+    for (int done = 0; done < S;) {
+        const int n = std::min(kGraphSweeps, S - done);
+        if (!g.ex.count(n)) SG_RET(capture(n));
+        cudaGraphExec_t ge = g.ex[n];
+        SG_RET(log.run(SG_KERNEL_SWEEP, units_per_sweep * n, st, [&]() -> int32_t {
+            const cudaError_t e = cudaGraphLaunch(ge, st);
+            if (e != cudaSuccess) {
+                set_error("graph launch failed: %s", cudaGetErrorString(e));
+                return SG_ECUDA;
+            }
+            return SG_OK;
+        }, (int64_t)per_sweep_launches * n + 1));
+        done += n;
+    }
+    return SG_OK;
+}
+
+// Runs of at least this many sweeps go through graphs; shorter ones launch directly.
+constexpr int kGraphMinSweeps = 16;
 
 // Instances per launch group: the grid's y extent holds one instance per row.
 constexpr size_t kMaxGroup = 65535;
@@ -305,8 +371,9 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
 
     bool unit_j = true;  // every coupling of the group has |J| = 1
     for (int a = 0; a < I; ++a) unit_j &= insts[members[a]]->unit_couplings;
-    DevBuf d_spins, d_E, d_E64, d_thr, d_keys, d_j6, d_flag, d_stage;
+    DevBuf d_spins, d_E, d_E64, d_thr, d_keys, d_j6, d_flag, d_stage, d_base;
     SG_RET(d_spins.alloc((size_t)I * N * Wn * 4, st));
+    SG_RET(d_base.alloc(sizeof(uint32_t), st));
     SG_RET(d_E.alloc(sizeof(int32_t) * (size_t)I * Rp, st));
     SG_RET(d_E64.alloc(sizeof(unsigned long long) * (size_t)I * Rp, st));
     SG_RET(d_thr.alloc(sizeof(uint32_t) * thr.size(), st));
@@ -337,13 +404,25 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
     // SA keeps no per-sweep energies: the energy of every replica is computed once,
     // from the final spins.
     SG_RET(log.run(SG_KERNEL_INIT, cells, st, [&] { return launch_init_spins(spins, kp, I, L, Wn, R, st); }));
-    for (int s = 0; s < S; ++s)
-        for (int c = 0; c < 2; ++c)
-            SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * R, st, [&] {
-                return launch_half_sweep_sa(spins, j6p, j1p, kp, d_thr.as<uint32_t>() + (size_t)s * kThrRow,
-                                            d_E.as<int32_t>(), d_flag.as<int>() + 1, unit_j, I, L, Wn, R, (uint32_t)s, c,
-                                            st);
-            }));
+    if (S >= kGraphMinSweeps) {
+        // the kernel reads row *base + c of the whole [S][kThrRow] table
+        SG_RET(run_sweep_graphs(S, d_base.as<uint32_t>(), st, log, 2, (int64_t)I * N * R,
+                                [&](cudaStream_t cs, int c) -> int32_t {
+                                    for (int colour = 0; colour < 2; ++colour)
+                                        SG_RET(launch_sweep_rows_sa(spins, j6p, j1p, kp, d_thr.as<uint32_t>(), unit_j,
+                                                                    I, L, Wn, R, (uint32_t)c, colour, cs,
+                                                                    d_base.as<uint32_t>(), nullptr));
+                                    return SG_OK;
+                                }));
+    } else {
+        for (int s = 0; s < S; ++s)
+            for (int c = 0; c < 2; ++c)
+                SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * R, st, [&] {
+                    return launch_half_sweep_sa(spins, j6p, j1p, kp, d_thr.as<uint32_t>() + (size_t)s * kThrRow,
+                                                d_E.as<int32_t>(), d_flag.as<int>() + 1, unit_j, I, L, Wn, R,
+                                                (uint32_t)s, c, st);
+                }));
+    }
     SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * (size_t)I * Rp, st));
     SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st); }));
 
@@ -417,8 +496,9 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     bool unit_j = true;
     for (int a = 0; a < I; ++a) unit_j &= insts[members[a]]->unit_couplings;
     DevBuf d_spins, d_E, d_E64, d_thr, d_keys, d_j6, d_flag, d_stage, d_perm, d_inv, d_acc, d_min,
-        d_xtab, d_xoff, d_xlen, d_xtail, d_done;
+        d_xtab, d_xoff, d_xlen, d_xtail, d_done, d_base;
     SG_RET(d_spins.alloc((size_t)I * N * Wn * 4, st));
+    SG_RET(d_base.alloc(sizeof(uint32_t), st));
     SG_RET(d_E.alloc(sizeof(int32_t) * (size_t)I * Rp, st));
     SG_RET(d_E64.alloc(sizeof(unsigned long long) * (size_t)I * Rp, st));
     SG_RET(d_thr.alloc(sizeof(uint32_t) * thr.size(), st));
@@ -485,7 +565,23 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     xa.K = K;
     xa.sweep_base = nullptr;
     unsigned* done = d_done.as<unsigned>();
-    for (int s = 0; s < S; ++s) {
+    if (S >= kGraphMinSweeps) {
+        ExchangeArgs xg = xa;
+        xg.sweep_base = d_base.as<uint32_t>();
+        SG_RET(run_sweep_graphs(S, d_base.as<uint32_t>(), st, log, 2, (int64_t)I * N * K,
+                                [&](cudaStream_t cs, int c) -> int32_t {
+                                    bool fused = false;
+                                    for (int colour = 0; colour < 2; ++colour)
+                                        SG_RET(launch_sweep_rows_pt(spins, j6p, j1p, kp, d_thr.as<uint32_t>(), perm, E,
+                                                                    unit_j, I, L, Wn, K, (uint32_t)c, colour,
+                                                                    colour == 1 ? &xg : nullptr, done,
+                                                                    colour == 1 ? &fused : nullptr, cs,
+                                                                    d_base.as<uint32_t>(), nullptr));
+                                    if (!fused) SG_RET(launch_pt_exchange(xg, I, (uint32_t)c, cs));
+                                    return SG_OK;
+                                }));
+    }
+    for (int s = 0; s < (S >= kGraphMinSweeps ? 0 : S); ++s) {
         bool fused = false;
         for (int c = 0; c < 2; ++c)
             SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * K, st, [&] {

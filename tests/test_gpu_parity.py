@@ -199,6 +199,17 @@ def test_pt_several_words(sg, L, K, S):
     _pt_compare(sg, inst, J3, egs, K, S, 0.2, 3.0, seed=13, iid=1)
 
 
+def test_runs_longer_than_one_graph_chunk(sg):
+    """Runs of 16 or more sweeps go through CUDA graphs of up to 100 sweeps with the
+    sweep index on the device: 230 and 251 sweeps end in a shorter last chunk."""
+    inst = sg.Instance.create(4, 7600)
+    J3, _, egs = inst.get()
+    _pt_compare(sg, inst, J3, egs, 8, 230, 0.2, 3.0, seed=17, iid=5)
+    inst6 = sg.Instance.create(6, 7601)
+    J3b, _, egsb = inst6.get()
+    _sa_compare(sg, inst6, J3b, egsb, 40, 251, 0.1, 3.0, geometric=True, seed=19, iid=2)
+
+
 def test_pt_general_couplings(sg):
     """Couplings with |J| = 2 and zeros take the replica-by-replica path, energies included."""
     L = 6
@@ -261,12 +272,12 @@ def test_batch_autotuner_records_and_reuses_choice(sg, monkeypatch, tmp_path):
     cache = tmp_path / "tune.json"
     monkeypatch.setenv("SG_AUTOTUNE_CACHE", str(cache))
     insts = [sg.Instance.create(L, 500 + L) for L in (8, 12, 16)]
-    params = [dict(replicas=32, sweeps=10, beta0=0.1, beta1=3.0, schedule="linear", seed=1,
-                   instance_id=k) for k in range(3)]
+    params = [dict(replicas=128, sweeps=10, beta0=0.1, beta1=3.0, schedule="linear", seed=1,
+                   instance_id=k) for k in range(3)]  # four words: plane widths 4, 2, 1
     first = sg.sa_run_batch(insts, params, spins="host")
     assert cache.exists()
     text = cache.read_text()
-    assert "8x32x10x1" in text and "16x32x10x1" in text
+    assert "8x128x10x1" in text and "16x128x10x1" in text
     second = sg.sa_run_batch(insts, params, spins="host")
     assert cache.read_text() == text
     for a, b in zip(first, second):
@@ -276,9 +287,9 @@ def test_batch_autotuner_records_and_reuses_choice(sg, monkeypatch, tmp_path):
 @pytest.mark.parametrize("wg,graph", [("1", "1"), ("2", "0"), ("4", "1")])
 def test_uneven_batch_any_plane_width(sg, monkeypatch, wg, graph):
     """Every words-per-plane choice and graph capture on or off give the same bytes
-    (R is a multiple of 16 so all widths apply)."""
+    (R = 100 spans four words, the last one ragged, so all widths apply)."""
     insts = [sg.Instance.create(L, 77 + L) for L in (4, 8, 6)]
-    params = [dict(replicas=16, sweeps=S, beta0=0.2, beta1=2.5, schedule="linear", seed=3,
+    params = [dict(replicas=100, sweeps=S, beta0=0.2, beta1=2.5, schedule="linear", seed=3,
                    instance_id=k) for k, S in enumerate((20, 9, 14))]
     monkeypatch.setenv("SG_BATCH_PLANES", "0")
     ref = sg.sa_run_batch(insts, params, spins="host")

@@ -58,10 +58,11 @@ def test_noalloc_energy_matches_allocating_entry_point(env):
 
 def test_noalloc_energy_rejects_oversized_requests(env):
     sg, torch = env
-    L = 64
+    # L = 64 with 512 configurations: 9 L^3 + 16 words of 4 L^3 bytes, about 19 MB
+    L, n = 64, 512
     J3_dev = torch.zeros((L ** 3, 3), dtype=torch.int8, device="cuda")
-    spins = torch.ones((64, L ** 3), dtype=torch.int8, device="cuda")
-    E_dev = torch.zeros(64, dtype=torch.int64, device="cuda")
+    spins = torch.ones((n, L ** 3), dtype=torch.int8, device="cuda")
+    E_dev = torch.zeros(n, dtype=torch.int64, device="cuda")
     with pytest.raises(sg.SGError) as e:
         sg.energy_noalloc(L, J3_dev, spins, E_dev)
     assert e.value.code == sg.SG_EINVAL
