@@ -33,6 +33,15 @@
 namespace sg {
 namespace {
 
+// Resident 256-thread blocks per SM the register allocation is sized for.  Two (up to
+// 128 registers) measured faster than three (80 registers) for the PT colour-0 launch,
+// where three fit without spills: the extra warps do not make up for the lost overlap.
+#ifndef SG_SWEEP_MINB
+#define SG_SWEEP_MINB 2
+#endif
+#ifndef SG_SWEEP_MINB_E
+#define SG_SWEEP_MINB_E 2
+#endif
 constexpr int kThrStride = 17;  // per-slot threshold row stride in shared memory (bank spread)
 constexpr int kTieCap = 16;     // queued tie entries per warp
 constexpr int kVBits = 10;      // planes of the per-thread energy counters
@@ -61,11 +70,16 @@ __device__ __forceinline__ uint32_t valid_bits(int Rvalid, int w)
     return left >= 32 ? 0xFFFFFFFFu : left <= 0 ? 0u : (1u << left) - 1u;
 }
 
-template <bool PT, bool UNITJ, bool XCH>
-__global__ void __launch_bounds__(256, 2) sweep_bits_kernel(const SweepArgs a)
+// ENERGY: a PT colour-1 launch (sums the energies); XCH: it also performs the exchange.
+// PIPE: unit couplings with one (site, word) item per thread and row; the next row's
+// words are loaded while the current row is updated.  That is safe: a half sweep reads
+// only words of the other colour, which no thread writes during the launch, and its own
+// word, which only this thread writes.
+template <bool PT, bool UNITJ, bool ENERGY, bool XCH, bool PIPE>
+__global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_MINB_E) sweep_bits_kernel(const SweepArgs a)
 {
     __shared__ uint32_t s_thr[PT ? 256 * kThrStride : kThrRow];
-    __shared__ uint32_t s_tp[(PT ? 8 : 1) * 24];  // threshold planes per word (unit couplings)
+    __shared__ __align__(16) uint32_t s_tp[(PT ? 8 : 1) * 24];  // threshold planes per word (unit couplings)
     __shared__ int s_E[PT ? 256 : 1];
     __shared__ uint4 s_ties[8 * kTieCap * 2];      // per warp: {site, storage, word, tie}, {c0, c1, -, -}
     __shared__ int s_tie_n[8];
@@ -78,9 +92,10 @@ __global__ void __launch_bounds__(256, 2) sweep_bits_kernel(const SweepArgs a)
     const RunKeys key = a.keys[inst];
     const uint32_t sweep = a.sweep + (a.sweep_base ? *a.sweep_base : 0u);
     uint32_t* __restrict__ s = a.spins + (size_t)inst * (size_t)LL * L * Wn;
+    const uint8_t* __restrict__ j1 = UNITJ ? a.j1_ptrs[inst] : nullptr;
     const int nthreads = blockDim.x * blockDim.y;
     const int tid = threadIdx.y * blockDim.x + threadIdx.x;
-    const bool energy = PT && a.colour == 1;
+    constexpr bool energy = ENERGY;
 
     if (PT) {
         for (int q = tid; q < Rp * kThrRow; q += nthreads) {
@@ -115,11 +130,15 @@ __global__ void __launch_bounds__(256, 2) sweep_bits_kernel(const SweepArgs a)
     const int g = threadIdx.x % G;
     const int j0 = threadIdx.x / G;
     const int JX = blockDim.x / G;
-    uint32_t tp[24];
-    if (UNITJ) {
+    // the 24 threshold planes of word w, read from shared memory where they are used
+    auto load_tp = [&](int w, uint32_t (&tp)[24]) {
+        const uint4* v = reinterpret_cast<const uint4*>(s_tp + (PT ? w : 0) * 24);
 #pragma unroll
-        for (int m = 0; m < 24; ++m) tp[m] = s_tp[(PT ? g : 0) * 24 + m];
-    }
+        for (int q = 0; q < 6; ++q) {
+            const uint4 x = v[q];
+            tp[4 * q] = x.x, tp[4 * q + 1] = x.y, tp[4 * q + 2] = x.z, tp[4 * q + 3] = x.w;
+        }
+    };
 
     // ---- deferred ties of this thread's warp ----
     const int warp = tid >> 5, lane = tid & 31;
@@ -180,55 +199,112 @@ __global__ void __launch_bounds__(256, 2) sweep_bits_kernel(const SweepArgs a)
         nitems = 0;
     };
 
+    // one word of one site with unit couplings: update, store, queue ties, count energy
+    auto update_unit = [&](int i, int is, int w, uint32_t self, const uint32_t (&n)[6], uint32_t sbits) {
+        uint32_t S[6];
+        mp::unit_signs(sbits, S);
+        const uint32_t valid = valid_bits(a.Rvalid, w);
+        uint32_t A[8];
+        mp::lead_planes((uint32_t)i, sweep, (uint32_t)w, key, A);
+        uint32_t tp[24];
+        load_tp(w, tp);
+        uint32_t flip, tie, c0, c1, c2;
+        mp::update_word_unit(self, n, S, valid, tp, A, &flip, &tie, &c0, &c1, &c2);
+        if (tie) flip |= queue_tie((uint32_t)i, (uint32_t)is, (uint32_t)w, tie, c0, c1);
+        if (energy) {
+            mp::count_after_flip(flip, c0, c1, c2);
+            mp::vadd3(V, c0, c1, c2);
+            if (++nitems == kVItems) fold_thread();
+        }
+        if (flip) s[(size_t)is * Wn + w] = self ^ flip;
+    };
+
     // a warp stays converged through a row when it lies in one row of threads, every
     // thread of it has the same number of sites in the row, and of words per site
     const bool uniform_rows = blockDim.x % 32 == 0 && H % JX == 0 && Wn % G == 0;
 
-    for (int c = 0; c < a.rows_per_thread; ++c) {
-        const int row = (c * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y;
-        if (row >= LL) break;
-        const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
-        const int y = row - z * L;
-        const int par = (y + z + a.colour) & 1;
-        const int dyp = (y + 1 == L ? 1 - L : 1) * L, dym = (y == 0 ? L - 1 : -1) * L;
-        const int dzp = (z + 1 == L ? 1 - L : 1) * LL, dzm = (z == 0 ? L - 1 : -1) * LL;
-        const int rowoff = row * L;
-        for (int j = j0; j < H; j += JX) {
-            const int i = rowoff + 2 * j + par;   // logical site (counters, couplings)
-            const int is = rowoff + par * H + j;  // storage position
+    if constexpr (PIPE) {
+        // one item per row: site j0 (JX == H) and word g (G == Wn) of rows c = 0, 1, ...
+        const int j = j0, w = g;
+        struct Item {
+            int i, is;
+            uint32_t self, n[6], sbits;
+        };
+        auto fetch = [&](int row, Item& it) {
+            const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
+            const int y = row - z * L;
+            const int par = (y + z + a.colour) & 1;
+            const int dyp = (y + 1 == L ? 1 - L : 1) * L, dym = (y == 0 ? L - 1 : -1) * L;
+            const int dzp = (z + 1 == L ? 1 - L : 1) * LL, dzm = (z == 0 ? L - 1 : -1) * LL;
+            const int rowoff = row * L;
+            it.i = rowoff + 2 * j + par;
+            it.is = rowoff + par * H + j;
             const int ho = rowoff + (1 - par) * H;
             const int jp = j + par == H ? 0 : j + par, jm = j + par == 0 ? H - 1 : j + par - 1;
-            const int nb[6] = {ho + jp, ho + jm, is + dyp, is + dym, is + dzp, is + dzm};
-            uint32_t S[6];
-            int J[6];
-            if (UNITJ) {
-                mp::unit_signs(a.j1_ptrs[inst][i], S);
-            } else {
-                const uint2 r = a.j6_ptrs[inst][i];
+            const int nb[6] = {ho + jp, ho + jm, it.is + dyp, it.is + dym, it.is + dzp, it.is + dzm};
+            it.sbits = j1[it.i];
+            it.self = s[(size_t)it.is * Wn + w];
 #pragma unroll
-                for (int q = 0; q < 6; ++q) J[q] = (int)(int8_t)(((q < 4 ? r.x : r.y) >> (8 * (q & 3))) & 0xFFu);
+            for (int q = 0; q < 6; ++q) it.n[q] = s[(size_t)nb[q] * Wn + w];
+        };
+        const int rstride = gridDim.x * blockDim.y;
+        int row = blockIdx.x * blockDim.y + threadIdx.y;
+        Item cur;
+        if (a.rows_per_thread > 0 && row < LL) fetch(row, cur);
+        for (int c = 0; c < a.rows_per_thread && row < LL; ++c) {
+            const int nrow = row + rstride;
+            const bool more = c + 1 < a.rows_per_thread && nrow < LL;
+            Item nxt;
+            if (more) fetch(nrow, nxt);
+            update_unit(cur.i, cur.is, w, cur.self, cur.n, cur.sbits);
+            if (uniform_rows) {
+                __syncwarp(wm);
+                if (s_tie_n[warp] >= kTieCap / 2) resolve_list();
             }
-            for (int w = g; w < Wn; w += G) {
-                const uint32_t self = s[(size_t)is * Wn + w];
-                uint32_t n[6];
-#pragma unroll
-                for (int q = 0; q < 6; ++q) n[q] = s[(size_t)nb[q] * Wn + w];
-                const uint32_t valid = valid_bits(a.Rvalid, w);
-                uint32_t A[8];
-                mp::lead_planes((uint32_t)i, sweep, (uint32_t)w, key, A);
-                uint32_t flip;
+            if (more) cur = nxt;
+            row = nrow;
+        }
+    } else {
+        for (int c = 0; c < a.rows_per_thread; ++c) {
+            const int row = (c * gridDim.x + blockIdx.x) * blockDim.y + threadIdx.y;
+            if (row >= LL) break;
+            const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
+            const int y = row - z * L;
+            const int par = (y + z + a.colour) & 1;
+            const int dyp = (y + 1 == L ? 1 - L : 1) * L, dym = (y == 0 ? L - 1 : -1) * L;
+            const int dzp = (z + 1 == L ? 1 - L : 1) * LL, dzm = (z == 0 ? L - 1 : -1) * LL;
+            const int rowoff = row * L;
+            for (int j = j0; j < H; j += JX) {
+                const int i = rowoff + 2 * j + par;   // logical site (counters, couplings)
+                const int is = rowoff + par * H + j;  // storage position
+                const int ho = rowoff + (1 - par) * H;
+                const int jp = j + par == H ? 0 : j + par, jm = j + par == 0 ? H - 1 : j + par - 1;
+                const int nb[6] = {ho + jp, ho + jm, is + dyp, is + dym, is + dzp, is + dzm};
+                uint32_t sbits = 0;
+                int J[6];
                 if (UNITJ) {
-                    uint32_t tie, c0, c1, c2;
-                    mp::update_word_unit(self, n, S, valid, tp, A, &flip, &tie, &c0, &c1, &c2);
-                    if (tie) flip |= queue_tie((uint32_t)i, (uint32_t)is, (uint32_t)w, tie, c0, c1);
-                    if (energy) {
-                        mp::count_after_flip(flip, c0, c1, c2);
-                        mp::vadd3(V, c0, c1, c2);
-                        if (++nitems == kVItems) fold_thread();
-                    }
+                    sbits = j1[i];
                 } else {
-                    flip = mp::update_word_general(self, n, J, valid, thr_row((uint32_t)w), PT ? kThrStride : 0, A,
-                                                   (uint32_t)i, sweep, (uint32_t)w, key);
+                    const uint2 r = a.j6_ptrs[inst][i];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q)
+                        J[q] = (int)(int8_t)(((q < 4 ? r.x : r.y) >> (8 * (q & 3))) & 0xFFu);
+                }
+                for (int w = g; w < Wn; w += G) {
+                    const uint32_t self = s[(size_t)is * Wn + w];
+                    uint32_t n[6];
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) n[q] = s[(size_t)nb[q] * Wn + w];
+                    if (UNITJ) {
+                        update_unit(i, is, w, self, n, sbits);
+                        continue;
+                    }
+                    const uint32_t valid = valid_bits(a.Rvalid, w);
+                    uint32_t A[8];
+                    mp::lead_planes((uint32_t)i, sweep, (uint32_t)w, key, A);
+                    const uint32_t flip = mp::update_word_general(self, n, J, valid, thr_row((uint32_t)w),
+                                                                  PT ? kThrStride : 0, A, (uint32_t)i, sweep,
+                                                                  (uint32_t)w, key);
                     if (energy) {  // slow path: each replica's s_i sum_q J_q s_q after the update
                         const uint32_t after = self ^ flip;
                         for (int b = 0; b < 32; ++b) {
@@ -239,13 +315,13 @@ __global__ void __launch_bounds__(256, 2) sweep_bits_kernel(const SweepArgs a)
                             if (e) atomicAdd(&s_E[32 * w + b], e);
                         }
                     }
+                    if (flip) s[(size_t)is * Wn + w] = self ^ flip;
                 }
-                if (flip) s[(size_t)is * Wn + w] = self ^ flip;
             }
-        }
-        if (uniform_rows) {
-            __syncwarp(wm);
-            if (s_tie_n[warp] >= kTieCap / 2) resolve_list();
+            if (uniform_rows) {
+                __syncwarp(wm);
+                if (s_tie_n[warp] >= kTieCap / 2) resolve_list();
+            }
         }
     }
     resolve_list();
@@ -298,7 +374,7 @@ struct SweepShape {
     int G, rows_per_thread;
 };
 
-SweepShape sweep_shape(int I, int L, int Wn)
+SweepShape sweep_shape(int I, int L, int Wn, int bps)
 {
     SweepShape sh;
     sh.G = Wn < 256 ? Wn : 256;
@@ -314,10 +390,9 @@ SweepShape sweep_shape(int I, int L, int Wn)
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    // rows per thread: enough blocks for about two per SM, so that each block fills its
-    // threshold tables and reduces its energies once for many rows
-    const long long bps = 2;
-    long long rpt = ((long long)LL * I + (long long)TY * bps * sms - 1) / ((long long)TY * bps * sms);
+    // rows per thread: about bps blocks per SM (as many as are resident), so that each
+    // block fills its threshold tables and reduces its energies once for many rows
+    long long rpt = ((long long)LL * I + (long long)TY * bps * sms - 1) / ((long long)TY * (long long)bps * sms);
     if (rpt < 1) rpt = 1;
     const char* e = getenv("SG_ROWS_RPT");  // tuning knob: rows per thread
     if (e && atoi(e) >= 1) rpt = atoi(e);
@@ -330,18 +405,27 @@ SweepShape sweep_shape(int I, int L, int Wn)
 template <bool PT>
 int32_t launch_rows(SweepArgs a, int I, bool unit_j, bool xch, bool* fused, cudaStream_t st)
 {
-    const SweepShape sh = sweep_shape(I, a.L, a.Wn);
+    const bool energy = PT && a.colour == 1;
+    const SweepShape sh = sweep_shape(I, a.L, a.Wn, PT && !energy ? SG_SWEEP_MINB : SG_SWEEP_MINB_E);
     a.G = sh.G;
     a.rows_per_thread = sh.rows_per_thread;
     a.Lmagic = (uint32_t)((0x100000000ull + (uint64_t)a.L - 1) / (uint64_t)a.L);
-    if (PT && xch) {
-        if (unit_j) sweep_bits_kernel<PT, true, true><<<sh.grid, sh.block, 0, st>>>(a);
-        else sweep_bits_kernel<PT, false, true><<<sh.grid, sh.block, 0, st>>>(a);
+    // one (site, word) item per thread and row: the whole colour half row of all words
+    const bool pipe = unit_j && sh.G == a.Wn && (int)sh.block.x == sh.G * (a.L / 2);
+    if (!unit_j) {
+        if (!energy) sweep_bits_kernel<PT, false, false, false, false><<<sh.grid, sh.block, 0, st>>>(a);
+        else if (xch) sweep_bits_kernel<PT, false, PT, PT, false><<<sh.grid, sh.block, 0, st>>>(a);
+        else sweep_bits_kernel<PT, false, PT, false, false><<<sh.grid, sh.block, 0, st>>>(a);
+    } else if (pipe) {
+        if (!energy) sweep_bits_kernel<PT, true, false, false, true><<<sh.grid, sh.block, 0, st>>>(a);
+        else if (xch) sweep_bits_kernel<PT, true, PT, PT, true><<<sh.grid, sh.block, 0, st>>>(a);
+        else sweep_bits_kernel<PT, true, PT, false, true><<<sh.grid, sh.block, 0, st>>>(a);
     } else {
-        if (unit_j) sweep_bits_kernel<PT, true, false><<<sh.grid, sh.block, 0, st>>>(a);
-        else sweep_bits_kernel<PT, false, false><<<sh.grid, sh.block, 0, st>>>(a);
+        if (!energy) sweep_bits_kernel<PT, true, false, false, false><<<sh.grid, sh.block, 0, st>>>(a);
+        else if (xch) sweep_bits_kernel<PT, true, PT, PT, false><<<sh.grid, sh.block, 0, st>>>(a);
+        else sweep_bits_kernel<PT, true, PT, false, false><<<sh.grid, sh.block, 0, st>>>(a);
     }
-    if (fused) *fused = PT && xch;
+    if (fused) *fused = energy && xch;
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("sweep launch failed: %s", cudaGetErrorString(e));

@@ -199,6 +199,14 @@ def test_pt_several_words(sg, L, K, S):
     _pt_compare(sg, inst, J3, egs, K, S, 0.2, 3.0, seed=13, iid=1)
 
 
+def test_sa_rows_wider_than_a_block(sg):
+    """L = 58 with 288 replicas: a colour half row holds 29 sites x 9 words, more than
+    one 256-thread block row, so threads walk several sites per row (no prefetch)."""
+    inst = sg.Instance.create(58, 7700)
+    J3, _, egs = inst.get()
+    _sa_compare(sg, inst, J3, egs, 288, 3, 0.1, 3.0, seed=23, iid=1, reps=[0, 31, 200, 287])
+
+
 def test_runs_longer_than_one_graph_chunk(sg):
     """Runs of 16 or more sweeps go through CUDA graphs of up to 100 sweeps with the
     sweep index on the device: 230 and 251 sweeps end in a shorter last chunk."""
