@@ -103,7 +103,7 @@ def _traffic_record():
     sources are unchanged since it was taken (else None)."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", "sweep_rows_pt_L64_I16_K32.traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", "sweep_bits_pt_L64_I16_K32.traffic.json")) as f:
             rec = json.load(f)
         h = hashlib.sha256()
         for src in rec["sources"]:
@@ -448,7 +448,7 @@ def batched_line(sg, args, torch, clocks_cls, local):
 
 def sa_line(sg, args, torch, clocks_cls, local):
     """SA throughput: one L=16 instance, 1024 replicas, 1000 sweeps, beta linear 0.1 -> 3.0;
-    a step is one sg_sa_run.  The spins (4 MB) stay in L2: the integer roof binds."""
+    a step is one sg_sa_run (32 words of 32 replicas per site: the row kernel, graph-captured)."""
     w = wl.SA_L16
     inst = sg.Instance.create(w.L, w.instance_seed(0), w.class_prob, True)
     attempts = w.L ** 3 * w.replicas * w.sweeps
@@ -484,7 +484,7 @@ def sa_line(sg, args, torch, clocks_cls, local):
                      peak_kind, traffic=None,
                      kernel="sa_planes_kernel" if sw["launches"] <= 4 * steps else "sweep_bits_kernel<SA>",
                      launch_ms=sw["device_ms"] / sw["launches"], share_of_step=sw["device_ms"] / ms,
-                     note="working set 4 MB: L2- or shared-memory-resident, so HBM is not what limits it")
+                     note="working set 0.5 MB of spin words: L2-resident, so HBM is not what limits it")
     eps = out["eps"]
     return {"metric": METRIC, "value": attempts * steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1,
             "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / steps,

@@ -14,16 +14,17 @@
  * The RNG is Philox4x32-10 (Salmon, Moraes, Dror, Shaw, "Parallel random numbers:
  * as easy as 1, 2, 3", SC'11), written here from that published description.
  *
- * Everything is deliberately slow: one Philox call per spin-flip attempt, one
- * site at a time, no blocking or vectorisation.
+ * Everything is deliberately slow: nine Philox blocks per spin-flip attempt (eight
+ * for the bit planes of the draw's leading byte, one for its low bits), one site at a
+ * time, no blocking or vectorisation.
  *
- * Readings of points the paper leaves open are listed in the design doc; the ones
- * that shape this file are: the three tile classes are fixed by their sets of
+ * Readings of points the paper leaves open that shape this file: the three tile
+ * classes are fixed by their sets of
  * frustrated faces (F22: two adjacent faces, F42: four faces with the two
  * unfrustrated ones opposite, F6: all six); the sum in Eq. 1 runs once over each
  * lattice edge; sites are swept in checkerboard order (colour 0, then colour 1);
  * the Metropolis draw is accepted when u < floor(2^32 exp(-beta dE)), with the
- * 32-bit uniform u of an attempt assembled from two Philox blocks (metropolis_uniform).
+ * 32-bit uniform u of an attempt assembled from Philox words (metropolis_uniform).
  */
 #include "oracle.h"
 

@@ -693,16 +693,22 @@ extern "C" int32_t sg_sa_run_batch(const sg_instance* const* insts, const sg_sa_
     }
     // A batch of uneven shapes runs in one persistent launch (batch.cu), and so does a
     // batch of small lattices whose half sweeps are too short to pay for a launch each
-    // (every plane then lives in shared memory for the whole run); other batches of one
-    // shape use the sweep kernels that spread each instance over many blocks.  Knob
-    // SG_BATCH_PLANES = 1 / 0 forces one or the other.
+    // (every plane then lives in shared memory for the whole run) -- provided it has
+    // enough words of 32 replicas to give every SM two planes, since a plane is one
+    // block's work.  Other batches of one shape use the sweep kernel that spreads each
+    // instance over many blocks.  Knob SG_BATCH_PLANES = 1 / 0 forces one or the other.
     bool small = n > 0;
     int64_t half_sweep = 0;  // attempts per half sweep of the whole batch
+    int64_t words = 0;       // planes of one word
     for (int a = 0; a < n; ++a) {
         small &= planes_smem_bytes(1, insts[a]->L) > 0;
         half_sweep += insts[a]->N / 2 * (int64_t)ps[a].replicas;
+        words += words_for(ps[a].replicas);
     }
-    small &= half_sweep <= (int64_t)1 << 24;
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    small &= half_sweep <= (int64_t)1 << 24 && words >= 2 * (int64_t)sms;
     const char* knob = getenv("SG_BATCH_PLANES");
     const bool planes = knob ? atoi(knob) == 1 : (groups.size() > 1 || small);
     if (planes && n > 0) {
