@@ -79,7 +79,7 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
     extern __shared__ __align__(16) uint32_t s_plane[];
     __shared__ int s_item;
     __shared__ uint32_t s_thr[kThrRow];
-    __shared__ uint4 s_ties[8 * kTieCap * 2];  // per warp: {site, storage, word, tie}, {c0, c1, -, -}
+    __shared__ uint4 s_ties[8 * kTieCap * 2];  // per warp: {site, storage, word index, tie}, {c0, c1, stored word, -}
     __shared__ int s_tie_n[8];
     const int tid = threadIdx.x, nthreads = blockDim.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -124,7 +124,8 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
                     const uint4 t = ties[2 * e], u = ties[2 * e + 1];
                     const uint32_t acc =
                         mp::resolve_tie_bits(t.w, u.x, u.y, s_thr, 0, t.x, (uint32_t)sw, t.z, key.k0, key.k1);
-                    if (acc) sp[(size_t)t.y * WG + (t.z - (uint32_t)p.w0)] ^= acc;
+                    // the word's owner stored u.z; nobody else writes it: no read back
+                    if (acc) sp[(size_t)t.y * WG + (t.z - (uint32_t)p.w0)] = u.z ^ acc;
                 }
                 __syncwarp();
                 if (lane == 0) s_tie_n[warp] = 0;
@@ -192,7 +193,7 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
                                     const int pos = atomicAdd(&s_tie_n[warp], 1);
                                     if (pos < kTieCap) {
                                         ties[2 * pos] = make_uint4((uint32_t)i_[u], (uint32_t)is_[u], w, tie);
-                                        ties[2 * pos + 1] = make_uint4(c0, c1, 0u, 0u);
+                                        ties[2 * pos + 1] = make_uint4(c0, c1, self[u][wi] ^ flip, 0u);
                                     } else {  // list full: decide here
                                         flip |= mp::resolve_tie_bits(tie, c0, c1, s_thr, 0, (uint32_t)i_[u],
                                                                      (uint32_t)sw, w, key.k0, key.k1);

@@ -14,8 +14,9 @@
 // of its leading byte A is bit b of word j % 4 of Philox(site, sweep, 2w + j / 4, 0) --
 // two blocks give the eight bit planes of all 32 leading bytes -- and B is the top 24 bits
 // of word (32w + b) % 4 of Philox(site, sweep, (32w + b) / 4, 4).  U < thr[k] is decided
-// by comparing A with the leading byte of thr[k], plane by plane from the top, for all 32
-// replicas at once; only when the two bytes are equal (probability 1/256) is B drawn.
+// by comparing A with the leading byte of thr[k] through a bit-sliced borrow chain, for
+// all 32 replicas at once; only when the two bytes are equal (probability 1/256) is B
+// drawn.
 #pragma once
 #include <stdint.h>
 
@@ -81,12 +82,14 @@ __device__ __forceinline__ void update_word_unit(uint32_t self, const uint32_t (
     satisfied_count(self, n, S, *c0, *c1, *c2);
     const uint32_t need = *c2 & valid;   // c >= 4: the flip raises the energy
     const uint32_t free = ~*c2 & valid;  // c <= 3: it does not
+    // A < T through the borrow of A - T, least significant plane first: the borrow out
+    // of a plane is the majority of (~A_j, T_j, borrow in), one three-input operation
     uint32_t lt = 0, eq = 0xFFFFFFFFu;
 #pragma unroll
-    for (int j = 7; j >= 0; --j) {
+    for (int j = 0; j < 8; ++j) {
         // threshold plane of each replica's k: c = 4 -> k = 2, c = 5 -> 4, c = 6 -> 6
         const uint32_t T = (*c1 & tp[16 + j]) | (~*c1 & ((*c0 & tp[8 + j]) | (~*c0 & tp[j])));
-        lt |= eq & ~A[j] & T;
+        lt = maj3(~A[j], T, lt);
         eq &= ~(A[j] ^ T);
     }
     *flip = free | (need & lt);

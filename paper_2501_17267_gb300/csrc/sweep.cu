@@ -43,7 +43,7 @@ namespace {
 #define SG_SWEEP_MINB_E 2
 #endif
 constexpr int kThrStride = 17;  // per-slot threshold row stride in shared memory (bank spread)
-constexpr int kTieCap = 16;     // queued tie entries per warp
+constexpr int kTieCap = 64;     // queued tie entries per warp (decided once half full)
 constexpr int kVBits = 10;      // planes of the per-thread energy counters
 constexpr int kVItems = ((1 << kVBits) - 1) / 6;  // items a counter holds before a fold
 
@@ -81,7 +81,7 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
     __shared__ uint32_t s_thr[PT ? 256 * kThrStride : kThrRow];
     __shared__ __align__(16) uint32_t s_tp[(PT ? 8 : 1) * 24];  // threshold planes per word (unit couplings)
     __shared__ int s_E[PT ? 256 : 1];
-    __shared__ uint4 s_ties[8 * kTieCap * 2];      // per warp: {site, storage, word, tie}, {c0, c1, -, -}
+    __shared__ uint4 s_ties[8 * kTieCap * 2];      // per warp: {site, storage, word index, tie}, {c0, c1, stored word, -}
     __shared__ int s_tie_n[8];
 
     const int inst = blockIdx.y;
@@ -147,10 +147,12 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
     uint4* ties = s_ties + warp * kTieCap * 2;
     auto thr_row = [&](uint32_t w) -> const uint32_t* { return PT ? s_thr + 32 * w * kThrStride : s_thr; };
     // applies the decided ties of one word (and, in a colour-1 PT launch, their energy
-    // change 2k to the slots' sums)
-    auto apply_ties = [&](uint32_t is, uint32_t w, uint32_t acc, uint32_t c0, uint32_t c1) {
+    // change 2k to the slots' sums).  `word` is the value the word's owner stored after
+    // its other flips; a word has at most one entry and nobody else writes it, so the
+    // result is stored without reading the word back.
+    auto apply_ties = [&](uint32_t is, uint32_t w, uint32_t acc, uint32_t c0, uint32_t c1, uint32_t word) {
         if (!acc) return;
-        s[(size_t)is * Wn + w] ^= acc;
+        s[(size_t)is * Wn + w] = word ^ acc;
         if (energy)
             for (uint32_t m = acc; m; m &= m - 1u) {
                 const int b = __ffs(m) - 1;
@@ -166,19 +168,20 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
             const uint4 t = ties[2 * e], u = ties[2 * e + 1];
             const uint32_t acc = mp::resolve_tie_bits(t.w, u.x, u.y, thr_row(t.z), PT ? kThrStride : 0, t.x, sweep,
                                                       t.z, key.k0, key.k1);
-            apply_ties(t.y, t.z, acc, u.x, u.y);
+            apply_ties(t.y, t.z, acc, u.x, u.y, u.z);
         }
         __syncwarp(wm);
         if (rank == 0) s_tie_n[warp] = 0;
         __syncwarp(wm);
     };
-    // queues the ties of one word; when the list is full they are decided here instead and
-    // the accepted ones returned, to join the word's flips
-    auto queue_tie = [&](uint32_t i, uint32_t is, uint32_t w, uint32_t tie, uint32_t c0, uint32_t c1) -> uint32_t {
+    // queues the ties of one word whose owner stores `word`; when the list is full they
+    // are decided here instead and the accepted ones returned, to join the word's flips
+    auto queue_tie = [&](uint32_t i, uint32_t is, uint32_t w, uint32_t tie, uint32_t c0, uint32_t c1,
+                         uint32_t word) -> uint32_t {
         const int pos = atomicAdd(&s_tie_n[warp], 1);
         if (pos < kTieCap) {
             ties[2 * pos] = make_uint4(i, is, w, tie);
-            ties[2 * pos + 1] = make_uint4(c0, c1, 0u, 0u);
+            ties[2 * pos + 1] = make_uint4(c0, c1, word, 0u);
             return 0u;
         }
         return mp::resolve_tie_bits(tie, c0, c1, thr_row(w), PT ? kThrStride : 0, i, sweep, w, key.k0, key.k1);
@@ -200,23 +203,24 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
     };
 
     // one word of one site with unit couplings: update, store, queue ties, count energy
-    auto update_unit = [&](int i, int is, int w, uint32_t self, const uint32_t (&n)[6], uint32_t sbits) {
+    // A: the word's eight leading-byte draw planes
+    // wp: the word's address
+    auto update_unit = [&](int i, int is, int w, uint32_t* wp, uint32_t self, const uint32_t (&n)[6], uint32_t sbits,
+                           const uint32_t (&A)[8]) {
         uint32_t S[6];
         mp::unit_signs(sbits, S);
         const uint32_t valid = valid_bits(a.Rvalid, w);
-        uint32_t A[8];
-        mp::lead_planes((uint32_t)i, sweep, (uint32_t)w, key, A);
         uint32_t tp[24];
         load_tp(w, tp);
         uint32_t flip, tie, c0, c1, c2;
         mp::update_word_unit(self, n, S, valid, tp, A, &flip, &tie, &c0, &c1, &c2);
-        if (tie) flip |= queue_tie((uint32_t)i, (uint32_t)is, (uint32_t)w, tie, c0, c1);
+        if (tie) flip |= queue_tie((uint32_t)i, (uint32_t)is, (uint32_t)w, tie, c0, c1, self ^ flip);
         if (energy) {
             mp::count_after_flip(flip, c0, c1, c2);
             mp::vadd3(V, c0, c1, c2);
             if (++nitems == kVItems) fold_thread();
         }
-        if (flip) s[(size_t)is * Wn + w] = self ^ flip;
+        if (flip) *wp = self ^ flip;
     };
 
     // a warp stays converged through a row when it lies in one row of threads, every
@@ -225,10 +229,16 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
 
     if constexpr (PIPE) {
         // one item per row: site j0 (JX == H) and word g (G == Wn) of rows c = 0, 1, ...
+        // The next row's words are loaded and its draw planes computed while the current
+        // row is updated: the Philox chains do not depend on spins, so they interleave
+        // with the current update's adder and compare.
         const int j = j0, w = g;
+        // every word index here is below 2^31 (L/2 * Wn <= 256 and L <= 256), so offsets
+        // are 32-bit
+        uint32_t* __restrict__ sw = s + w;
         struct Item {
             int i, is;
-            uint32_t self, n[6], sbits;
+            uint32_t self, n[6], sbits, A[8];
         };
         auto fetch = [&](int row, Item& it) {
             const int z = (int)__umulhi((uint32_t)row, a.Lmagic);
@@ -243,26 +253,35 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
             const int jp = j + par == H ? 0 : j + par, jm = j + par == 0 ? H - 1 : j + par - 1;
             const int nb[6] = {ho + jp, ho + jm, it.is + dyp, it.is + dym, it.is + dzp, it.is + dzm};
             it.sbits = j1[it.i];
-            it.self = s[(size_t)it.is * Wn + w];
+            it.self = sw[(uint32_t)(it.is * Wn)];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) it.n[q] = s[(size_t)nb[q] * Wn + w];
+            for (int q = 0; q < 6; ++q) it.n[q] = sw[(uint32_t)(nb[q] * Wn)];
+            mp::lead_planes((uint32_t)it.i, sweep, (uint32_t)w, key, it.A);
         };
         const int rstride = gridDim.x * blockDim.y;
         int row = blockIdx.x * blockDim.y + threadIdx.y;
-        Item cur;
-        if (a.rows_per_thread > 0 && row < LL) fetch(row, cur);
-        for (int c = 0; c < a.rows_per_thread && row < LL; ++c) {
+        // rows c and c + 1 alternate between two buffers (unrolled by two: no copies)
+        Item b0, b1;
+        // updates the row in `cur` while fetching the next one into `nxt`; false when
+        // there is no next row
+        auto step = [&](int c, Item& cur, Item& nxt) -> bool {
             const int nrow = row + rstride;
             const bool more = c + 1 < a.rows_per_thread && nrow < LL;
-            Item nxt;
             if (more) fetch(nrow, nxt);
-            update_unit(cur.i, cur.is, w, cur.self, cur.n, cur.sbits);
+            update_unit(cur.i, cur.is, w, sw + (uint32_t)(cur.is * Wn), cur.self, cur.n, cur.sbits, cur.A);
             if (uniform_rows) {
                 __syncwarp(wm);
                 if (s_tie_n[warp] >= kTieCap / 2) resolve_list();
             }
-            if (more) cur = nxt;
             row = nrow;
+            return more;
+        };
+        if (a.rows_per_thread > 0 && row < LL) {
+            fetch(row, b0);
+            for (int c = 0;; c += 2) {
+                if (!step(c, b0, b1)) break;
+                if (!step(c + 1, b1, b0)) break;
+            }
         }
     } else {
         for (int c = 0; c < a.rows_per_thread; ++c) {
@@ -295,13 +314,13 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
                     uint32_t n[6];
 #pragma unroll
                     for (int q = 0; q < 6; ++q) n[q] = s[(size_t)nb[q] * Wn + w];
+                    uint32_t A[8];
+                    mp::lead_planes((uint32_t)i, sweep, (uint32_t)w, key, A);
                     if (UNITJ) {
-                        update_unit(i, is, w, self, n, sbits);
+                        update_unit(i, is, w, s + (size_t)is * Wn + w, self, n, sbits, A);
                         continue;
                     }
                     const uint32_t valid = valid_bits(a.Rvalid, w);
-                    uint32_t A[8];
-                    mp::lead_planes((uint32_t)i, sweep, (uint32_t)w, key, A);
                     const uint32_t flip = mp::update_word_general(self, n, J, valid, thr_row((uint32_t)w),
                                                                   PT ? kThrStride : 0, A, (uint32_t)i, sweep,
                                                                   (uint32_t)w, key);
