@@ -45,6 +45,7 @@ namespace {
 constexpr int kThrStride = 17;  // per-slot threshold row stride in shared memory (bank spread)
 constexpr int kTieCap = 64;     // queued tie entries per warp (decided once half full)
 constexpr int kVBits = 10;      // planes of the per-thread energy counters
+constexpr int kPlanes = 28;     // threshold planes kept per word
 constexpr int kVItems = ((1 << kVBits) - 1) / 6;  // items a counter holds before a fold
 
 struct SweepArgs {
@@ -79,7 +80,8 @@ template <bool PT, bool UNITJ, bool ENERGY, bool XCH, bool PIPE>
 __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_MINB_E) sweep_bits_kernel(const SweepArgs a)
 {
     __shared__ uint32_t s_thr[PT ? 256 * kThrStride : kThrRow];
-    __shared__ __align__(16) uint32_t s_tp[(PT ? 8 : 1) * 24];  // threshold planes per word (unit couplings)
+    // per word: 24 threshold-byte planes, 3 planes "threshold has low bits" (k = 2, 4, 6), 1 spare
+    __shared__ __align__(16) uint32_t s_tp[(PT ? 8 : 1) * kPlanes];
     __shared__ int s_E[PT ? 256 : 1];
     __shared__ uint4 s_ties[8 * kTieCap * 2];      // per warp: {site, storage, word index, tie}, {c0, c1, stored word, -}
     __shared__ int s_tie_n[8];
@@ -115,12 +117,16 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
     __syncthreads();
     if (UNITJ) {
         const int nw = PT ? Wn : 1;
-        for (int q = tid; q < nw * 24; q += nthreads) {
-            const int w = q / 24, m = (q % 24) / 8, j = q % 8, k = 2 + 2 * m;
+        for (int q = tid; q < nw * kPlanes; q += nthreads) {
+            const int w = q / kPlanes, p = q % kPlanes;
             uint32_t plane = 0;
-            for (int b = 0; b < 32; ++b) {
-                const uint32_t th = PT ? s_thr[(32 * w + b) * kThrStride + k] : s_thr[k];
-                plane |= mp::threshold_plane_bit(th, j) << b;
+            if (p < 27) {
+                const int m = p < 24 ? p / 8 : p - 24, k = 2 + 2 * m;
+                for (int b = 0; b < 32; ++b) {
+                    const uint32_t th = PT ? s_thr[(32 * w + b) * kThrStride + k] : s_thr[k];
+                    const uint32_t bit = p < 24 ? mp::threshold_plane_bit(th, p % 8) : (uint32_t)((th & 0xFFFFFFu) != 0u);
+                    plane |= bit << b;
+                }
             }
             s_tp[q] = plane;
         }
@@ -132,12 +138,18 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
     const int JX = blockDim.x / G;
     // the 24 threshold planes of word w, read from shared memory where they are used
     auto load_tp = [&](int w, uint32_t (&tp)[24]) {
-        const uint4* v = reinterpret_cast<const uint4*>(s_tp + (PT ? w : 0) * 24);
+        const uint4* v = reinterpret_cast<const uint4*>(s_tp + (PT ? w : 0) * kPlanes);
 #pragma unroll
         for (int q = 0; q < 6; ++q) {
             const uint4 x = v[q];
             tp[4 * q] = x.x, tp[4 * q + 1] = x.y, tp[4 * q + 2] = x.z, tp[4 * q + 3] = x.w;
         }
+    };
+    // replicas of word w whose threshold for their satisfied count (c0, c1 of c = 4, 5, 6)
+    // has nonzero low 24 bits: only those can accept on a tie of the leading bytes
+    auto tie_can_accept = [&](int w, uint32_t c0, uint32_t c1) -> uint32_t {
+        const uint4 z = reinterpret_cast<const uint4*>(s_tp + (PT ? w : 0) * kPlanes)[6];
+        return (c1 & z.z) | (~c1 & ((c0 & z.y) | (~c0 & z.x)));
     };
 
     // ---- deferred ties of this thread's warp ----
@@ -174,6 +186,9 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
         if (rank == 0) s_tie_n[warp] = 0;
         __syncwarp(wm);
     };
+    // a warp stays converged through a row when it lies in one row of threads, every
+    // thread of it has the same number of sites in the row, and of words per site
+    const bool uniform_rows = blockDim.x % 32 == 0 && H % JX == 0 && Wn % G == 0;
     // queues the ties of one word whose owner stores `word`; when the list is full they
     // are decided here instead and the accepted ones returned, to join the word's flips
     auto queue_tie = [&](uint32_t i, uint32_t is, uint32_t w, uint32_t tie, uint32_t c0, uint32_t c1,
@@ -214,6 +229,7 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
         load_tp(w, tp);
         uint32_t flip, tie, c0, c1, c2;
         mp::update_word_unit(self, n, S, valid, tp, A, &flip, &tie, &c0, &c1, &c2);
+        tie &= tie_can_accept(w, c0, c1);  // the others reject whatever the low bits
         if (tie) flip |= queue_tie((uint32_t)i, (uint32_t)is, (uint32_t)w, tie, c0, c1, self ^ flip);
         if (energy) {
             mp::count_after_flip(flip, c0, c1, c2);
@@ -222,10 +238,6 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
         }
         if (flip) *wp = self ^ flip;
     };
-
-    // a warp stays converged through a row when it lies in one row of threads, every
-    // thread of it has the same number of sites in the row, and of words per site
-    const bool uniform_rows = blockDim.x % 32 == 0 && H % JX == 0 && Wn % G == 0;
 
     if constexpr (PIPE) {
         // one item per row: site j0 (JX == H) and word g (G == Wn) of rows c = 0, 1, ...
