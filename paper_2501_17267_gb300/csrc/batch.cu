@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
                                                         unsigned* __restrict__ next)
 {
     constexpr int U = 4 / WG;
-    constexpr int kTieCap = 16;  // queued tie entries per warp
+    constexpr int kTieCap = 32;  // queued tie entries per warp (decided once half full)
     extern __shared__ __align__(16) uint32_t s_plane[];
     __shared__ int s_item;
     __shared__ uint32_t s_thr[kThrRow];
@@ -111,9 +111,12 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
             if (tid < kThrRow) s_thr[tid] = p.thr[(size_t)sw * kThrRow + tid];
             __syncthreads();
             uint32_t tp[24];  // threshold planes of the sweep (the same for every replica)
+            uint32_t lz[3];   // thresholds k = 2, 4, 6 with nonzero low bits: ties there can accept
             if (UNITJ) {
 #pragma unroll
                 for (int m = 0; m < 24; ++m) tp[m] = mp::threshold_plane_bit(s_thr[2 + 2 * (m / 8)], m % 8) ? ~0u : 0u;
+#pragma unroll
+                for (int m = 0; m < 3; ++m) lz[m] = (s_thr[2 + 2 * m] & 0xFFFFFFu) ? ~0u : 0u;
             }
             // Deferred ties of this warp, decided by all its lanes together (every lane
             // runs the same iterations of the site loop below).
@@ -189,6 +192,7 @@ __global__ void __launch_bounds__(256) sa_planes_kernel(const Plane* __restrict_
                             if (UNITJ) {
                                 uint32_t tie, c0, c1, c2;
                                 mp::update_word_unit(self[u][wi], nw, S[u], valid, tp, A, &flip, &tie, &c0, &c1, &c2);
+                                tie &= (c1 & lz[2]) | (~c1 & ((c0 & lz[1]) | (~c0 & lz[0])));  // others reject
                                 if (tie) {
                                     const int pos = atomicAdd(&s_tie_n[warp], 1);
                                     if (pos < kTieCap) {
