@@ -218,6 +218,21 @@ def test_runs_longer_than_one_graph_chunk(sg):
     _sa_compare(sg, inst6, J3b, egsb, 40, 251, 0.1, 3.0, geometric=True, seed=19, iid=2)
 
 
+@pytest.mark.parametrize("L,K,S", [(32, 64, 16), (16, 128, 20)])
+def test_pt_graph_runs_with_one_warp_per_row(sg, L, K, S):
+    """Graph-captured runs (16 or more sweeps) of shapes where a warp is exactly one row
+    of threads: two words per site at L = 32, four at L = 16."""
+    inst = sg.Instance.create(L, 7800 + L)
+    J3, _, egs = inst.get()
+    _pt_compare(sg, inst, J3, egs, K, S, 0.2, 3.0, seed=29, iid=6)
+
+
+def test_sa_graph_run_with_one_warp_per_row(sg):
+    inst = sg.Instance.create(32, 7900)
+    J3, _, egs = inst.get()
+    _sa_compare(sg, inst, J3, egs, 64, 17, 0.1, 3.0, seed=31, iid=3, reps=[0, 33, 63])
+
+
 def test_pt_general_couplings(sg):
     """Couplings with |J| = 2 and zeros take the replica-by-replica path, energies included."""
     L = 6
