@@ -448,7 +448,8 @@ def batched_line(sg, args, torch, clocks_cls, local):
 
 def sa_line(sg, args, torch, clocks_cls, local):
     """SA throughput: one L=16 instance, 1024 replicas, 1000 sweeps, beta linear 0.1 -> 3.0;
-    a step is one sg_sa_run (32 words of 32 replicas per site: the row kernel, graph-captured)."""
+    a step is one sg_sa_run: 32 words of 32 replicas per site, each word annealed by one
+    thread-block cluster for all 1000 sweeps in a single launch."""
     w = wl.SA_L16
     inst = sg.Instance.create(w.L, w.instance_seed(0), w.class_prob, True)
     attempts = w.L ** 3 * w.replicas * w.sweeps
@@ -482,7 +483,7 @@ def sa_line(sg, args, torch, clocks_cls, local):
     if sw["launches"] and sw["device_ms"] > 0:
         roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), 2.0 / 8.0 + 3.0 / w.replicas, sms, sm_mhz, peak,
                      peak_kind, traffic=None,
-                     kernel="sa_planes_kernel" if sw["launches"] <= 4 * steps else "sweep_bits_kernel<SA>",
+                     kernel="sa_cluster_kernel" if sw["launches"] <= 4 * steps else "sweep_bits_kernel<SA>",
                      launch_ms=sw["device_ms"] / sw["launches"], share_of_step=sw["device_ms"] / ms,
                      note="working set 0.5 MB of spin words: L2-resident, so HBM is not what limits it")
     eps = out["eps"]

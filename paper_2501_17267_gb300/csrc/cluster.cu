@@ -1,0 +1,282 @@
+// cluster.cu -- simulated annealing (App. D.1) of small lattices with many replicas:
+// one launch runs every sweep, each word of 32 replicas on its own thread-block cluster.
+//
+// A half sweep of a small lattice is too little work to pay for a launch, and a whole
+// lattice per block (batch.cu) leaves most SMs idle when an instance has few words.
+// Here cluster (word w, instance) of C blocks splits the lattice into C slabs of L / C
+// z-planes; block r keeps slab r of word w in its shared memory for the whole run.  The
+// sites of one colour read only sites of the other colour: x and y neighbours lie in
+// the block's own slab, z neighbours across a slab boundary in the next block's slab,
+// read through distributed shared memory.  A cluster barrier separates half sweeps.
+// Every attempt draws the same counters as the row kernel (site, sweep, word), so the
+// results are bit-identical to it and to the oracle.
+#include <cooperative_groups.h>
+#include <stdint.h>
+#include <stdlib.h>
+
+#include <algorithm>
+
+#include "metropolis.cuh"
+#include "philox.cuh"
+#include "sg_internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace sg {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kTieCap = 32;  // queued tie entries per warp
+
+struct ClusterArgs {
+    uint32_t* spins;                // [I][N][Wn] words, storage order
+    const uint8_t* const* j1_ptrs;  // per instance: [N] coupling sign bits (all |J| = 1)
+    const RunKeys* keys;            // [I]
+    const uint32_t* thr;            // [S][kThrRow]
+    int L, Wn, R, S, C;             // side, words, replicas, sweeps, blocks per cluster
+    uint32_t Hmagic;                // ceil(2^32 / (L / 2))
+};
+
+__device__ __forceinline__ uint32_t word_valid_bits(int R, int w)
+{
+    const int left = R - 32 * w;
+    return left >= 32 ? 0xFFFFFFFFu : left <= 0 ? 0u : (1u << left) - 1u;
+}
+
+__global__ void __launch_bounds__(kBlock) sa_cluster_kernel(const ClusterArgs a)
+{
+    extern __shared__ uint32_t slab[];  // [L / C][L][L] words of this block's slab, storage order
+    __shared__ uint4 s_ties[(kBlock / 32) * kTieCap * 2];  // per warp: {site, local, -, tie}, {c0, c1, word, -}
+    __shared__ int s_tie_n[kBlock / 32];
+
+    cg::cluster_group cluster = cg::this_cluster();
+    const int r = (int)cluster.block_rank();
+    const int C = a.C;
+    const int w = blockIdx.y, inst = blockIdx.z;
+    const int L = a.L, H = L >> 1, LL = L * L;
+    const int zc = L / C;              // z-planes per slab
+    const int slab_words = zc * LL;
+    const int z0 = r * zc;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const RunKeys key = a.keys[inst];
+    const uint8_t* __restrict__ j1 = a.j1_ptrs[inst];
+    uint32_t* __restrict__ g = a.spins + (size_t)inst * LL * L * a.Wn + w;  // word w of site 0
+    // slabs of the blocks above (z0 + zc) and below (z0 - 1), periodic in z
+    const uint32_t* up = cluster.map_shared_rank(slab, (r + 1) % C);
+    const uint32_t* dn = cluster.map_shared_rank(slab, (r + C - 1) % C);
+    const uint32_t valid = word_valid_bits(a.R, w);
+    uint4* ties = s_ties + warp * kTieCap * 2;
+    const int items = zc * L * H;  // sites of one colour in the slab
+
+    // geometry of slab item q (site j of slab row rl) in a half sweep of colour `colour`:
+    // its slab position, its six neighbours' (z neighbours in another block's slab when
+    // `zup` / `zdn`), its logical index and its coupling sign bits
+    struct Site {
+        int is, nb[6];
+        bool zup, zdn;
+        uint32_t i, sbits;
+    };
+    auto site_of = [&](int q, int colour) {
+        Site t;
+        const int rl = H == 1 ? q : (int)__umulhi((uint32_t)q, a.Hmagic);
+        const int j = q - rl * H;
+        const int zl = rl / L, y = rl - zl * L;
+        const int z = z0 + zl;
+        const int par = (y + z + colour) & 1;
+        const int rowoff = rl * L;
+        const int pos = par * H + j;
+        t.is = rowoff + pos;
+        const int ho = rowoff + (1 - par) * H;
+        t.nb[0] = ho + (j + par == H ? 0 : j + par);
+        t.nb[1] = ho + (j + par == 0 ? H - 1 : j + par - 1);
+        t.nb[2] = t.is + (y + 1 == L ? -(L - 1) * L : L);
+        t.nb[3] = t.is + (y == 0 ? (L - 1) * L : -L);
+        t.zup = zl + 1 >= zc;
+        t.zdn = zl == 0;
+        t.nb[4] = t.zup ? y * L + pos : t.is + LL;
+        t.nb[5] = t.zdn ? (zc - 1) * LL + y * L + pos : t.is - LL;
+        t.i = (uint32_t)((z * L + y) * L + 2 * j + par);
+        t.sbits = j1[t.i];
+        return t;
+    };
+    // this thread's first item of each colour, fixed for the run
+    Site first0, first1;
+    if (tid < items) {
+        first0 = site_of(tid, 0);
+        first1 = site_of(tid, 1);
+    }
+    // The draws of this thread's first item of a half sweep depend only on its site and
+    // the sweep, so they are computed while the cluster barrier before it completes.
+    uint32_t A0[8];
+    auto draws_ahead = [&](int sw, int colour) {
+        if (sw < a.S && tid < items) mp::lead_planes((colour ? first1 : first0).i, (uint32_t)sw, (uint32_t)w, key, A0);
+    };
+
+    for (int q = tid; q < slab_words; q += kBlock) slab[q] = g[(size_t)(z0 * LL + q) * a.Wn];
+    if (tid < kBlock / 32) s_tie_n[tid] = 0;
+    cluster.barrier_arrive();
+    draws_ahead(0, 0);
+    cluster.barrier_wait();  // every slab loaded before any block reads its neighbours'
+
+    for (int sw = 0; sw < a.S; ++sw) {
+        const uint32_t* thr = a.thr + (size_t)sw * kThrRow;  // the sweep's thresholds, k = 0 .. 15
+        uint32_t tp[24], lz[3];  // its threshold planes: the same for every replica
+        {
+            const uint32_t t2 = thr[2], t4 = thr[4], t6 = thr[6];
+#pragma unroll
+            for (int m = 0; m < 24; ++m)
+                tp[m] = mp::threshold_plane_bit(m < 8 ? t2 : m < 16 ? t4 : t6, m % 8) ? ~0u : 0u;
+            lz[0] = (t2 & 0xFFFFFFu) ? ~0u : 0u;
+            lz[1] = (t4 & 0xFFFFFFu) ? ~0u : 0u;
+            lz[2] = (t6 & 0xFFFFFFu) ? ~0u : 0u;
+        }
+        // one half sweep of colour `colour`; `fst`: this thread's first item of that colour
+        auto half = [&](const int colour, const Site& fst) {
+            for (int q = tid; q < items; q += kBlock) {
+                const Site t = q == tid ? fst : site_of(q, colour);
+                const uint32_t self = slab[t.is];
+                uint32_t n[6];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) n[k] = slab[t.nb[k]];
+                n[4] = t.zup ? up[t.nb[4]] : slab[t.nb[4]];
+                n[5] = t.zdn ? dn[t.nb[5]] : slab[t.nb[5]];
+                uint32_t S[6];
+                mp::unit_signs(t.sbits, S);
+                uint32_t A[8];
+                if (q == tid) {
+#pragma unroll
+                    for (int m = 0; m < 8; ++m) A[m] = A0[m];
+                } else {
+                    mp::lead_planes(t.i, (uint32_t)sw, (uint32_t)w, key, A);
+                }
+                uint32_t flip, tie, c0, c1, c2;
+                mp::update_word_unit(self, n, S, valid, tp, A, &flip, &tie, &c0, &c1, &c2);
+                tie &= (c1 & lz[2]) | (~c1 & ((c0 & lz[1]) | (~c0 & lz[0])));  // the others reject
+                if (tie) {
+                    const int p = atomicAdd(&s_tie_n[warp], 1);
+                    if (p < kTieCap) {
+                        ties[2 * p] = make_uint4(t.i, (uint32_t)t.is, 0u, tie);
+                        ties[2 * p + 1] = make_uint4(c0, c1, self ^ flip, 0u);
+                    } else {  // list full: decide here
+                        flip |= mp::resolve_tie_bits(tie, c0, c1, thr, 0, t.i, (uint32_t)sw, (uint32_t)w, key.k0,
+                                                     key.k1);
+                    }
+                }
+                if (flip) slab[t.is] = self ^ flip;
+            }
+            // this warp's ties, decided by its lanes together (a word has at most one
+            // entry, and its owner stored the entry's word: a blind store)
+            __syncwarp();
+            const int nt = min(s_tie_n[warp], kTieCap);
+            for (int e = lane; e < nt; e += 32) {
+                const uint4 t = ties[2 * e], u = ties[2 * e + 1];
+                const uint32_t acc =
+                    mp::resolve_tie_bits(t.w, u.x, u.y, thr, 0, t.x, (uint32_t)sw, (uint32_t)w, key.k0, key.k1);
+                if (acc) slab[t.y] = u.z ^ acc;
+            }
+            __syncwarp();
+            if (lane == 0) s_tie_n[warp] = 0;
+            // the half sweep is complete in every slab once all blocks have arrived
+            cluster.barrier_arrive();
+            if (colour == 0) draws_ahead(sw, 1);
+            else draws_ahead(sw + 1, 0);
+            cluster.barrier_wait();
+        };
+        half(0, first0);
+        half(1, first1);
+    }
+    for (int q = tid; q < slab_words; q += kBlock) g[(size_t)(z0 * LL + q) * a.Wn] = slab[q];
+    cluster.sync();  // no block leaves while another may still read its slab
+}
+
+}  // namespace
+
+// Blocks per cluster for an SA run of I instances of side L with Wn words, or 0 when the
+// run is better served by the row kernel: a divisor C <= 8 of L whose slab fits shared
+// memory, the largest for which all I * Wn clusters are resident at once (as the driver
+// reports for this kernel, so that the run is one wave).  Knob SG_SA_CLUSTER_C forces C.
+int sa_cluster_blocks(int I, int L, int Wn, int64_t half_sweep_attempts)
+{
+    if (half_sweep_attempts > ((int64_t)1 << 24)) return 0;  // long half sweeps: the row kernel
+    int dev = 0, smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    const int64_t clusters = (int64_t)I * Wn;
+    const char* e = getenv("SG_SA_CLUSTER_C");
+    const int forced = e ? atoi(e) : 0;
+    for (int C = 8; C >= 1; --C) {
+        if (L % C || (forced && C != forced)) continue;
+        const size_t bytes = (size_t)(L / C) * L * L * 4;
+        if (bytes + 12 * 1024 > (size_t)smem) continue;
+        if (forced) return C;
+        if (bytes > 48 * 1024 &&
+            cudaFuncSetAttribute(sa_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchConfig_t cfg{};
+        cfg.gridDim = dim3(C, (unsigned)std::min<int64_t>(clusters, 65535), 1);
+        cfg.blockDim = dim3(kBlock, 1, 1);
+        cfg.dynamicSmemBytes = bytes;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeClusterDimension;
+        attr[0].val.clusterDim.x = C;
+        attr[0].val.clusterDim.y = 1;
+        attr[0].val.clusterDim.z = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        int active = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, sa_cluster_kernel, &cfg) != cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (active >= clusters) return C;
+    }
+    return 0;
+}
+
+int32_t launch_sa_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKeys* keys, const uint32_t* thr,
+                          int I, int L, int Wn, int R, int S, int C, cudaStream_t st)
+{
+    ClusterArgs a{};
+    a.spins = reinterpret_cast<uint32_t*>(spins);
+    a.j1_ptrs = j1_ptrs;
+    a.keys = keys;
+    a.thr = thr;
+    a.L = L;
+    a.Wn = Wn;
+    a.R = R;
+    a.S = S;
+    a.C = C;
+    const int H = L / 2;
+    a.Hmagic = H == 1 ? 0u : (uint32_t)((0x100000000ull + (uint64_t)H - 1) / (uint64_t)H);
+    const size_t smem = (size_t)(L / C) * L * L * 4;
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(sa_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        set_error("sa_cluster_kernel: cannot use %zu bytes of shared memory", smem);
+        return SG_ECUDA;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(C, Wn, I);
+    cfg.blockDim = dim3(kBlock, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, sa_cluster_kernel, a);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("sa_cluster_kernel launch failed: %s", cudaGetErrorString(e));
+        return SG_ECUDA;
+    }
+    return SG_OK;
+}
+
+}  // namespace sg

@@ -188,6 +188,13 @@ int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
                              const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st,
                              const uint32_t* sweep_base = nullptr, int* status = nullptr);
+// cluster.cu: SA of small lattices, all sweeps in one launch, one thread-block cluster of C
+// blocks per (word, instance); sa_cluster_blocks gives C, or 0 when the row kernel should
+// run instead (long half sweeps, slabs too large, or more clusters than fit at once).
+int sa_cluster_blocks(int I, int L, int Wn, int64_t half_sweep_attempts);
+int32_t launch_sa_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKeys* keys,
+                          const uint32_t* thr /* [S][kThrRow] */, int I, int L, int Wn, int R, int S, int C,
+                          cudaStream_t st);
 int32_t launch_pt_exchange(const ExchangeArgs& x, int I, uint32_t sweep, cudaStream_t st);
 int32_t launch_pt_setup(const unsigned long long* E64, int32_t* E, uint8_t* rung_of_slot,
                         uint8_t* slot_of_rung, unsigned long long* accepts, int32_t* minE,

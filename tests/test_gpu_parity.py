@@ -207,6 +207,27 @@ def test_sa_rows_wider_than_a_block(sg):
     _sa_compare(sg, inst, J3, egs, 288, 3, 0.1, 3.0, seed=23, iid=1, reps=[0, 31, 200, 287])
 
 
+@pytest.mark.parametrize("L,R,S", [(16, 1024, 30), (8, 64, 40), (6, 40, 25), (2, 12, 20), (64, 32, 3),
+                                   (10, 100, 17), (4, 33, 60)])
+def test_sa_cluster_kernel_equals_row_kernel_and_oracle(sg, monkeypatch, L, R, S):
+    """Small lattices run every sweep in one launch, a word of 32 replicas per thread-block
+    cluster whose blocks hold z-slabs (neighbour slabs read through distributed shared
+    memory): identical to the row kernel, and to the oracle on sampled replicas.  Slabs
+    of one z-plane (L = 8, C = 8), six blocks (L = 6), L = 2 (both z neighbours in the
+    other block), ragged last words."""
+    inst = sg.Instance.create(L, 8000 + L)
+    J3, _, egs = inst.get()
+    monkeypatch.setenv("SG_SA_CLUSTER", "1")
+    a = sg.sa_run(inst, R, S, 0.1, 3.0, "geometric", 37, 2, spins="host")
+    monkeypatch.setenv("SG_SA_CLUSTER", "0")
+    b = sg.sa_run(inst, R, S, 0.1, 3.0, "geometric", 37, 2, spins="host")
+    assert np.array_equal(a["spins"], b["spins"]) and np.array_equal(a["E"], b["E"])
+    reps = sorted({0, R // 3, R - 1})
+    ospins, oE = o.sa_run(L, J3, 37, 2, S, 0.1, 3.0, True, reps=reps)
+    assert np.array_equal(a["spins"][reps], ospins)
+    assert np.array_equal(a["E"][reps], oE)
+
+
 def test_runs_longer_than_one_graph_chunk(sg):
     """Runs of 16 or more sweeps go through CUDA graphs of up to 100 sweeps with the
     sweep index on the device: 230 and 251 sweeps end in a shorter last chunk."""
