@@ -597,11 +597,28 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
     for (int a = 0; a < I; ++a) max_L = std::max(max_L, insts[members[a]]->L);
     auto smem_for = [&](int WG) { return planes_smem_bytes(WG, max_L); };
     auto blocks_for = [&](int WG) { return planes_blocks(WG, unit, smem_for(WG)); };
+    // Candidate 0: planes of one word, each annealed by a thread-block cluster of Ccl blocks
+    // (cluster.cu), so that a large plane is not one block's work alone.
+    int Ccl = 0;
+    if (unit) {
+        std::vector<int> Ls(I);
+        for (int a = 0; a < I; ++a) Ls[a] = insts[members[a]]->L;
+        Ccl = sa_cluster_list_blocks(Ls.data(), I, max_L);
+    }
+    auto width = [](int wg) { return wg == 0 ? 1 : wg; };  // words per plane in memory
+    // planes running at once: blocks, or clusters (one block per SM)
+    auto concurrency = [&](int wg) { return wg == 0 ? std::max(1, sms / Ccl) : blocks_for(wg); };
+    auto sweep_launch = [&](int wg, const Plane* d_pl, const int* d_ord, int n, unsigned* d_next,
+                            cudaStream_t s) -> int32_t {
+        if (wg == 0) return launch_sa_cluster_planes(d_pl, d_ord, n, d_next, Ccl, max_L, s);
+        return launch_sa_planes(wg, d_pl, d_ord, n, d_next, unit, blocks_for(wg), s, smem_for(wg));
+    };
 
-    // ---- autotune the words per plane: measured throughput on the batch itself, then the
-    // makespan bound max(total / rate, largest plane / per-block rate) ----
+    // ---- autotune the words per plane (or clusters): measured throughput on the batch
+    // itself, then the makespan bound max(total / rate, largest plane / per-plane rate) ----
     std::vector<int> cands;
     for (int wg = wg_max; wg >= 1; wg >>= 1) cands.push_back(wg);
+    if (Ccl > 0) cands.push_back(0);
     std::string key;
     {
         std::map<std::tuple<int, int, int>, int> mix;
@@ -610,7 +627,8 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
         cudaDeviceProp prop;
         cudaGetDeviceProperties(&prop, dev);
         std::ostringstream ks;
-        ks << prop.name << "/" << sms << "/" << (unit ? "u" : "g") << "/smem" << smem_for(1) / 1024 << "/t3";
+        ks << prop.name << "/" << sms << "/" << (unit ? "u" : "g") << "/smem" << smem_for(1) / 1024 << "/c" << Ccl
+           << "/t4";
         for (auto& m : mix)
             ks << "/" << std::get<0>(m.first) << "x" << std::get<1>(m.first) << "x" << std::get<2>(m.first) << "x" << m.second;
         key = ks.str();
@@ -621,11 +639,13 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
     const char* force = getenv("SG_BATCH_WG");
     if (force && atoi(force) >= 1 && wg_max % atoi(force) == 0) {
         WG = atoi(force);
+    } else if (force && force[0] == '0' && Ccl > 0) {
+        WG = 0;
     } else if (cands.size() > 1) {
         std::lock_guard<std::mutex> lock(g_tune_mu);
         tune_load();
         auto hit = g_tune_mem.find(key);
-        if (hit != g_tune_mem.end() && wg_max % hit->second == 0) {
+        if (hit != g_tune_mem.end() && (hit->second == 0 ? Ccl > 0 : wg_max % hit->second == 0)) {
             WG = hit->second;
         } else {
             double best = 1e300;
@@ -633,16 +653,16 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
                 std::vector<Plane> planes;
                 std::vector<double> work;
                 size_t words = 0;
-                make_planes(wg, nullptr, &planes, &work, &words);
+                make_planes(width(wg), nullptr, &planes, &work, &words);
                 Buf d_sp, d_pl, d_ord, d_next;
                 SG_B(d_sp.alloc(words * 4, st));
-                make_planes(wg, static_cast<uint32_t*>(d_sp.p), &planes, &work, &words);
+                make_planes(width(wg), static_cast<uint32_t*>(d_sp.p), &planes, &work, &words);
                 // trial: a few sweeps of every plane, enough (up to 64) for about 1e9
                 // attempts, so that launch and copy costs do not decide small batches
                 double per_sweep = 0;
                 int s_min = 1 << 30;
                 for (auto& pl : planes) {
-                    per_sweep += (double)pl.L * pl.L * pl.L * 32 * wg;
+                    per_sweep += (double)pl.L * pl.L * pl.L * 32 * width(wg);
                     s_min = std::min(s_min, std::max(pl.S, 1));
                 }
                 const int trial_sweeps =
@@ -650,7 +670,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
                 double trial_work = 0;
                 for (auto& pl : planes) {
                     pl.s_end = std::min(pl.S, trial_sweeps);
-                    trial_work += (double)pl.L * pl.L * pl.L * 32 * wg * pl.s_end;
+                    trial_work += (double)pl.L * pl.L * pl.L * 32 * width(wg) * pl.s_end;
                 }
                 const std::vector<int> order = lpt_order(work);
                 SG_B(d_pl.alloc(sizeof(Plane) * planes.size(), st));
@@ -658,16 +678,15 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
                 SG_B(d_next.alloc(sizeof(unsigned), st));
                 SG_TRY_CUDA(cudaMemcpyAsync(d_pl.p, planes.data(), sizeof(Plane) * planes.size(), cudaMemcpyHostToDevice, st));
                 SG_TRY_CUDA(cudaMemcpyAsync(d_ord.p, order.data(), sizeof(int) * order.size(), cudaMemcpyHostToDevice, st));
-                SG_B(launch_planes_init(wg, static_cast<Plane*>(d_pl.p), (int)planes.size(), st));
-                const int blocks = blocks_for(wg);
+                SG_B(launch_planes_init(width(wg), static_cast<Plane*>(d_pl.p), (int)planes.size(), st));
+                const int conc = concurrency(wg);
                 double t_best = 1e300;
                 for (int rep = 0; rep < 2; ++rep) {
                     SG_TRY_CUDA(cudaMemsetAsync(d_next.p, 0, sizeof(unsigned), st));
                     SG_TRY_CUDA(cudaStreamSynchronize(st));
                     const auto t0 = std::chrono::steady_clock::now();
-                    SG_B(launch_sa_planes(wg, static_cast<Plane*>(d_pl.p), static_cast<int*>(d_ord.p),
-                                          (int)planes.size(), static_cast<unsigned*>(d_next.p), unit, blocks, st,
-                                          smem_for(wg)));
+                    SG_B(sweep_launch(wg, static_cast<Plane*>(d_pl.p), static_cast<int*>(d_ord.p),
+                                      (int)planes.size(), static_cast<unsigned*>(d_next.p), st));
                     SG_TRY_CUDA(cudaStreamSynchronize(st));
                     t_best = std::min(t_best, std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count());
                 }
@@ -677,7 +696,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
                     total += w;
                     biggest = std::max(biggest, w);
                 }
-                const double est = std::max(total / rate, biggest / (rate / std::min<double>(blocks, work.size())));
+                const double est = std::max(total / rate, biggest / (rate / std::min<double>(conc, work.size())));
                 if (est < best) {
                     best = est;
                     WG = wg;
@@ -693,16 +712,17 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
     std::vector<Plane> planes;
     std::vector<double> work;
     size_t words = 0;
-    make_planes(WG, nullptr, &planes, &work, &words);
+    const int WGm = width(WG);  // words per plane in memory
+    make_planes(WGm, nullptr, &planes, &work, &words);
     Buf d_sp, d_pl, d_ord, d_next, d_E, d_outs, d_stage;
     SG_B(d_sp.alloc(words * 4, st));
-    make_planes(WG, static_cast<uint32_t*>(d_sp.p), &planes, &work, &words);
+    make_planes(WGm, static_cast<uint32_t*>(d_sp.p), &planes, &work, &words);
     const std::vector<int> order = lpt_order(work);
     const int n = (int)planes.size();
     SG_B(d_pl.alloc(sizeof(Plane) * n, st));
     SG_B(d_ord.alloc(sizeof(int) * n, st));
     SG_B(d_next.alloc(sizeof(unsigned), st));
-    SG_B(d_E.alloc(sizeof(unsigned long long) * (size_t)n * 32 * WG, st));
+    SG_B(d_E.alloc(sizeof(unsigned long long) * (size_t)n * 32 * WGm, st));
     // spin outputs: device targets directly, host targets through one staging area
     std::vector<int8_t*> outp(I, nullptr);
     size_t stage_bytes = 0;
@@ -726,7 +746,6 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
     SG_TRY_CUDA(cudaMemcpyAsync(d_outs.p, outp.data(), sizeof(int8_t*) * I, cudaMemcpyHostToDevice, st));
     SG_TRY_CUDA(cudaStreamSynchronize(st));  // host arrays above are stack/heap temporaries
 
-    const int blocks = blocks_for(WG);
     // launch statistics: with timing on, the run launches directly and brackets the
     // persistent sweep launch with events
     const bool timed = stats_timing();
@@ -746,14 +765,14 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
     }
     auto device_work = [&](cudaStream_t s) -> int32_t {
         SG_TRY_CUDA(cudaMemsetAsync(d_next.p, 0, sizeof(unsigned), s));
-        SG_TRY_CUDA(cudaMemsetAsync(d_E.p, 0, sizeof(unsigned long long) * (size_t)n * 32 * WG, s));
-        SG_B(launch_planes_init(WG, static_cast<Plane*>(d_pl.p), n, s));
+        SG_TRY_CUDA(cudaMemsetAsync(d_E.p, 0, sizeof(unsigned long long) * (size_t)n * 32 * WGm, s));
+        SG_B(launch_planes_init(WGm, static_cast<Plane*>(d_pl.p), n, s));
         if (timed) SG_TRY_CUDA(cudaEventRecord(ev[0], s));
-        SG_B(launch_sa_planes(WG, static_cast<Plane*>(d_pl.p), static_cast<int*>(d_ord.p), n,
-                              static_cast<unsigned*>(d_next.p), unit, blocks, s, smem_for(WG)));
+        SG_B(sweep_launch(WG, static_cast<Plane*>(d_pl.p), static_cast<int*>(d_ord.p), n,
+                          static_cast<unsigned*>(d_next.p), s));
         if (timed) SG_TRY_CUDA(cudaEventRecord(ev[1], s));
-        SG_B(launch_planes_energy(WG, static_cast<Plane*>(d_pl.p), n, static_cast<unsigned long long*>(d_E.p), s));
-        SG_B(launch_planes_unpack(WG, static_cast<Plane*>(d_pl.p), n, static_cast<int8_t* const*>(d_outs.p), s));
+        SG_B(launch_planes_energy(WGm, static_cast<Plane*>(d_pl.p), n, static_cast<unsigned long long*>(d_E.p), s));
+        SG_B(launch_planes_unpack(WGm, static_cast<Plane*>(d_pl.p), n, static_cast<int8_t* const*>(d_outs.p), s));
         return SG_OK;
     };
     // the device part of the run is one CUDA graph (knob SG_BATCH_GRAPH=0 launches directly)
@@ -784,7 +803,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
         SG_B(device_work(st));
     }
 
-    std::vector<unsigned long long> E((size_t)n * 32 * WG);
+    std::vector<unsigned long long> E((size_t)n * 32 * WGm);
     SG_TRY_CUDA(cudaMemcpyAsync(E.data(), d_E.p, sizeof(unsigned long long) * E.size(), cudaMemcpyDeviceToHost, st));
     for (int a = 0; a < I; ++a) {
         const sg_sa_result& o = outs[members[a]];
@@ -813,10 +832,10 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
         const int a = pl.out;
         const sg_sa_result& o = outs[members[a]];
         const int64_t egs = insts[members[a]]->e_gs;
-        for (int rb = 0; rb < 32 * WG; ++rb) {
+        for (int rb = 0; rb < 32 * WGm; ++rb) {
             const int r = 32 * pl.w0 + rb;
             if (r >= pl.R) continue;
-            o.E[r] = (int64_t)(long long)E[(size_t)q * 32 * WG + rb];
+            o.E[r] = (int64_t)(long long)E[(size_t)q * 32 * WGm + rb];
             if (o.eps) o.eps[r] = (double)(o.E[r] - egs) / (double)(-egs);
         }
     }

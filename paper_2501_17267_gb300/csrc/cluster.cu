@@ -43,28 +43,38 @@ __device__ __forceinline__ uint32_t word_valid_bits(int R, int w)
     return left >= 32 ? 0xFFFFFFFFu : left <= 0 ? 0u : (1u << left) - 1u;
 }
 
-__global__ void __launch_bounds__(kBlock) sa_cluster_kernel(const ClusterArgs a)
-{
-    extern __shared__ uint32_t slab[];  // [L / C][L][L] words of this block's slab, storage order
-    __shared__ uint4 s_ties[(kBlock / 32) * kTieCap * 2];  // per warp: {site, local, -, tie}, {c0, c1, word, -}
-    __shared__ int s_tie_n[kBlock / 32];
+// One word of one lattice, annealed by a cluster of C blocks (block r: z-slab r): the
+// plane's word of site s is g[s * stride]; the draws use word index w of the instance.
+struct PlaneRun {
+    uint32_t* g;
+    int stride;
+    const uint8_t* j1;    // [N] coupling sign bits (all |J| = 1)
+    const uint32_t* thr;  // [S][kThrRow]
+    RunKeys key;
+    int L, w, R, s_begin, s_end;  // side, word, replicas of the instance, sweeps [s_begin, s_end)
+    uint32_t Hmagic;              // ceil(2^32 / (L / 2))
+};
 
+// Called by every thread of every block of the cluster; slab: dynamic shared memory of
+// at least (L / C) * L * L words.  Ends with the plane written back and a cluster barrier.
+__device__ __forceinline__ void anneal_plane(const PlaneRun& p, const int C, uint32_t* slab, uint4* s_ties,
+                                             int* s_tie_n)
+{
     cg::cluster_group cluster = cg::this_cluster();
     const int r = (int)cluster.block_rank();
-    const int C = a.C;
-    const int w = blockIdx.y, inst = blockIdx.z;
-    const int L = a.L, H = L >> 1, LL = L * L;
+    const int w = p.w;
+    const int L = p.L, H = L >> 1, LL = L * L;
     const int zc = L / C;              // z-planes per slab
     const int slab_words = zc * LL;
     const int z0 = r * zc;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const RunKeys key = a.keys[inst];
-    const uint8_t* __restrict__ j1 = a.j1_ptrs[inst];
-    uint32_t* __restrict__ g = a.spins + (size_t)inst * LL * L * a.Wn + w;  // word w of site 0
+    const RunKeys key = p.key;
+    const uint8_t* __restrict__ j1 = p.j1;
+    uint32_t* __restrict__ g = p.g;
     // slabs of the blocks above (z0 + zc) and below (z0 - 1), periodic in z
     const uint32_t* up = cluster.map_shared_rank(slab, (r + 1) % C);
     const uint32_t* dn = cluster.map_shared_rank(slab, (r + C - 1) % C);
-    const uint32_t valid = word_valid_bits(a.R, w);
+    const uint32_t valid = word_valid_bits(p.R, w);
     uint4* ties = s_ties + warp * kTieCap * 2;
     const int items = zc * L * H;  // sites of one colour in the slab
 
@@ -78,7 +88,7 @@ __global__ void __launch_bounds__(kBlock) sa_cluster_kernel(const ClusterArgs a)
     };
     auto site_of = [&](int q, int colour) {
         Site t;
-        const int rl = H == 1 ? q : (int)__umulhi((uint32_t)q, a.Hmagic);
+        const int rl = H == 1 ? q : (int)__umulhi((uint32_t)q, p.Hmagic);
         const int j = q - rl * H;
         const int zl = rl / L, y = rl - zl * L;
         const int z = z0 + zl;
@@ -109,17 +119,17 @@ __global__ void __launch_bounds__(kBlock) sa_cluster_kernel(const ClusterArgs a)
     // the sweep, so they are computed while the cluster barrier before it completes.
     uint32_t A0[8];
     auto draws_ahead = [&](int sw, int colour) {
-        if (sw < a.S && tid < items) mp::lead_planes((colour ? first1 : first0).i, (uint32_t)sw, (uint32_t)w, key, A0);
+        if (sw < p.s_end && tid < items) mp::lead_planes((colour ? first1 : first0).i, (uint32_t)sw, (uint32_t)w, key, A0);
     };
 
-    for (int q = tid; q < slab_words; q += kBlock) slab[q] = g[(size_t)(z0 * LL + q) * a.Wn];
+    for (int q = tid; q < slab_words; q += kBlock) slab[q] = g[(size_t)(z0 * LL + q) * p.stride];
     if (tid < kBlock / 32) s_tie_n[tid] = 0;
     cluster.barrier_arrive();
-    draws_ahead(0, 0);
+    draws_ahead(p.s_begin, 0);
     cluster.barrier_wait();  // every slab loaded before any block reads its neighbours'
 
-    for (int sw = 0; sw < a.S; ++sw) {
-        const uint32_t* thr = a.thr + (size_t)sw * kThrRow;  // the sweep's thresholds, k = 0 .. 15
+    for (int sw = p.s_begin; sw < p.s_end; ++sw) {
+        const uint32_t* thr = p.thr + (size_t)sw * kThrRow;  // the sweep's thresholds, k = 0 .. 15
         uint32_t tp[24], lz[3];  // its threshold planes: the same for every replica
         {
             const uint32_t t2 = thr[2], t4 = thr[4], t6 = thr[6];
@@ -185,8 +195,69 @@ __global__ void __launch_bounds__(kBlock) sa_cluster_kernel(const ClusterArgs a)
         half(0, first0);
         half(1, first1);
     }
-    for (int q = tid; q < slab_words; q += kBlock) g[(size_t)(z0 * LL + q) * a.Wn] = slab[q];
-    cluster.sync();  // no block leaves while another may still read its slab
+    for (int q = tid; q < slab_words; q += kBlock) g[(size_t)(z0 * LL + q) * p.stride] = slab[q];
+    cluster.sync();  // no block goes on (or leaves) while another may still read its slab
+}
+
+__global__ void __launch_bounds__(kBlock) sa_cluster_kernel(const ClusterArgs a)
+{
+    extern __shared__ uint32_t slab[];  // [L / C][L][L] words of this block's slab, storage order
+    __shared__ uint4 s_ties[(kBlock / 32) * kTieCap * 2];  // per warp: {site, local, -, tie}, {c0, c1, word, -}
+    __shared__ int s_tie_n[kBlock / 32];
+    const int w = blockIdx.y, inst = blockIdx.z;
+    PlaneRun p;
+    p.g = a.spins + (size_t)inst * a.L * a.L * a.L * a.Wn + w;
+    p.stride = a.Wn;
+    p.j1 = a.j1_ptrs[inst];
+    p.thr = a.thr;
+    p.key = a.keys[inst];
+    p.L = a.L;
+    p.w = w;
+    p.R = a.R;
+    p.s_begin = 0;
+    p.s_end = a.S;
+    p.Hmagic = a.Hmagic;
+    anneal_plane(p, a.C, slab, s_ties, s_tie_n);
+}
+
+// Persistent form for batches (batch.cu's planes of one word, [N][1]): clusters take
+// planes from `order` (longest first) through the counter `next` until none is left;
+// every plane's side is a multiple of C.
+// (Registers are not capped: one block per SM without spills measured 8 % faster on the
+// uneven-batch workload than two per SM with a 128-register cap.)
+__global__ void __launch_bounds__(kBlock, 1) sa_cluster_list_kernel(const Plane* __restrict__ planes,
+                                                                 const int* __restrict__ order, int n,
+                                                                 unsigned* __restrict__ next, int C)
+{
+    extern __shared__ uint32_t slab[];
+    __shared__ uint4 s_ties[(kBlock / 32) * kTieCap * 2];
+    __shared__ int s_tie_n[kBlock / 32];
+    __shared__ int s_item;
+    cg::cluster_group cluster = cg::this_cluster();
+    const int r = (int)cluster.block_rank();
+    for (;;) {
+        if (r == 0 && threadIdx.x == 0) {  // claim the next plane for the whole cluster
+            const int it = (int)atomicAdd(next, 1u);
+            for (int k = 0; k < C; ++k) *cluster.map_shared_rank(&s_item, k) = it;
+        }
+        cluster.sync();
+        const int it = s_item;
+        if (it >= n) break;
+        const Plane& q = planes[order[it]];
+        PlaneRun p;
+        p.g = q.spins;
+        p.stride = 1;
+        p.j1 = q.j1;
+        p.thr = q.thr;
+        p.key = RunKeys{q.k0, q.k1};
+        p.L = q.L;
+        p.w = q.w0;
+        p.R = q.R;
+        p.s_begin = q.s_begin;
+        p.s_end = q.s_end;
+        p.Hmagic = q.Hmagic;
+        anneal_plane(p, C, slab, s_ties, s_tie_n);  // ends with a cluster barrier
+    }
 }
 
 }  // namespace
@@ -234,6 +305,81 @@ int sa_cluster_blocks(int I, int L, int Wn, int64_t half_sweep_attempts)
         if (active >= clusters) return C;
     }
     return 0;
+}
+
+namespace {
+// Resident clusters of C blocks with `smem` bytes each for `fn`, or 0.
+int active_clusters(const void* fn, int C, size_t smem)
+{
+    if (smem > 48 * 1024 &&
+        cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(C, 1, 1);
+    cfg.blockDim = dim3(kBlock, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    int active = 0;
+    if (cudaOccupancyMaxActiveClusters(&active, fn, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return active;
+}
+}  // namespace
+
+int sa_cluster_list_blocks(const int* Ls, int n, int max_L)
+{
+    int dev = 0, smem = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    for (int C = 8; C >= 2; --C) {
+        bool ok = true;
+        for (int k = 0; k < n && ok; ++k) ok = Ls[k] % C == 0;
+        if (!ok) continue;
+        const size_t bytes = (size_t)(max_L / C) * max_L * max_L * 4;
+        if (bytes + 12 * 1024 > (size_t)smem) continue;
+        if (active_clusters((const void*)sa_cluster_list_kernel, C, bytes) > 0) return C;
+    }
+    return 0;
+}
+
+int32_t launch_sa_cluster_planes(const Plane* d_planes, const int* d_order, int n, unsigned* d_next, int C,
+                                 int max_L, cudaStream_t st)
+{
+    const size_t smem = (size_t)(max_L / C) * max_L * max_L * 4;
+    const int clusters = active_clusters((const void*)sa_cluster_list_kernel, C, smem);
+    if (clusters < 1) {
+        set_error("sa_cluster_list_kernel: no cluster of %d blocks with %zu bytes fits", C, smem);
+        return SG_ECUDA;
+    }
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(C * std::min(clusters, n), 1, 1);
+    cfg.blockDim = dim3(kBlock, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = C;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    const cudaError_t e = cudaLaunchKernelEx(&cfg, sa_cluster_list_kernel, d_planes, d_order, n, d_next, C);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        set_error("sa_cluster_list_kernel launch failed: %s", cudaGetErrorString(e));
+        return SG_ECUDA;
+    }
+    return SG_OK;
 }
 
 int32_t launch_sa_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKeys* keys, const uint32_t* thr,

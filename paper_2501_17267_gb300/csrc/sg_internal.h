@@ -195,6 +195,11 @@ int sa_cluster_blocks(int I, int L, int Wn, int64_t half_sweep_attempts);
 int32_t launch_sa_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKeys* keys,
                           const uint32_t* thr /* [S][kThrRow] */, int I, int L, int Wn, int R, int S, int C,
                           cudaStream_t st);
+// The persistent cluster form for batches of one-word planes (batch.cu): C for planes of
+// sides Ls (every side a multiple of C, the slab of the largest fitting), or 0.
+int sa_cluster_list_blocks(const int* Ls, int n, int max_L);
+int32_t launch_sa_cluster_planes(const Plane* d_planes, const int* d_order, int n, unsigned* d_next, int C,
+                                 int max_L, cudaStream_t st);
 int32_t launch_pt_exchange(const ExchangeArgs& x, int I, uint32_t sweep, cudaStream_t st);
 int32_t launch_pt_setup(const unsigned long long* E64, int32_t* E, uint8_t* rung_of_slot,
                         uint8_t* slot_of_rung, unsigned long long* accepts, int32_t* minE,

@@ -328,10 +328,11 @@ def test_batch_autotuner_records_and_reuses_choice(sg, monkeypatch, tmp_path):
         assert np.array_equal(a["spins"], b["spins"])
 
 
-@pytest.mark.parametrize("wg,graph", [("1", "1"), ("2", "0"), ("4", "1")])
+@pytest.mark.parametrize("wg,graph", [("1", "1"), ("2", "0"), ("4", "1"), ("0", "1"), ("0", "0")])
 def test_uneven_batch_any_plane_width(sg, monkeypatch, wg, graph):
-    """Every words-per-plane choice and graph capture on or off give the same bytes
-    (R = 100 spans four words, the last one ragged, so all widths apply)."""
+    """Every words-per-plane choice, the thread-block-cluster form ("0": one-word planes,
+    each split into z-slabs across a cluster; here C = 2 for L = 4, 8, 6) and graph
+    capture on or off give the same bytes (R = 100 spans four words, the last ragged)."""
     insts = [sg.Instance.create(L, 77 + L) for L in (4, 8, 6)]
     params = [dict(replicas=100, sweeps=S, beta0=0.2, beta1=2.5, schedule="linear", seed=3,
                    instance_id=k) for k, S in enumerate((20, 9, 14))]
