@@ -433,7 +433,7 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
                 }));
     }
     SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * (size_t)I * Rp, st));
-    SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st); }));
+    SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st, unit_j ? j1p : nullptr); }));
 
     std::vector<long long> E64((size_t)I * Rp);
     int flags[2] = {0, 0};
@@ -555,7 +555,7 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     const int64_t cells = (int64_t)I * N * Rp;
     unsigned long long* E64d = d_E64.as<unsigned long long>();
     SG_RET(log.run(SG_KERNEL_INIT, cells, st, [&] { return launch_init_spins(spins, kp, I, L, Wn, K, st); }));
-    SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st); }));
+    SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st, unit_j ? j1p : nullptr); }));
     SG_RET(log.run(SG_KERNEL_OTHER, (int64_t)I * Rp, st, [&] {
         return launch_pt_setup(E64d, E, perm, inv, acc, minE, I, Rp, K, st);
     }));
@@ -605,7 +605,7 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
                            [&] { return launch_pt_exchange(xa, I, (uint32_t)s, st); }));
     }
     SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * (size_t)I * Rp, st));
-    SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st); }));
+    SG_RET(log.run(SG_KERNEL_ENERGY, cells, st, [&] { return launch_energy(spins, j6p, I, L, Wn, E64d, st, unit_j ? j1p : nullptr); }));
     SG_RET(log.run(SG_KERNEL_OTHER, (int64_t)I * Rp, st, [&] {
         return launch_check_energy(E64d, E, I, Rp, K, d_flag.as<int>(), st);
     }));

@@ -12,6 +12,7 @@
 #include <algorithm>
 
 #include "exchange.cuh"
+#include "metropolis.cuh"
 #include "philox.cuh"
 #include "sg_internal.h"
 
@@ -113,6 +114,80 @@ energy_bits_kernel(const uint32_t* __restrict__ spins, const uint2* const* __res
         }
         if (e) atomicAdd(&Ei[32 * w + lane], (unsigned long long)e);
     }
+}
+
+// All |J| = 1: H = 3N - 2 * (satisfied forward bonds), a bond being satisfied when its
+// term J s_i s_j is -1.  Each warp takes one word w and each of its threads a set of
+// sites; a thread adds the bit-sliced count (0..3) of its sites' satisfied forward bonds
+// into vertical counters, and the warp reduces them through a 32 x 32 bit transpose.
+constexpr int kEBits = 24;  // counter planes: up to 2^24 - 1 per thread
+
+__global__ void __launch_bounds__(kBlock)
+energy_unit_kernel(const uint32_t* __restrict__ spins, const uint8_t* const* __restrict__ j1_ptrs, int L, int Wn,
+                   unsigned long long* __restrict__ E_out)
+{
+    const int inst = blockIdx.y;
+    const int64_t N = (int64_t)L * L * L;
+    const int H = L >> 1;
+    const uint8_t* __restrict__ j1 = j1_ptrs[inst];
+    const uint32_t* __restrict__ s = spins + (size_t)inst * (size_t)N * Wn;
+    const int lane = threadIdx.x & 31;
+    const int gw = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // warp index in the instance's grid
+    const int nw = (gridDim.x * blockDim.x) >> 5;
+    const int wpw = nw / Wn;  // warps per word
+    if (gw >= wpw * Wn) return;  // whole warps only
+    const int w = gw % Wn;
+    const int64_t chunk = (int64_t)(gw / Wn) * 32 + lane, nchunks = (int64_t)wpw * 32;
+    uint32_t V[kEBits];
+#pragma unroll
+    for (int k = 0; k < kEBits; ++k) V[k] = 0;
+    int64_t nsites = 0;
+    for (int64_t is = chunk; is < N; is += nchunks) {  // storage position
+        const int row = (int)(is / L), pos = (int)(is - (int64_t)row * L);
+        const int z = row / L, y = row - z * L;
+        const int par = pos >= H ? 1 : 0, j = pos - par * H, x = 2 * j + par;
+        const int xp = x + 1 == L ? 0 : x + 1;
+        const int posx = (xp & 1) * H + (xp >> 1);
+        const int rowy = z * L + (y + 1 == L ? 0 : y + 1), rowz = (z + 1 == L ? 0 : z + 1) * L + y;
+        const uint32_t me = s[is * Wn + w];
+        const uint32_t nx = s[((int64_t)row * L + posx) * Wn + w];
+        const uint32_t ny = s[((int64_t)rowy * L + pos) * Wn + w];
+        const uint32_t nz = s[((int64_t)rowz * L + pos) * Wn + w];
+        const uint32_t sb = j1[(int64_t)row * L + x];
+        // satisfied: the spins differ under J > 0, agree under J < 0 (bits 0, 2, 4: +x, +y, +z)
+        const uint32_t a = me ^ nx ^ (0u - (sb & 1u));
+        const uint32_t b = me ^ ny ^ (0u - ((sb >> 2) & 1u));
+        const uint32_t c = me ^ nz ^ (0u - ((sb >> 4) & 1u));
+        const uint32_t c0 = a ^ b ^ c, c1 = mp::maj3(a, b, c);  // the count: planes of weight 1, 2
+        // V += (c1 c0), the carry rippled up until it is gone
+        uint32_t carry = V[0] & c0;
+        V[0] ^= c0;
+        {
+            const uint32_t t = V[1] ^ c1 ^ carry;
+            carry = mp::maj3(V[1], c1, carry);
+            V[1] = t;
+        }
+#pragma unroll
+        for (int k = 2; k < kEBits; ++k) {
+            if (!carry) break;
+            const uint32_t t = V[k] & carry;
+            V[k] ^= carry;
+            carry = t;
+        }
+        ++nsites;
+    }
+    // lane r of the transposed planes holds replica r of every lane's counter
+    uint32_t T[kEBits];
+#pragma unroll
+    for (int k = 0; k < kEBits; ++k) T[k] = mp::warp_transpose(V[k], lane);
+    long long sat = 0;
+#pragma unroll
+    for (int k = 0; k < kEBits; ++k) sat += (long long)__popc(T[k]) << k;
+    long long sites = nsites;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sites += __shfl_xor_sync(0xFFFFFFFFu, sites, o);
+    const long long e = 3 * sites - 2 * sat;
+    if (e) atomicAdd(&E_out[(size_t)inst * 32 * Wn + 32 * w + lane], (unsigned long long)e);
 }
 
 // ---------------------------------------------------------------- parallel tempering
@@ -248,8 +323,20 @@ int32_t launch_init_spins(int8_t* spins, const RunKeys* keys_dev, int I, int L, 
 }
 
 int32_t launch_energy(const int8_t* spins, const uint2* const* j6_ptrs, int I, int L, int Wn,
-                      unsigned long long* E_out, cudaStream_t st)
+                      unsigned long long* E_out, cudaStream_t st, const uint8_t* const* j1_ptrs)
 {
+    if (j1_ptrs) {  // all |J| = 1: the bit-sliced kernel, at least two warps per word
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        const int64_t N = (int64_t)L * L * L;
+        const int64_t want_warps = std::max<int64_t>(2 * Wn, (8LL * sms * (kBlock / 32) + I - 1) / I);
+        const int64_t max_warps = std::max<int64_t>(Wn, (N * Wn + 31) / 32);  // a site per lane at most
+        const int64_t warps = (std::min(want_warps, max_warps) + Wn - 1) / Wn * Wn;  // a multiple of Wn
+        const int gx = (int)std::min<int64_t>((warps * 32 + kBlock - 1) / kBlock, 1 << 20);
+        energy_unit_kernel<<<dim3(gx, I), kBlock, 0, st>>>((const uint32_t*)spins, j1_ptrs, L, Wn, E_out);
+        return check_launch("energy_unit");
+    }
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);

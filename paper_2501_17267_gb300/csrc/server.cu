@@ -376,8 +376,11 @@ int32_t admit_request(sg_server* srv, Request* q)
     SG_TRY_CUDA(cudaMemsetAsync(q->at<void>(y.done), 0, 4, st));
     const RunKeys* kp = q->at<RunKeys>(y.keys);
     const uint2* const* j6p = q->at<const uint2*>(y.jp);
+    const uint8_t* const* j1p = reinterpret_cast<const uint8_t* const*>(q->at<const void*>(y.jp) + 1);
     rc = launch_init_spins(q->at<int8_t>(y.spins), kp, 1, q->L, q->Wn, q->req.width, st);
-    if (rc == SG_OK) rc = launch_energy(q->at<int8_t>(y.spins), j6p, 1, q->L, q->Wn, q->at<unsigned long long>(y.E64), st);
+    if (rc == SG_OK)
+        rc = launch_energy(q->at<int8_t>(y.spins), j6p, 1, q->L, q->Wn, q->at<unsigned long long>(y.E64), st,
+                           q->inst->unit_couplings ? j1p : nullptr);
     if (rc == SG_OK)
         rc = launch_pt_setup(q->at<unsigned long long>(y.E64), q->at<int32_t>(y.E), q->at<uint8_t>(y.perm),
                              q->at<uint8_t>(y.inv), q->at<unsigned long long>(y.acc), q->at<int32_t>(y.minE), 1,
@@ -439,7 +442,7 @@ int32_t capture_chunk(Request* q, int n, cudaGraphExec_t* out)
         advance_kernel<<<1, 1, 0, st>>>(base, (uint32_t)n);
         if (q->mode == kRowsSA) {
             cudaMemsetAsync(q->at<void>(y.E64), 0, 8 * (size_t)q->Rp, st);
-            rc = launch_energy(spins, j6p, 1, q->L, q->Wn, q->at<unsigned long long>(y.E64), st);
+            rc = launch_energy(spins, j6p, 1, q->L, q->Wn, q->at<unsigned long long>(y.E64), st, unit ? j1p : nullptr);
             if (rc == SG_OK)
                 min_energy_kernel<<<1, 256, 0, st>>>(q->at<unsigned long long>(y.E64), q->req.width,
                                                      q->at<long long>(y.out));

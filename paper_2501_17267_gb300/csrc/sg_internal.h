@@ -154,8 +154,10 @@ int32_t launch_prepare_j6(const int8_t* J3_dev, uint2* j6_dev, uint8_t* j1_dev, 
                           cudaStream_t st);
 int32_t launch_init_spins(int8_t* spins, const RunKeys* keys_dev, int I, int L, int Wn, int R,
                           cudaStream_t st);
+// j1_ptrs (per instance sign bits) only when every coupling is +-1: the bit-sliced kernel
 int32_t launch_energy(const int8_t* spins, const uint2* const* j6_ptrs, int I, int L, int Wn,
-                      unsigned long long* E_out /* [I][32*Wn], added to */, cudaStream_t st);
+                      unsigned long long* E_out /* [I][32*Wn], added to */, cudaStream_t st,
+                      const uint8_t* const* j1_ptrs = nullptr);
 int32_t launch_half_sweep_sa(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_row /* kThrRow */, int32_t* E, int* status,
