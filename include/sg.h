@@ -138,6 +138,46 @@ int32_t sg_sa_run_batch(const sg_instance* const* insts, const sg_sa_params* ps,
                         sg_sa_result* outs, void* stream);
 
 /* ------------------------------------------------------------------------ */
+/* Fragment meta-heuristic (Sec. II; App. A, Fig. 5) with SA fragment        */
+/* anneals.                                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* The paper's linear-time meta-heuristic bootstraps local optimisations of small
+ * cubic fragments (its own runs contract tensor networks; it notes that SA can take
+ * their place).  Our reading: spins are fixed in l^3 waves -- wave a + l*(b + l*c)
+ * fixes every spin with coordinates congruent to (a, b, c) mod l -- and spin i is
+ * fixed from the cube of side l centred on it: the cube's spins fixed by earlier waves
+ * keep their values, the others are annealed (32 independent reads, `sweeps`
+ * checkerboard sweeps along the geometric schedule beta0 -> beta1) with only the
+ * bonds inside the cube, and spin i takes its value in the read of lowest cube
+ * energy (the first such read).  With L a multiple of l the cubes of one wave are
+ * disjoint and are annealed in parallel.  Draws: read r at cube site q (q = dx +
+ * l*(dy + l*dz), offsets from the cube's corner) uses word r % 4 of the Philox block
+ * at counter (i, sweep, 8q + r/4, 5); initial values sweep 0xFFFFFFFF, bit 31. */
+typedef struct sg_fragment_params {
+    int32_t l;             /* fragment side: odd, 1 <= l < L, L a multiple of l, l <= 7 */
+    int32_t sweeps;        /* >= 0 sweeps per fragment anneal */
+    double beta0, beta1;   /* geometric schedule end points, > 0 */
+    uint32_t instance_id;  /* mixed into the RNG key */
+    uint64_t seed;         /* run seed */
+} sg_fragment_params;
+
+typedef struct sg_fragment_result {
+    int64_t E;             /* energy (Eq. 1) of the configuration reached */
+    double eps;            /* its optimality gap (Eq. 2) */
+    int8_t* spins;         /* [N] the configuration, may be NULL */
+    int32_t spins_mem;     /* SG_MEM_HOST or SG_MEM_DEVICE for `spins` */
+} sg_fragment_result;
+
+/* Run the meta-heuristic on n instances of one side L with one set of parameters
+ * (wave by wave, all instances' fragments of a wave in one launch).  Errors:
+ * SG_EINVAL (unequal L or parameters, l not as stated), SG_ENOMEM, SG_ECUDA. */
+int32_t sg_fragment_run_batch(const sg_instance* const* insts, const sg_fragment_params* p, int32_t n,
+                              sg_fragment_result* outs, void* stream);
+int32_t sg_fragment_run(const sg_instance* inst, const sg_fragment_params* p, sg_fragment_result* out,
+                        void* stream);
+
+/* ------------------------------------------------------------------------ */
 /* Parallel tempering (App. D.2).                                            */
 /* ------------------------------------------------------------------------ */
 

@@ -479,3 +479,114 @@ int or_pt_run(int L, const int8_t* J3, uint64_t seed, uint32_t instance_id,
     free(beta); free(perm); free(slot);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Linear-time fragment meta-heuristic (Sec. II; App. A, Fig. 5), with      */
+/* simulated annealing as the subsystem optimizer (the paper's suggestion;  */
+/* its own runs contract tensor-network fragments).                          */
+/* ------------------------------------------------------------------------ */
+
+/* Our reading of the bootstrapping.  Spins are fixed ("decimated") in l^3 waves; wave
+ * w = a + l*(b + l*c) fixes every spin whose coordinates are congruent to (a, b, c)
+ * mod l.  The fragment of spin i is the cube of side l centred on it (offsets -h .. h,
+ * h = (l - 1) / 2, periodic); with L a multiple of l the fragments of one wave are
+ * disjoint.  Inside the fragment the spins fixed by earlier waves keep their values,
+ * the others are annealed: OR_FRAGMENT_READS independent reads, S checkerboard sweeps
+ * (colour by x + y + z as for the whole lattice) along the geometric schedule
+ * b0 -> b1, Metropolis with only the bonds whose two ends lie in the fragment (bonds
+ * leaving it are dropped).  Spin i then takes its value in the read of lowest fragment
+ * energy (the first such read).  Draws: read r at fragment site q = dx + l*(dy + l*dz)
+ * (d = offset + h) uses word r % 4 of the block at counter (i, sweep, 8*q + r/4,
+ * FRAGMENT) as its 32-bit uniform; initial values use sweep 0xFFFFFFFF, bit 31. */
+int or_fragment_run(int L, const int8_t* J3, int l, int S, double b0, double b1, uint64_t seed,
+                    uint32_t instance_id, int8_t* spins_out, int64_t* E_out)
+{
+    if (L < 2 || (L % 2) != 0 || l < 1 || (l % 2) == 0 || (L % l) != 0 || l >= L || S < 0) return -1;
+    const int64_t N = (int64_t)L * L * L;
+    const int h = (l - 1) / 2, V = l * l * l, R = OR_FRAGMENT_READS;
+    double* beta = (double*)malloc(sizeof(double) * (size_t)(S > 0 ? S : 1));
+    int8_t* f = (int8_t*)malloc((size_t)V * (size_t)R);   /* f[r * V + q] */
+    int8_t* fixed = (int8_t*)malloc((size_t)V);
+    int64_t* site = (int64_t*)malloc(sizeof(int64_t) * (size_t)V);
+    if (!beta || !f || !fixed || !site) {
+        free(beta); free(f); free(fixed); free(site);
+        return -2;
+    }
+    or_beta_schedule(S, b0, b1, 1, beta);
+    uint32_t k0, k1;
+    run_key(seed, instance_id, &k0, &k1);
+    for (int64_t i = 0; i < N; ++i) spins_out[i] = 0; /* 0: not fixed yet */
+
+    for (int w = 0; w < l * l * l; ++w) {
+        const int a = w % l, b = (w / l) % l, c = w / (l * l);
+        for (int cz = c; cz < L; cz += l)
+            for (int cy = b; cy < L; cy += l)
+                for (int cx = a; cx < L; cx += l) {
+                    const int64_t centre = or_site(L, cx, cy, cz);
+                    /* the fragment's sites, and which of them earlier waves fixed */
+                    for (int q = 0; q < V; ++q) {
+                        const int dx = q % l, dy = (q / l) % l, dz = q / (l * l);
+                        site[q] = or_site(L, cx + dx - h, cy + dy - h, cz + dz - h);
+                        fixed[q] = spins_out[site[q]] != 0;
+                    }
+                    /* anneal every read */
+                    for (int r = 0; r < R; ++r) {
+                        int8_t* s = f + (int64_t)r * V;
+                        for (int q = 0; q < V; ++q) {
+                            if (fixed[q]) {
+                                s[q] = spins_out[site[q]];
+                            } else {
+                                uint32_t u = philox_word(k0, k1, (uint32_t)centre, OR_SWEEP_INIT,
+                                                         (uint32_t)(8 * q + r / 4), OR_DOMAIN_FRAGMENT, r % 4);
+                                s[q] = (u >> 31) ? -1 : +1;
+                            }
+                        }
+                        for (int sw = 0; sw < S; ++sw)
+                            for (int colour = 0; colour < 2; ++colour)
+                                for (int q = 0; q < V; ++q) {
+                                    const int dx = q % l, dy = (q / l) % l, dz = q / (l * l);
+                                    if (fixed[q] || ((cx + dx - h + cy + dy - h + cz + dz - h) & 1) != colour)
+                                        continue;
+                                    /* local field over the bonds inside the fragment */
+                                    int hf = 0;
+                                    const int dd[3] = {dx, dy, dz};
+                                    for (int d = 0; d < 3; ++d) {
+                                        const int step = d == 0 ? 1 : d == 1 ? l : l * l;
+                                        if (dd[d] + 1 < l) hf += J3[3 * site[q] + d] * s[q + step];
+                                        if (dd[d] > 0) hf += J3[3 * site[q - step] + d] * s[q - step];
+                                    }
+                                    const int x = s[q] * hf;
+                                    int accept = x >= 0;
+                                    if (!accept) {
+                                        const uint32_t u = philox_word(k0, k1, (uint32_t)centre, (uint32_t)sw,
+                                                                       (uint32_t)(8 * q + r / 4),
+                                                                       OR_DOMAIN_FRAGMENT, r % 4);
+                                        accept = u < or_metropolis_threshold(beta[sw], -2 * x);
+                                    }
+                                    if (accept) s[q] = (int8_t)(-s[q]);
+                                }
+                    }
+                    /* the read of lowest fragment energy sets the centre spin */
+                    int best = 0;
+                    int64_t best_e = 0;
+                    for (int r = 0; r < R; ++r) {
+                        const int8_t* s = f + (int64_t)r * V;
+                        int64_t e = 0;
+                        for (int q = 0; q < V; ++q) {
+                            const int dx = q % l, dy = (q / l) % l, dz = q / (l * l);
+                            if (dx + 1 < l) e += (int64_t)J3[3 * site[q] + 0] * s[q] * s[q + 1];
+                            if (dy + 1 < l) e += (int64_t)J3[3 * site[q] + 1] * s[q] * s[q + l];
+                            if (dz + 1 < l) e += (int64_t)J3[3 * site[q] + 2] * s[q] * s[q + l * l];
+                        }
+                        if (r == 0 || e < best_e) {
+                            best = r;
+                            best_e = e;
+                        }
+                    }
+                    spins_out[centre] = f[(int64_t)best * V + (h + l * (h + l * h))];
+                }
+    }
+    *E_out = or_energy(L, J3, spins_out);
+    free(beta); free(f); free(fixed); free(site);
+    return 0;
+}

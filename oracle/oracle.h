@@ -19,8 +19,10 @@ enum {
     OR_DOMAIN_EXCHANGE = 1,   /* counter (rung pair k, sweep, 0, 1)  */
     OR_DOMAIN_GENERATE = 2,   /* counter (tile, 0, 0, 2)              */
     OR_DOMAIN_GAUGE = 3,      /* counter (site, 0, 0, 3)              */
-    OR_DOMAIN_TAIL = 4        /* counter (site, sweep, replica/4, 4): low 24 bits of a draw */
+    OR_DOMAIN_TAIL = 4,       /* counter (site, sweep, replica/4, 4): low 24 bits of a draw */
+    OR_DOMAIN_FRAGMENT = 5    /* counter (centre, sweep, 8*q + read/4, 5): fragment anneals */
 };
+#define OR_FRAGMENT_READS 32
 #define OR_SWEEP_INIT 0xFFFFFFFFu
 
 void or_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4]);
@@ -52,6 +54,9 @@ int or_pt_run(int L, const int8_t* J3, uint64_t seed, uint32_t instance_id,
               int K, int S, double bmin, double bmax,
               int8_t* spins_out, int64_t* E_out, int32_t* perm_out,
               int64_t* minE_out, int64_t* accepts_out);
+
+int or_fragment_run(int L, const int8_t* J3, int l, int S, double b0, double b1, uint64_t seed,
+                    uint32_t instance_id, int8_t* spins_out, int64_t* E_out);
 
 #ifdef __cplusplus
 }

@@ -70,6 +70,7 @@ def lib():
                 "or_init_spin": (ctypes.c_int8, [u64, u32, i64, i32]),
                 "or_sa_run": (i32, [i32, P, u64, u32, i32, dbl, dbl, i32, P, i32, P, P]),
                 "or_pt_run": (i32, [i32, P, u64, u32, i32, i32, dbl, dbl, P, P, P, P, P]),
+                "or_fragment_run": (i32, [i32, P, i32, i32, dbl, dbl, u64, u32, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -213,3 +214,17 @@ def pt_run(L: int, J3: np.ndarray, seed: int, instance_id: int, K: int, S: int,
         raise ValueError(f"or_pt_run failed ({rc})")
     return {"spins": spins, "E": E, "perm": perm, "minE": int(minE.value),
             "accepts": acc[: max(K - 1, 0)]}
+
+
+def fragment_run(L: int, J3: np.ndarray, l: int, S: int, b0: float, b1: float, seed: int = 0,
+                 instance_id: int = 0):
+    """Fragment meta-heuristic with SA fragment anneals (Sec. II, App. A; see
+    or_fragment_run).  -> (spins (N,) int8, E)."""
+    N = L ** 3
+    J3 = np.ascontiguousarray(J3, dtype=np.int8)
+    spins = np.zeros(N, dtype=np.int8)
+    E = ctypes.c_int64()
+    rc = lib().or_fragment_run(L, _p(J3), l, S, b0, b1, seed, instance_id, _p(spins), ctypes.byref(E))
+    if rc != 0:
+        raise ValueError(f"or_fragment_run failed ({rc})")
+    return spins, int(E.value)

@@ -770,6 +770,109 @@ extern "C" int32_t sg_pt_run(const sg_instance* inst, const sg_pt_params* p, sg_
     return sg_pt_run_batch(&inst, p, 1, out, stream);
 }
 
+extern "C" int32_t sg_fragment_run_batch(const sg_instance* const* insts, const sg_fragment_params* ps, int32_t n,
+                                         sg_fragment_result* outs, void* stream)
+{
+    clear_error();
+    if (n < 0 || (n > 0 && (!insts || !ps || !outs))) {
+        set_error("bad batch arguments");
+        return SG_EINVAL;
+    }
+    if (n == 0) return SG_OK;
+    const sg_fragment_params& p = ps[0];
+    for (int a = 0; a < n; ++a) {
+        if (!insts[a] || !outs) {
+            set_error("NULL instance");
+            return SG_EINVAL;
+        }
+        const sg_fragment_params& q = ps[a];
+        if (insts[a]->L != insts[0]->L || q.l != p.l || q.sweeps != p.sweeps || q.beta0 != p.beta0 ||
+            q.beta1 != p.beta1) {
+            set_error("a fragment batch needs one L and one (l, sweeps, beta0, beta1)");
+            return SG_EINVAL;
+        }
+        if (outs[a].spins && outs[a].spins_mem != SG_MEM_HOST && outs[a].spins_mem != SG_MEM_DEVICE) {
+            set_error("bad spins_mem");
+            return SG_EINVAL;
+        }
+    }
+    const int L = insts[0]->L, l = p.l, S = p.sweeps;
+    if (l < 1 || l > 7 || (l % 2) == 0 || l >= L || L % l != 0 || S < 0 || !beta_ok(p.beta0) || !beta_ok(p.beta1)) {
+        set_error("fragment side l must be odd, 1 <= l <= 7, l < L and divide L; sweeps >= 0; betas > 0");
+        return SG_EINVAL;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int I = n;
+    const int64_t N = insts[0]->N;
+    std::vector<double> beta((size_t)std::max(S, 1));
+    beta_schedule(S, p.beta0, p.beta1, 1, beta.data());
+    std::vector<uint32_t> thr((size_t)std::max(S, 1) * kThrRow);
+    for (int s = 0; s < S; ++s) metropolis_row(beta[s], &thr[(size_t)s * kThrRow]);
+    std::vector<RunKeys> keys(I);
+    std::vector<const void*> jp((size_t)I);
+    for (int a = 0; a < I; ++a) {
+        keys[a] = make_key(ps[a].seed, ps[a].instance_id);
+        const uint2* j6 = nullptr;
+        SG_RET(instance_device_j6(const_cast<sg_instance*>(insts[a]), st, &j6, nullptr));
+        jp[a] = j6;
+    }
+    DevBuf d_spins, d_thr, d_keys, d_j6, d_words, d_E64, d_bad, d_one;
+    SG_RET(d_spins.alloc((size_t)I * N, st));
+    SG_RET(d_thr.alloc(sizeof(uint32_t) * thr.size(), st));
+    SG_RET(d_keys.alloc(sizeof(RunKeys) * I, st));
+    SG_RET(d_j6.alloc(sizeof(void*) * I, st));
+    SG_RET(d_words.alloc((size_t)N * 4, st));
+    SG_RET(d_E64.alloc(sizeof(unsigned long long) * 32 * (size_t)I, st));
+    SG_RET(d_bad.alloc(sizeof(int), st));
+    SG_TRY_CUDA(cudaMemcpyAsync(d_thr.as<void>(), thr.data(), sizeof(uint32_t) * thr.size(), cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(d_keys.as<void>(), keys.data(), sizeof(RunKeys) * I, cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemcpyAsync(d_j6.as<void>(), jp.data(), sizeof(void*) * I, cudaMemcpyHostToDevice, st));
+    SG_TRY_CUDA(cudaMemsetAsync(d_spins.as<void>(), 0, (size_t)I * N, st));
+    SG_TRY_CUDA(cudaMemsetAsync(d_E64.as<void>(), 0, sizeof(unsigned long long) * 32 * (size_t)I, st));
+    SG_TRY_CUDA(cudaMemsetAsync(d_bad.as<void>(), 0, sizeof(int), st));
+    LaunchLog log;
+    const int64_t V = (int64_t)l * l * l;
+    // attempts: wave w anneals V - w free sites of each of N / V fragments, 32 reads, S sweeps
+    const int64_t attempts = (int64_t)I * N * 32 * S * (V + 1) / 2;
+    SG_RET(log.run(SG_KERNEL_SWEEP, attempts, st, [&] {
+        return launch_fragment_waves(d_spins.as<int8_t>(), d_j6.as<const uint2*>(), d_keys.as<RunKeys>(),
+                                     d_thr.as<uint32_t>(), I, L, l, S, st);
+    }, V));
+    // energies (Eq. 1): each configuration packed as one word of a single replica
+    for (int a = 0; a < I; ++a) {
+        SG_RET(log.run(SG_KERNEL_OTHER, N, st, [&] {
+            return launch_pack_spins(d_spins.as<int8_t>() + (size_t)a * N, d_words.as<int8_t>(), L, 32, 1,
+                                     d_bad.as<int>(), st);
+        }));
+        SG_RET(log.run(SG_KERNEL_ENERGY, N, st, [&] {
+            return launch_energy(d_words.as<int8_t>(), d_j6.as<const uint2*>() + a, 1, L, 1,
+                                 d_E64.as<unsigned long long>() + 32 * (size_t)a, st);
+        }));
+    }
+    std::vector<unsigned long long> E64((size_t)32 * I);
+    SG_TRY_CUDA(cudaMemcpyAsync(E64.data(), d_E64.as<void>(), sizeof(unsigned long long) * E64.size(),
+                                cudaMemcpyDeviceToHost, st));
+    for (int a = 0; a < I; ++a)
+        if (outs[a].spins)
+            SG_TRY_CUDA(cudaMemcpyAsync(outs[a].spins, d_spins.as<int8_t>() + (size_t)a * N, (size_t)N,
+                                        outs[a].spins_mem == SG_MEM_DEVICE ? cudaMemcpyDeviceToDevice
+                                                                           : cudaMemcpyDeviceToHost,
+                                        st));
+    SG_TRY_CUDA(cudaStreamSynchronize(st));
+    log.finish();
+    for (int a = 0; a < I; ++a) {
+        outs[a].E = (int64_t)(long long)E64[(size_t)32 * a];
+        outs[a].eps = eps_of(outs[a].E, insts[a]->e_gs);
+    }
+    return SG_OK;
+}
+
+extern "C" int32_t sg_fragment_run(const sg_instance* inst, const sg_fragment_params* p, sg_fragment_result* out,
+                                   void* stream)
+{
+    return sg_fragment_run_batch(&inst, p, 1, out, stream);
+}
+
 extern "C" int32_t sg_energy(const sg_instance* inst_c, const int8_t* spins, int32_t n_configs,
                              int32_t mem_kind, int64_t* E_out, void* stream)
 {

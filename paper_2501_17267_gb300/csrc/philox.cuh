@@ -67,6 +67,7 @@ constexpr uint32_t kDomainExchange = 1;
 constexpr uint32_t kDomainGenerate = 2;
 constexpr uint32_t kDomainGauge = 3;
 constexpr uint32_t kDomainTail = 4;  // low 24 bits of a Metropolis draw, counter (site, sweep, word, 4)
+constexpr uint32_t kDomainFragment = 5;  // fragment anneals, counter (centre, sweep, 8q + read/4, 5)
 constexpr uint32_t kSweepInit = 0xFFFFFFFFu;
 
 }  // namespace sg

@@ -202,6 +202,10 @@ int32_t launch_sa_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const Ru
 int sa_cluster_list_blocks(const int* Ls, int n, int max_L);
 int32_t launch_sa_cluster_planes(const Plane* d_planes, const int* d_order, int n, unsigned* d_next, int C,
                                  int max_L, cudaStream_t st);
+// fragment.cu: the fragment meta-heuristic's waves (one launch per wave) on [I][N] int8 spins
+// (0 = not fixed yet; all fixed on return), thr: [S][kThrRow] geometric schedule.
+int32_t launch_fragment_waves(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys, const uint32_t* thr,
+                              int I, int L, int l, int S, cudaStream_t st);
 int32_t launch_pt_exchange(const ExchangeArgs& x, int I, uint32_t sweep, cudaStream_t st);
 int32_t launch_pt_setup(const unsigned long long* E64, int32_t* E, uint8_t* rung_of_slot,
                         uint8_t* slot_of_rung, unsigned long long* accepts, int32_t* minE,

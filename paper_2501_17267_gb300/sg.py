@@ -61,6 +61,15 @@ class PTResult(ctypes.Structure):
                 ("min_eps", ctypes.c_double), ("spins", _P), ("spins_mem", ctypes.c_int32)]
 
 
+class FragmentParams(ctypes.Structure):
+    _fields_ = [("l", ctypes.c_int32), ("sweeps", ctypes.c_int32), ("beta0", ctypes.c_double),
+                ("beta1", ctypes.c_double), ("instance_id", ctypes.c_uint32), ("seed", ctypes.c_uint64)]
+
+
+class FragmentResult(ctypes.Structure):
+    _fields_ = [("E", ctypes.c_int64), ("eps", ctypes.c_double), ("spins", _P), ("spins_mem", ctypes.c_int32)]
+
+
 KERNEL_KINDS = ("init", "energy", "sweep", "exchange", "other")
 
 
@@ -98,6 +107,8 @@ _SIGS = {
     "sg_pt_run": [_P, ctypes.POINTER(PTParams), ctypes.POINTER(PTResult), _P],
     "sg_pt_run_batch": [_P, _P, ctypes.c_int32, _P, _P],
     "sg_energy": [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P],
+    "sg_fragment_run_batch": [_P, _P, ctypes.c_int32, _P, _P],
+    "sg_fragment_run": [_P, ctypes.POINTER(FragmentParams), ctypes.POINTER(FragmentResult), _P],
     "sg_energy_noalloc": [ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P],
     "sg_version": [],
     "sg_stats_enable": [ctypes.c_int32],
@@ -271,6 +282,39 @@ def sa_run(inst: Instance, replicas: int, sweeps: int, beta0: float, beta1: floa
     p = dict(replicas=replicas, sweeps=sweeps, beta0=beta0, beta1=beta1, schedule=schedule,
              seed=seed, instance_id=instance_id)
     return sa_run_batch([inst], [p], spins=[spins], stream=stream)[0]
+
+
+def fragment_run_batch(insts, params, spins=None, stream=None):
+    """The fragment meta-heuristic (Sec. II; App. A) with SA fragment anneals, on
+    instances of one side L.  params: list of dicts with keys l, sweeps, beta0, beta1,
+    seed, instance_id (l, sweeps and betas equal across the batch).  spins: None,
+    'host', 'device' or a list of per-instance targets.  Returns a list of dicts
+    {E, eps, spins}."""
+    n = len(insts)
+    handles = (_P * n)(*[i.handle.value for i in insts])
+    ps = (FragmentParams * n)(*[FragmentParams(p["l"], p["sweeps"], p["beta0"], p["beta1"],
+                                               p.get("instance_id", 0), p.get("seed", 0)) for p in params])
+    outs = (FragmentResult * n)()
+    keep = []
+    for a, inst in enumerate(insts):
+        tgt = spins[a] if isinstance(spins, (list, tuple)) else spins
+        obj, ptr, mem = _spins_target(tgt, 1, inst.N)
+        outs[a] = FragmentResult(0, 0.0, ptr, mem)
+        keep.append(obj)
+    _check(_lib.sg_fragment_run_batch(handles, ps, n, outs, _stream_handle(stream)))
+    res = []
+    for a in range(n):
+        sp = keep[a]
+        if sp is not None:
+            sp = sp.reshape(-1)
+        res.append({"E": int(outs[a].E), "eps": float(outs[a].eps), "spins": sp})
+    return res
+
+
+def fragment_run(inst: Instance, l: int, sweeps: int, beta0: float, beta1: float, seed: int = 0,
+                 instance_id: int = 0, spins=None, stream=None):
+    p = dict(l=l, sweeps=sweeps, beta0=beta0, beta1=beta1, seed=seed, instance_id=instance_id)
+    return fragment_run_batch([inst], [p], spins=[spins], stream=stream)[0]
 
 
 def pt_run_batch(insts, params, spins=None, stream=None):
