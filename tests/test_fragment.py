@@ -138,3 +138,10 @@ def test_fragment_batch_equals_separate_runs(sg):
         assert np.array_equal(one["spins"], b["spins"]) and one["E"] == b["E"]
     with pytest.raises(sg.SGError):
         sg.fragment_run(insts[0], 3, 4, 0.5, 6.0)  # 3 does not divide 10
+
+
+def test_fit_inverse_L_recovers_the_asymptote():
+    from paper_2501_17267_gb300 import fragments
+    Ls = [10, 20, 30, 40, 50]
+    a, b = fragments.fit_inverse_L(Ls, [0.4 / L + 0.031 for L in Ls])
+    assert a == pytest.approx(0.4) and b == pytest.approx(0.031)
