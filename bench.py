@@ -499,6 +499,82 @@ def sa_line(sg, args, torch, clocks_cls, local):
                     "max": float(max(eps))}}
 
 
+# ---------------------------------------------------------------- fragment meta-heuristic leg
+
+FRAG = dict(L=50, l=5, sweeps=20, beta0=0.5, beta1=6.0, instances=20)
+# a fragment site's draws: one Philox4x32-10 block (20 multiplies) serves 4 reads, at most
+FRAG_MULS_PER_ATTEMPT = 5.0
+
+
+def fragment_line(sg, args, torch, clocks_cls, local):
+    """The fragment meta-heuristic (Sec. II) with SA fragment anneals: 20 F6 instances at
+    L = 50, cubes of side 5, 20 sweeps of 32 reads per fragment; a step is one
+    sg_fragment_run_batch (125 wave launches).  The oracle is timed beside it on one
+    L = 10 instance (same per-attempt work)."""
+    f = FRAG
+    insts = [sg.Instance.create(f["L"], 9 * 10 ** 6 + 1000 * f["L"] + k, (0, 0, 1), True)
+             for k in range(f["instances"])]
+    params = [dict(l=f["l"], sweeps=f["sweeps"], beta0=f["beta0"], beta1=f["beta1"], seed=1, instance_id=k)
+              for k in range(f["instances"])]
+    V = f["l"] ** 3
+    attempts = f["instances"] * f["L"] ** 3 * 32 * f["sweeps"] * (V + 1) / 2
+    stream = torch.cuda.current_stream()
+    steps = max(args.steps, 3)
+    clocks = clocks_cls(local)
+    clocks.start()
+    flush = _l2_flusher(torch)
+    for _ in range(max(args.warmup, 3)):
+        flush()
+        out = sg.fragment_run_batch(insts, params)
+    sg.stats_read(reset=True)
+    sg.stats_enable(True)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks.mark()
+    ev0.record(stream)
+    for _ in range(steps):
+        flush()
+        out = sg.fragment_run_batch(insts, params)
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    sg.stats_enable(False)
+    st = sg.stats_read(reset=True)
+    ms = ev0.elapsed_time(ev1)
+    sw = st["sweep"]
+    peak, peak_kind, sm_mhz = _peaks()
+    sms = torch.cuda.get_device_properties(local).multi_processor_count
+    roof = None
+    if sw["launches"] and sw["device_ms"] > 0:
+        rate = sw["units"] / (sw["device_ms"] / 1000.0)
+        mul_peak = sms * WIDE_MULS_PER_SM_CLOCK * sm_mhz * 1e6 / 1e12
+        tmul = rate * FRAG_MULS_PER_ATTEMPT / 1e12
+        roof = {"bound": "alu", "achieved": tmul, "peak": mul_peak, "unit": "T 32x32->64-bit multiplies/s",
+                "frac": tmul / mul_peak, "muls_per_attempt": FRAG_MULS_PER_ATTEMPT,
+                "peak_source": f"derived: {sms} SMs x {WIDE_MULS_PER_SM_CLOCK} multiplies per clock at {sm_mhz:.0f} MHz",
+                "attempts_per_s": rate, "kernel": "fragment_wave_kernel", "traffic": None,
+                "launch_ms": sw["device_ms"] / sw["launches"], "share_of_step": sw["device_ms"] / ms,
+                "note": "reads updated one by one (fragments may hold |J| = 2 or 0 bonds and cube boundaries); "
+                        "muls_per_attempt is the most the draws can cost"}
+    cpu = None
+    if not args.no_cpu:
+        from oracle import oracle as o
+        J3, _, _ = o.generate(10, 7, (0, 0, 1), True)
+        t0 = time.perf_counter()
+        o.fragment_run(10, J3, f["l"], f["sweeps"], f["beta0"], f["beta1"], 1, 0)
+        dt = time.perf_counter() - t0
+        cpu = {"value": 10 ** 3 * 32 * f["sweeps"] * (V + 1) / 2 / dt, "unit": UNIT, "cores": 1, "kind": "oracle",
+               "sample": f"one F6 instance at L = 10, same l, sweeps and schedule ({dt:.1f} s, one core)"}
+    eps = [r["eps"] for r in out]
+    return {"metric": METRIC, "value": attempts * steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1,
+            "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
+            "config": {"workload": "fragment_F6_L50_l5_S20", **f,
+                       "cache": "L2 flushed (256 MB written) before every timed step"},
+            "roofline": roof, "cpu_baseline": cpu, "gpu_launches": sum(v["launches"] for v in st.values()),
+            "clocks": clk, "mean_eps": float(sum(eps) / len(eps))}
+
+
 # ---------------------------------------------------------------- GPU leg
 
 def main():
@@ -513,7 +589,7 @@ def main():
     ap.add_argument("--ref-sweeps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--workload", default="pt", choices=["pt", "serving", "batched", "sa"],
+    ap.add_argument("--workload", default="pt", choices=["pt", "serving", "batched", "sa", "fragment"],
                     help="pt: the PT throughput line (with a short serving leg); serving: the "
                          "serving stream alone; batched: 512 uneven SA instances in one launch; "
                          "sa: SA throughput at L=16 with 1024 replicas")
@@ -569,9 +645,9 @@ def main():
         if world > 1:
             torch.distributed.barrier()
 
-    if args.workload in ("batched", "sa"):
+    if args.workload in ("batched", "sa", "fragment"):
         if rank == 0:
-            fn = batched_line if args.workload == "batched" else sa_line
+            fn = {"batched": batched_line, "sa": sa_line, "fragment": fragment_line}[args.workload]
             print(json.dumps(fn(sg, args, torch, ClockSampler, local)), flush=True)
         barrier()
         if world > 1:
