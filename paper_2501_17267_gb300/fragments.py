@@ -45,6 +45,34 @@ def gap_vs_L(sg, Ls, l: int = 5, sweeps: int = 20, beta0: float = 0.5, beta1: fl
     return rows, dict(a=a, eps_lin=b)
 
 
+def gallus_class_prob(family: str, p6: float):
+    """Tile-class probabilities (F22, F42, F6) of the paper's families (Sec. II): gallus_26
+    mixes F22 and F6, gallus_46 mixes F42 and F6, p6 being the F6 share."""
+    if family == "gallus_26":
+        return (1.0 - p6, 0.0, p6)
+    if family == "gallus_46":
+        return (0.0, 1.0 - p6, p6)
+    raise ValueError(family)
+
+
+def gap_vs_p6(sg, p6s, families=("gallus_26", "gallus_46"), L: int = 30, l: int = 5, sweeps: int = 20,
+              beta0: float = 0.5, beta1: float = 6.0, instances: int = 20, seed_base: int = 8 * 10 ** 6):
+    """Mean gap per family and p6 at one L (the paper's Fig. 1 experiment)."""
+    rows = []
+    for fi, fam in enumerate(families):
+        for pi, p6 in enumerate(p6s):
+            insts = [sg.Instance.create(L, seed_base + 10 ** 5 * fi + 1000 * pi + k, gallus_class_prob(fam, p6), True)
+                     for k in range(instances)]
+            params = [dict(l=l, sweeps=sweeps, beta0=beta0, beta1=beta1, seed=1, instance_id=k)
+                      for k in range(instances)]
+            res = sg.fragment_run_batch(insts, params)
+            eps = np.array([r["eps"] for r in res])
+            rows.append(dict(family=fam, p6=p6, mean_eps=float(eps.mean()), std_eps=float(eps.std())))
+            for i in insts:
+                i.close()
+    return rows
+
+
 def main(argv=None):
     import argparse
     import json
@@ -56,10 +84,20 @@ def main(argv=None):
     ap.add_argument("--beta0", type=float, default=0.5)
     ap.add_argument("--beta1", type=float, default=6.0)
     ap.add_argument("--instances", type=int, default=20)
+    ap.add_argument("--gallus", action="store_true", help="gap vs p6 of gallus_26 / gallus_46 at L = 30")
     args = ap.parse_args(argv)
     from . import sg
 
     out = []
+    if args.gallus:
+        p6s = [round(0.1 * k, 1) for k in range(11)]
+        for S in args.sweeps:
+            rows = gap_vs_p6(sg, p6s, L=30, l=args.l, sweeps=S, beta0=args.beta0, beta1=args.beta1,
+                             instances=args.instances)
+            row = dict(l=args.l, sweeps=S, L=30, points=rows)
+            print(json.dumps(row), flush=True)
+            out.append(row)
+        return out
     for S in args.sweeps:
         rows, fit = gap_vs_L(sg, args.L, args.l, S, args.beta0, args.beta1, args.instances)
         row = dict(l=args.l, sweeps=S, beta0=args.beta0, beta1=args.beta1, points=rows, fit=fit)

@@ -145,3 +145,12 @@ def test_fit_inverse_L_recovers_the_asymptote():
     Ls = [10, 20, 30, 40, 50]
     a, b = fragments.fit_inverse_L(Ls, [0.4 / L + 0.031 for L in Ls])
     assert a == pytest.approx(0.4) and b == pytest.approx(0.031)
+
+
+def test_gallus_families_mix_the_stated_classes():
+    from paper_2501_17267_gb300 import fragments
+    assert fragments.gallus_class_prob("gallus_26", 0.8) == pytest.approx((0.2, 0.0, 0.8))
+    assert fragments.gallus_class_prob("gallus_46", 0.8) == pytest.approx((0.0, 0.2, 0.8))
+    assert fragments.gallus_class_prob("gallus_26", 1.0) == fragments.gallus_class_prob("gallus_46", 1.0)
+    with pytest.raises(ValueError):
+        fragments.gallus_class_prob("gallus_22", 0.5)
