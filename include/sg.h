@@ -177,6 +177,15 @@ int32_t sg_fragment_run_batch(const sg_instance* const* insts, const sg_fragment
 int32_t sg_fragment_run(const sg_instance* inst, const sg_fragment_params* p, sg_fragment_result* out,
                         void* stream);
 
+/* The same waves and cubes with the centre spin set by the exact zero-temperature
+ * (tropical) marginal of its cube, the limit beta -> infinity of the paper's
+ * tensor-network fragment contraction (App. A; the tropical form is suggested in
+ * Sec. III): the lowest cube energy over the cube's free spins with s_c = +1 is compared
+ * with that with s_c = -1 (+1 on a tie), by enumerating all states of the free spins.
+ * Only p->l is used, l in {1, 3} (at most 27 free spins).  Errors as sg_fragment_run. */
+int32_t sg_fragment_tropical_run_batch(const sg_instance* const* insts, const sg_fragment_params* p, int32_t n,
+                                       sg_fragment_result* outs, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Parallel tempering (App. D.2).                                            */
 /* ------------------------------------------------------------------------ */

@@ -590,3 +590,106 @@ int or_fragment_run(int L, const int8_t* J3, int l, int S, double b0, double b1,
     free(beta); free(f); free(fixed); free(site);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Exact fragment decimation in the zero-temperature (tropical) limit:      */
+/* the tensor-network step of App. A with the fragment contracted exactly   */
+/* by enumeration.                                                          */
+/* ------------------------------------------------------------------------ */
+
+/* Free spins k = 0 .. F-1 with fields h[k] and couplings Jff[k*F + j] (symmetric, zero
+ * diagonal); energy E(s) = sum_k h_k s_k + sum_{k<j} Jff[k][j] s_k s_j.  m_plus / m_minus:
+ * the lowest energy over the states with s_c = +1 / -1.  Enumerates all 2^F states in
+ * Gray-code order (state g = n ^ (n >> 1), bit k set: s_k = -1), each energy obtained
+ * from the previous one by the change of the one spin that flips. */
+int or_fragment_min_energies(int F, const int* h, const int8_t* Jff, int c, int64_t* m_plus, int64_t* m_minus)
+{
+    if (F < 1 || F > 30 || c < 0 || c >= F) return -1;
+    int8_t s[32];
+    int nn[32], nj[32][32];  /* the spins coupled to spin k */
+    int8_t nJ[32][32];
+    int64_t E = 0;
+    for (int k = 0; k < F; ++k) {
+        s[k] = 1;
+        E += h[k];
+        nn[k] = 0;
+        for (int j = 0; j < F; ++j)
+            if (j != k && Jff[k * F + j] != 0) {
+                nj[k][nn[k]] = j;
+                nJ[k][nn[k]++] = Jff[k * F + j];
+            }
+    }
+    for (int k = 0; k < F; ++k)
+        for (int j = k + 1; j < F; ++j) E += Jff[k * F + j];
+    int64_t mp = E, mm = INT64_MAX;
+    const uint64_t total = (uint64_t)1 << F;
+    for (uint64_t n = 1; n < total; ++n) {
+        int k = 0;
+        while (!((n >> k) & 1u)) ++k;  /* the bit that changes from g(n-1) to g(n) */
+        int64_t field = h[k];
+        for (int t = 0; t < nn[k]; ++t) field += (int64_t)nJ[k][t] * s[nj[k][t]];
+        E -= 2 * (int64_t)s[k] * field;
+        s[k] = (int8_t)(-s[k]);
+        if (s[c] > 0) {
+            if (E < mp) mp = E;
+        } else {
+            if (E < mm) mm = E;
+        }
+    }
+    *m_plus = mp;
+    *m_minus = mm;
+    return 0;
+}
+
+/* The waves and cubes of or_fragment_run (readings A13, A14), with the centre spin set
+ * by the exact zero-temperature marginal: +1 when the lowest cube energy with s_c = +1
+ * is at most the lowest with s_c = -1, else -1.  Cube sides l <= 3 (2^27 states). */
+int or_fragment_tropical(int L, const int8_t* J3, int l, int8_t* spins_out, int64_t* E_out)
+{
+    if (L < 2 || (L % 2) != 0 || l < 1 || l > 3 || (l % 2) == 0 || (L % l) != 0 || l >= L) return -1;
+    const int64_t N = (int64_t)L * L * L;
+    const int h = (l - 1) / 2, V = l * l * l;
+    int64_t site[27];
+    int idx[27];
+    int hf[27];
+    int8_t Jff[27 * 27];
+    for (int64_t i = 0; i < N; ++i) spins_out[i] = 0;
+    for (int w = 0; w < V; ++w) {
+        const int a = w % l, b = (w / l) % l, c = w / (l * l);
+        for (int cz = c; cz < L; cz += l)
+            for (int cy = b; cy < L; cy += l)
+                for (int cx = a; cx < L; cx += l) {
+                    int F = 0, cf = -1;
+                    for (int q = 0; q < V; ++q) {
+                        const int dx = q % l, dy = (q / l) % l, dz = q / (l * l);
+                        site[q] = or_site(L, cx + dx - h, cy + dy - h, cz + dz - h);
+                        idx[q] = spins_out[site[q]] != 0 ? -1 : F++;
+                        if (q == h + l * (h + l * h)) cf = idx[q];
+                    }
+                    for (int k = 0; k < F; ++k) hf[k] = 0;
+                    for (int k = 0; k < F * F; ++k) Jff[k] = 0;
+                    /* bonds inside the cube: fixed-free ones become fields */
+                    for (int q = 0; q < V; ++q) {
+                        const int dd[3] = {q % l, (q / l) % l, q / (l * l)};
+                        for (int d = 0; d < 3; ++d) {
+                            const int step = d == 0 ? 1 : d == 1 ? l : l * l;
+                            if (dd[d] + 1 >= l) continue;
+                            const int r = q + step, J = J3[3 * site[q] + d];
+                            if (idx[q] >= 0 && idx[r] >= 0) {
+                                Jff[idx[q] * F + idx[r]] = (int8_t)(Jff[idx[q] * F + idx[r]] + J);
+                                Jff[idx[r] * F + idx[q]] = (int8_t)(Jff[idx[r] * F + idx[q]] + J);
+                            } else if (idx[q] >= 0) {
+                                hf[idx[q]] += J * spins_out[site[r]];
+                            } else if (idx[r] >= 0) {
+                                hf[idx[r]] += J * spins_out[site[q]];
+                            }
+                        }
+                    }
+                    int64_t mp, mm;
+                    if (or_fragment_min_energies(F, hf, Jff, cf, &mp, &mm) != 0) return -3;
+                    spins_out[site[h + l * (h + l * h)]] = mp <= mm ? 1 : -1;
+                }
+    }
+    *E_out = or_energy(L, J3, spins_out);
+    return 0;
+}

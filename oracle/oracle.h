@@ -57,6 +57,8 @@ int or_pt_run(int L, const int8_t* J3, uint64_t seed, uint32_t instance_id,
 
 int or_fragment_run(int L, const int8_t* J3, int l, int S, double b0, double b1, uint64_t seed,
                     uint32_t instance_id, int8_t* spins_out, int64_t* E_out);
+int or_fragment_min_energies(int F, const int* h, const int8_t* Jff, int c, int64_t* m_plus, int64_t* m_minus);
+int or_fragment_tropical(int L, const int8_t* J3, int l, int8_t* spins_out, int64_t* E_out);
 
 #ifdef __cplusplus
 }

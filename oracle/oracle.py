@@ -71,6 +71,8 @@ def lib():
                 "or_sa_run": (i32, [i32, P, u64, u32, i32, dbl, dbl, i32, P, i32, P, P]),
                 "or_pt_run": (i32, [i32, P, u64, u32, i32, i32, dbl, dbl, P, P, P, P, P]),
                 "or_fragment_run": (i32, [i32, P, i32, i32, dbl, dbl, u64, u32, P, P]),
+                "or_fragment_min_energies": (i32, [i32, P, P, i32, P, P]),
+                "or_fragment_tropical": (i32, [i32, P, i32, P, P]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -227,4 +229,28 @@ def fragment_run(L: int, J3: np.ndarray, l: int, S: int, b0: float, b1: float, s
     rc = lib().or_fragment_run(L, _p(J3), l, S, b0, b1, seed, instance_id, _p(spins), ctypes.byref(E))
     if rc != 0:
         raise ValueError(f"or_fragment_run failed ({rc})")
+    return spins, int(E.value)
+
+
+def fragment_min_energies(h, Jff, c: int):
+    """Lowest energy of sum_k h_k s_k + sum_{k<j} Jff[k, j] s_k s_j over the states with
+    s_c = +1 and with s_c = -1 (exact enumeration).  -> (m_plus, m_minus)."""
+    h = np.ascontiguousarray(h, dtype=np.int32)
+    J = np.ascontiguousarray(Jff, dtype=np.int8)
+    mp, mm = ctypes.c_int64(), ctypes.c_int64()
+    rc = lib().or_fragment_min_energies(len(h), _p(h), _p(J), c, ctypes.byref(mp), ctypes.byref(mm))
+    if rc != 0:
+        raise ValueError(f"or_fragment_min_energies failed ({rc})")
+    return int(mp.value), int(mm.value)
+
+
+def fragment_tropical(L: int, J3: np.ndarray, l: int):
+    """Fragment decimation with exact zero-temperature fragment marginals (l <= 3).
+    -> (spins (N,) int8, E)."""
+    J3 = np.ascontiguousarray(J3, dtype=np.int8)
+    spins = np.zeros(L ** 3, dtype=np.int8)
+    E = ctypes.c_int64()
+    rc = lib().or_fragment_tropical(L, _p(J3), l, _p(spins), ctypes.byref(E))
+    if rc != 0:
+        raise ValueError(f"or_fragment_tropical failed ({rc})")
     return spins, int(E.value)

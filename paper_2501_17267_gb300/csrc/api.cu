@@ -770,8 +770,9 @@ extern "C" int32_t sg_pt_run(const sg_instance* inst, const sg_pt_params* p, sg_
     return sg_pt_run_batch(&inst, p, 1, out, stream);
 }
 
-extern "C" int32_t sg_fragment_run_batch(const sg_instance* const* insts, const sg_fragment_params* ps, int32_t n,
-                                         sg_fragment_result* outs, void* stream)
+namespace {
+int32_t fragment_batch(const sg_instance* const* insts, const sg_fragment_params* ps, int32_t n,
+                       sg_fragment_result* outs, void* stream, bool tropical)
 {
     clear_error();
     if (n < 0 || (n > 0 && (!insts || !ps || !outs))) {
@@ -796,16 +797,18 @@ extern "C" int32_t sg_fragment_run_batch(const sg_instance* const* insts, const 
             return SG_EINVAL;
         }
     }
-    const int L = insts[0]->L, l = p.l, S = p.sweeps;
-    if (l < 1 || l > 7 || (l % 2) == 0 || l >= L || L % l != 0 || S < 0 || !beta_ok(p.beta0) || !beta_ok(p.beta1)) {
-        set_error("fragment side l must be odd, 1 <= l <= 7, l < L and divide L; sweeps >= 0; betas > 0");
+    const int L = insts[0]->L, l = p.l, S = tropical ? 0 : p.sweeps;
+    if (l < 1 || l > (tropical ? 3 : 7) || (l % 2) == 0 || l >= L || L % l != 0 ||
+        (!tropical && (S < 0 || !beta_ok(p.beta0) || !beta_ok(p.beta1)))) {
+        set_error("fragment side l must be odd, 1 <= l <= %d, l < L and divide L; sweeps >= 0; betas > 0",
+                  tropical ? 3 : 7);
         return SG_EINVAL;
     }
     cudaStream_t st = (cudaStream_t)stream;
     const int I = n;
     const int64_t N = insts[0]->N;
     std::vector<double> beta((size_t)std::max(S, 1));
-    beta_schedule(S, p.beta0, p.beta1, 1, beta.data());
+    if (S > 0) beta_schedule(S, p.beta0, p.beta1, 1, beta.data());
     std::vector<uint32_t> thr((size_t)std::max(S, 1) * kThrRow);
     for (int s = 0; s < S; ++s) metropolis_row(beta[s], &thr[(size_t)s * kThrRow]);
     std::vector<RunKeys> keys(I);
@@ -832,9 +835,15 @@ extern "C" int32_t sg_fragment_run_batch(const sg_instance* const* insts, const 
     SG_TRY_CUDA(cudaMemsetAsync(d_bad.as<void>(), 0, sizeof(int), st));
     LaunchLog log;
     const int64_t V = (int64_t)l * l * l;
-    // attempts: wave w anneals V - w free sites of each of N / V fragments, 32 reads, S sweeps
-    const int64_t attempts = (int64_t)I * N * 32 * S * (V + 1) / 2;
-    SG_RET(log.run(SG_KERNEL_SWEEP, attempts, st, [&] {
+    // attempts: wave w anneals V - w free sites of each of N / V fragments, 32 reads, S sweeps;
+    // tropical: wave w enumerates 2^(V - w) states of each of N / V fragments
+    int64_t units = (int64_t)I * N * 32 * S * (V + 1) / 2;
+    if (tropical) {
+        units = 0;
+        for (int w = 0; w < V; ++w) units += (int64_t)I * (N / V) * ((int64_t)1 << (V - w));
+    }
+    SG_RET(log.run(SG_KERNEL_SWEEP, units, st, [&] {
+        if (tropical) return launch_fragment_tropical_waves(d_spins.as<int8_t>(), d_j6.as<const uint2*>(), I, L, l, st);
         return launch_fragment_waves(d_spins.as<int8_t>(), d_j6.as<const uint2*>(), d_keys.as<RunKeys>(),
                                      d_thr.as<uint32_t>(), I, L, l, S, st);
     }, V));
@@ -865,6 +874,19 @@ extern "C" int32_t sg_fragment_run_batch(const sg_instance* const* insts, const 
         outs[a].eps = eps_of(outs[a].E, insts[a]->e_gs);
     }
     return SG_OK;
+}
+}  // namespace
+
+extern "C" int32_t sg_fragment_run_batch(const sg_instance* const* insts, const sg_fragment_params* ps, int32_t n,
+                                         sg_fragment_result* outs, void* stream)
+{
+    return fragment_batch(insts, ps, n, outs, stream, false);
+}
+
+extern "C" int32_t sg_fragment_tropical_run_batch(const sg_instance* const* insts, const sg_fragment_params* ps,
+                                                  int32_t n, sg_fragment_result* outs, void* stream)
+{
+    return fragment_batch(insts, ps, n, outs, stream, true);
 }
 
 extern "C" int32_t sg_fragment_run(const sg_instance* inst, const sg_fragment_params* p, sg_fragment_result* out,

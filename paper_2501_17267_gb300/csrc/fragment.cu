@@ -159,6 +159,96 @@ __global__ void __launch_bounds__(kWarps * 32) fragment_wave_kernel(const FragAr
     if (lane == 0) sp[centre] = ((words[h + l * (h + l * h)] >> br) & 1u) ? (int8_t)-1 : (int8_t)1;
 }
 
+// Exact zero-temperature fragment marginals (l <= 3): the centre spin of each fragment
+// is set by comparing the lowest cube energy over the cube's free spins with s_c = +1 and
+// with s_c = -1 (+1 on a tie).  One block per fragment; its threads split the 2^F states
+// of the F free spins into contiguous stretches of the Gray-code order (state g(n) =
+// n ^ (n >> 1)), each energy obtained from the previous one by the flipped spin's change.
+constexpr int kTropBlock = 256;
+
+__global__ void __launch_bounds__(kTropBlock) fragment_tropical_kernel(int8_t* spins, const uint2* const* j6_ptrs,
+                                                                       int L, int l, int wave)
+{
+    __shared__ int s_F, s_cf;
+    __shared__ int s_h[27], s_nn[27];
+    __shared__ int s_nj[27][6], s_nJ[27][6];
+    __shared__ int s_mp[kTropBlock / 32], s_mm[kTropBlock / 32];
+    const int inst = blockIdx.y, tid = threadIdx.x;
+    const int h = (l - 1) / 2, V = l * l * l, per = L / l;
+    const int frag = blockIdx.x;
+    const int ca = wave % l, cb = (wave / l) % l, cc = wave / (l * l);
+    const int cx = ca + l * (frag % per), cy = cb + l * ((frag / per) % per), cz = cc + l * (frag / (per * per));
+    int8_t* __restrict__ sp = spins + (size_t)inst * L * L * L;
+    const uint2* __restrict__ j6 = j6_ptrs[inst];
+    auto site_of = [&](int q) {
+        const int dx = q % l, dy = (q / l) % l, dz = q / (l * l);
+        return ((cx + dx - h + L) % L) + L * (((cy + dy - h + L) % L) + L * ((cz + dz - h + L) % L));
+    };
+    if (tid == 0) {
+        int idx[27];
+        int F = 0;
+        for (int q = 0; q < V; ++q) idx[q] = sp[site_of(q)] != 0 ? -1 : F++;
+        for (int k = 0; k < F; ++k) s_h[k] = 0, s_nn[k] = 0;
+        for (int q = 0; q < V; ++q) {  // bonds inside the cube, each once (+x, +y, +z)
+            const int dd[3] = {q % l, (q / l) % l, q / (l * l)};
+            const uint2 rec = j6[site_of(q)];
+            for (int d = 0; d < 3; ++d) {
+                const int step = d == 0 ? 1 : d == 1 ? l : l * l;
+                if (dd[d] + 1 >= l) continue;
+                const int r = q + step;
+                const int J = coupling(rec, 2 * d);
+                if (idx[q] >= 0 && idx[r] >= 0) {
+                    const int a = idx[q], b = idx[r];
+                    s_nj[a][s_nn[a]] = b, s_nJ[a][s_nn[a]++] = J;
+                    s_nj[b][s_nn[b]] = a, s_nJ[b][s_nn[b]++] = J;
+                } else if (idx[q] >= 0) {
+                    s_h[idx[q]] += J * sp[site_of(r)];
+                } else if (idx[r] >= 0) {
+                    s_h[idx[r]] += J * sp[site_of(q)];
+                }
+            }
+        }
+        s_F = F;
+        s_cf = idx[h + l * (h + l * h)];
+    }
+    __syncthreads();
+    const int F = s_F, cf = s_cf;
+    const uint32_t total = 1u << F;
+    const uint32_t seg = (total + kTropBlock - 1) / kTropBlock;
+    const uint32_t n0 = tid * seg, n1 = min(n0 + seg, total);
+    int mp = 0x7FFFFFFF, mm = 0x7FFFFFFF;
+    if (n0 < total) {
+        uint32_t st = n0 ^ (n0 >> 1);  // bit k set: free spin k is -1
+        auto sv = [&](int k) { return ((st >> k) & 1u) ? -1 : 1; };
+        int E = 0;
+        for (int k = 0; k < F; ++k) {
+            E += s_h[k] * sv(k);
+            for (int t = 0; t < s_nn[k]; ++t)
+                if (s_nj[k][t] > k) E += s_nJ[k][t] * sv(k) * sv(s_nj[k][t]);
+        }
+        if (sv(cf) > 0) mp = E; else mm = E;
+        for (uint32_t n = n0 + 1; n < n1; ++n) {
+            const int k = __ffs(n) - 1;  // the spin that flips from g(n - 1) to g(n)
+            int field = s_h[k];
+            for (int t = 0; t < s_nn[k]; ++t) field += s_nJ[k][t] * sv(s_nj[k][t]);
+            E -= 2 * sv(k) * field;
+            st ^= 1u << k;
+            if (sv(cf) > 0) mp = min(mp, E); else mm = min(mm, E);
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        mp = min(mp, __shfl_xor_sync(0xFFFFFFFFu, mp, o));
+        mm = min(mm, __shfl_xor_sync(0xFFFFFFFFu, mm, o));
+    }
+    if ((tid & 31) == 0) s_mp[tid >> 5] = mp, s_mm[tid >> 5] = mm;
+    __syncthreads();
+    if (tid == 0) {
+        for (int k = 1; k < kTropBlock / 32; ++k) mp = min(mp, s_mp[k]), mm = min(mm, s_mm[k]);
+        sp[cx + L * (cy + L * cz)] = mp <= mm ? (int8_t)1 : (int8_t)-1;
+    }
+}
+
 int32_t check(const char* what)
 {
     cudaError_t e = cudaGetLastError();
@@ -188,6 +278,19 @@ int32_t launch_fragment_waves(int8_t* spins, const uint2* const* j6_ptrs, const 
     for (int w = 0; w < l * l * l; ++w) {
         fragment_wave_kernel<<<grid, kWarps * 32, 0, st>>>(a, w);
         const int32_t rc = check("fragment_wave_kernel");
+        if (rc != SG_OK) return rc;
+    }
+    return SG_OK;
+}
+
+int32_t launch_fragment_tropical_waves(int8_t* spins, const uint2* const* j6_ptrs, int I, int L, int l,
+                                       cudaStream_t st)
+{
+    const int per = L / l;
+    const dim3 grid(per * per * per, I);
+    for (int w = 0; w < l * l * l; ++w) {
+        fragment_tropical_kernel<<<grid, kTropBlock, 0, st>>>(spins, j6_ptrs, L, l, w);
+        const int32_t rc = check("fragment_tropical_kernel");
         if (rc != SG_OK) return rc;
     }
     return SG_OK;

@@ -206,6 +206,9 @@ int32_t launch_sa_cluster_planes(const Plane* d_planes, const int* d_order, int 
 // (0 = not fixed yet; all fixed on return), thr: [S][kThrRow] geometric schedule.
 int32_t launch_fragment_waves(int8_t* spins, const uint2* const* j6_ptrs, const RunKeys* keys, const uint32_t* thr,
                               int I, int L, int l, int S, cudaStream_t st);
+// the same waves with exact zero-temperature fragment marginals (l <= 3)
+int32_t launch_fragment_tropical_waves(int8_t* spins, const uint2* const* j6_ptrs, int I, int L, int l,
+                                       cudaStream_t st);
 int32_t launch_pt_exchange(const ExchangeArgs& x, int I, uint32_t sweep, cudaStream_t st);
 int32_t launch_pt_setup(const unsigned long long* E64, int32_t* E, uint8_t* rung_of_slot,
                         uint8_t* slot_of_rung, unsigned long long* accepts, int32_t* minE,

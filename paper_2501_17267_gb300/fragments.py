@@ -23,20 +23,25 @@ def fit_inverse_L(Ls, eps):
 
 
 def gap_vs_L(sg, Ls, l: int = 5, sweeps: int = 20, beta0: float = 0.5, beta1: float = 6.0,
-             instances: int = 20, seed_base: int = 9 * 10 ** 6):
-    """Mean gap and throughput at each L, and the a / L + b fit."""
+             instances: int = 20, seed_base: int = 9 * 10 ** 6, tropical: bool = False):
+    """Mean gap and throughput at each L, and the a / L + b fit.  tropical: exact
+    zero-temperature cube marginals (l <= 3) instead of SA anneals; the rate is then in
+    enumerated cube states per second."""
     rows = []
     for L in Ls:
         insts = [sg.Instance.create(L, seed_base + 1000 * L + k, F6, True) for k in range(instances)]
         params = [dict(l=l, sweeps=sweeps, beta0=beta0, beta1=beta1, seed=1, instance_id=k)
                   for k in range(instances)]
-        sg.fragment_run_batch(insts[:1], params[:1])  # warm-up
+        sg.fragment_run_batch(insts[:1], params[:1], tropical=tropical)  # warm-up
         t0 = time.perf_counter()
-        res = sg.fragment_run_batch(insts, params)
+        res = sg.fragment_run_batch(insts, params, tropical=tropical)
         dt = time.perf_counter() - t0
         eps = np.array([r["eps"] for r in res])
         V = l ** 3
-        attempts = instances * L ** 3 * 32 * sweeps * (V + 1) / 2
+        if tropical:
+            attempts = instances * (L ** 3 // V) * sum(2 ** (V - w) for w in range(V))
+        else:
+            attempts = instances * L ** 3 * 32 * sweeps * (V + 1) / 2
         rows.append(dict(L=L, mean_eps=float(eps.mean()), std_eps=float(eps.std()), seconds=dt,
                          attempts_per_s=attempts / dt, instances=instances))
         for i in insts:
@@ -85,6 +90,7 @@ def main(argv=None):
     ap.add_argument("--beta1", type=float, default=6.0)
     ap.add_argument("--instances", type=int, default=20)
     ap.add_argument("--gallus", action="store_true", help="gap vs p6 of gallus_26 / gallus_46 at L = 30")
+    ap.add_argument("--tropical", action="store_true", help="exact zero-temperature cube marginals (l <= 3)")
     args = ap.parse_args(argv)
     from . import sg
 
@@ -98,6 +104,11 @@ def main(argv=None):
             print(json.dumps(row), flush=True)
             out.append(row)
         return out
+    if args.tropical:
+        rows, fit = gap_vs_L(sg, args.L, args.l, 0, 1.0, 1.0, args.instances, tropical=True)
+        row = dict(l=args.l, tropical=True, points=rows, fit=fit)
+        print(json.dumps(row), flush=True)
+        return [row]
     for S in args.sweeps:
         rows, fit = gap_vs_L(sg, args.L, args.l, S, args.beta0, args.beta1, args.instances)
         row = dict(l=args.l, sweeps=S, beta0=args.beta0, beta1=args.beta1, points=rows, fit=fit)

@@ -108,6 +108,7 @@ _SIGS = {
     "sg_pt_run_batch": [_P, _P, ctypes.c_int32, _P, _P],
     "sg_energy": [_P, _P, ctypes.c_int32, ctypes.c_int32, _P, _P],
     "sg_fragment_run_batch": [_P, _P, ctypes.c_int32, _P, _P],
+    "sg_fragment_tropical_run_batch": [_P, _P, ctypes.c_int32, _P, _P],
     "sg_fragment_run": [_P, ctypes.POINTER(FragmentParams), ctypes.POINTER(FragmentResult), _P],
     "sg_energy_noalloc": [ctypes.c_int32, _P, _P, ctypes.c_int32, _P, _P],
     "sg_version": [],
@@ -284,15 +285,16 @@ def sa_run(inst: Instance, replicas: int, sweeps: int, beta0: float, beta1: floa
     return sa_run_batch([inst], [p], spins=[spins], stream=stream)[0]
 
 
-def fragment_run_batch(insts, params, spins=None, stream=None):
+def fragment_run_batch(insts, params, spins=None, stream=None, tropical=False):
     """The fragment meta-heuristic (Sec. II; App. A) with SA fragment anneals, on
     instances of one side L.  params: list of dicts with keys l, sweeps, beta0, beta1,
     seed, instance_id (l, sweeps and betas equal across the batch).  spins: None,
-    'host', 'device' or a list of per-instance targets.  Returns a list of dicts
-    {E, eps, spins}."""
+    'host', 'device' or a list of per-instance targets.  tropical: the centre spins set
+    by exact zero-temperature cube marginals instead (l in {1, 3}; sweeps and betas
+    unused).  Returns a list of dicts {E, eps, spins}."""
     n = len(insts)
     handles = (_P * n)(*[i.handle.value for i in insts])
-    ps = (FragmentParams * n)(*[FragmentParams(p["l"], p["sweeps"], p["beta0"], p["beta1"],
+    ps = (FragmentParams * n)(*[FragmentParams(p["l"], p.get("sweeps", 0), p.get("beta0", 1.0), p.get("beta1", 1.0),
                                                p.get("instance_id", 0), p.get("seed", 0)) for p in params])
     outs = (FragmentResult * n)()
     keep = []
@@ -301,7 +303,8 @@ def fragment_run_batch(insts, params, spins=None, stream=None):
         obj, ptr, mem = _spins_target(tgt, 1, inst.N)
         outs[a] = FragmentResult(0, 0.0, ptr, mem)
         keep.append(obj)
-    _check(_lib.sg_fragment_run_batch(handles, ps, n, outs, _stream_handle(stream)))
+    fn = _lib.sg_fragment_tropical_run_batch if tropical else _lib.sg_fragment_run_batch
+    _check(fn(handles, ps, n, outs, _stream_handle(stream)))
     res = []
     for a in range(n):
         sp = keep[a]
@@ -315,6 +318,10 @@ def fragment_run(inst: Instance, l: int, sweeps: int, beta0: float, beta1: float
                  instance_id: int = 0, spins=None, stream=None):
     p = dict(l=l, sweeps=sweeps, beta0=beta0, beta1=beta1, seed=seed, instance_id=instance_id)
     return fragment_run_batch([inst], [p], spins=[spins], stream=stream)[0]
+
+
+def fragment_tropical_run(inst: Instance, l: int, spins=None, stream=None):
+    return fragment_run_batch([inst], [dict(l=l)], spins=[spins], stream=stream, tropical=True)[0]
 
 
 def pt_run_batch(insts, params, spins=None, stream=None):

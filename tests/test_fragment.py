@@ -154,3 +154,57 @@ def test_gallus_families_mix_the_stated_classes():
     assert fragments.gallus_class_prob("gallus_26", 1.0) == fragments.gallus_class_prob("gallus_46", 1.0)
     with pytest.raises(ValueError):
         fragments.gallus_class_prob("gallus_22", 0.5)
+
+
+# --------------------------------------------------------------------------- tropical
+
+def test_enumerated_minima_equal_plain_brute_force():
+    """The Gray-code enumeration of or_fragment_min_energies against a direct sum over
+    every state, on random fields and couplings (|J| <= 2, zeros included)."""
+    import itertools
+    rng = np.random.default_rng(0)
+    for F in (1, 2, 5, 9, 11):
+        for _ in range(4):
+            h = rng.integers(-6, 7, F)
+            J = np.zeros((F, F), dtype=np.int8)
+            for k in range(F):
+                for j in range(k + 1, F):
+                    J[k, j] = J[j, k] = rng.integers(-2, 3)
+            c = int(rng.integers(0, F))
+            best = {1: None, -1: None}
+            for st in itertools.product((1, -1), repeat=F):
+                s = np.array(st)
+                e = int(h @ s) + sum(int(J[k, j]) * s[k] * s[j] for k in range(F) for j in range(k + 1, F))
+                if best[s[c]] is None or e < best[s[c]]:
+                    best[s[c]] = e
+            assert o.fragment_min_energies(h, J, c) == (best[1], best[-1])
+
+
+def test_tropical_single_site_fragments_choose_plus_one():
+    """l = 1: no bond inside a cube, both values have energy 0, the tie gives +1."""
+    J3, _, _ = o.generate(4, 3, (1 / 3, 1 / 3, 1 / 3), True)
+    spins, E = o.fragment_tropical(4, J3, 1)
+    assert (spins == 1).all() and E == int(J3.astype(np.int64).sum())
+
+
+def test_tropical_last_wave_spins_follow_their_field_exactly():
+    """l = 3: a last-wave spin is its cube's only free spin, all six neighbours fixed
+    inside the cube: it is +1 exactly when its local field is <= 0."""
+    L = 6
+    J3, _, egs = o.generate(L, 44, (0, 0, 1), True)
+    spins, E = o.fragment_tropical(L, J3, 3)
+    assert E == o.energy(L, J3, spins) and E >= egs
+    for i in range(L ** 3):
+        if _class(L, 3, i) == 26:
+            h = o.local_field(L, J3, spins, i)
+            assert spins[i] == (1 if h <= 0 else -1)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("L,l", [(6, 3), (4, 1)])
+def test_tropical_fragments_match_oracle(sg, L, l):
+    inst = sg.Instance.create(L, 44 if L == 6 else 3, (0, 0, 1), True)
+    J3, _, egs = inst.get()
+    res = sg.fragment_tropical_run(inst, l, spins="host")
+    ospins, oE = o.fragment_tropical(L, J3, l)
+    assert np.array_equal(res["spins"], ospins) and res["E"] == oE
