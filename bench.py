@@ -429,7 +429,8 @@ def batched_line(sg, args, torch, clocks_cls, local):
     roof = None
     if sw["device_ms"] > 0:
         roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), 2.0 / 8.0 + 3.0 / w.replicas, sms, sm_mhz, peak,
-                     peak_kind, traffic=None, kernel="sa_planes_kernel",
+                     peak_kind, traffic=None,
+                     kernel="persistent batch kernel (one plane per block, or per thread-block cluster: autotuned)",
                      launch_ms=sw["device_ms"] / max(sw["launches"], 1))
     value = attempts * args.steps / (ms / 1000.0)
     eps = [float(e) for o in out for e in o["eps"][:4]]
