@@ -671,11 +671,11 @@ def main():
         return
 
     S = args.sweeps
-    base = rank * WORK.instances
-    insts = [sg.Instance.create(WORK.L, WORK.instance_seed(base + k), WORK.class_prob, True)
-             for k in range(WORK.instances)]
+    from paper_2501_17267_gb300 import ranks
+    mine = ranks.rank_units(rank, WORK.instances)  # this rank's instances (weak scaling)
+    insts = [sg.Instance.create(WORK.L, WORK.instance_seed(g), WORK.class_prob, True) for g in mine]
     params = [dict(temps=WORK.temps, sweeps=S, beta_min=WORK.beta_min, beta_max=WORK.beta_max,
-                   seed=WORK.run_seed, instance_id=base + k) for k in range(WORK.instances)]
+                   seed=WORK.run_seed, instance_id=g) for g in mine]
     stream = torch.cuda.current_stream()
 
     def step():
@@ -704,12 +704,9 @@ def main():
     sg.stats_enable(False)
     st = sg.stats_read(reset=True)
     ms = ev0.elapsed_time(ev1)
-    t = torch.tensor([ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-    ms_max = float(t.item())
+    ms_max = ranks.max_over_ranks(ms, device="cuda")
     attempts_per_step = WORK.instances * WORK.temps * WORK.L ** 3 * S
-    value = attempts_per_step * world * args.steps / (ms_max / 1000.0)
+    value = ranks.job_rate(attempts_per_step, world, args.steps, ms_max)
     launches = sum(v["launches"] for v in st.values())
 
     # roofline of the sweep kernel, from its launches' CUDA-event durations in the timed
@@ -751,11 +748,9 @@ def main():
         torch.cuda.synchronize()
         barrier()
         e_s = time.perf_counter() - t0
-        te = torch.tensor([e_s], dtype=torch.float64, device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(te, op=torch.distributed.ReduceOp.MAX)
+        e_max = ranks.max_over_ranks(e_s, device="cuda")
         K = WORK.temps
-        e2e = {"value": attempts_per_step * world * args.steps / float(te.item()), "unit": UNIT,
+        e2e = {"value": ranks.job_rate(attempts_per_step, world, args.steps, 1000.0 * e_max), "unit": UNIT,
                "h2d_bytes_per_step": WORK.instances * 3 * WORK.L ** 3,
                "d2h_bytes_per_step": WORK.instances * (8 * K + 4 * K + 8 * (K - 1) + 8 + 8)}
 
