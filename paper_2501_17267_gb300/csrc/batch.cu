@@ -19,6 +19,7 @@
 
 #include <algorithm>
 #include <chrono>
+#include <filesystem>
 #include <fstream>
 #include <map>
 #include <mutex>
@@ -486,10 +487,10 @@ void tune_store()
 {
     const std::string path = tune_path();
     const size_t slash = path.rfind('/');
-    if (slash != std::string::npos) {
-        const std::string dir = path.substr(0, slash);
-        std::string cmd = "mkdir -p '" + dir + "' 2>/dev/null";
-        if (system(cmd.c_str()) != 0) return;
+    if (slash != std::string::npos && slash > 0) {
+        std::error_code ec;  // the cache is an optimisation: a directory that cannot be made is skipped
+        std::filesystem::create_directories(path.substr(0, slash), ec);
+        if (ec) return;
     }
     std::ofstream f(path);
     if (!f) return;

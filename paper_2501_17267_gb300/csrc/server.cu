@@ -300,7 +300,6 @@ int32_t prepare_request(ScheduleCache& cache, Request* q)
     q->target = inst->e_gs + (int64_t)floor(r.eps_target * (double)abs_gs);
     if (r.kind == SG_REQ_SA) {
         q->mode = q->L <= plane_max_L() ? kPlanes : kRowsSA;
-        if (q->mode == kRowsSA && !rows_kernel_supports(q->Wn)) q->mode = kPlanes;
         const auto key = std::make_tuple(r.sweeps_per_restart, r.beta0, r.beta1, r.schedule);
         std::lock_guard<std::mutex> lock(cache.mu);
         auto it = cache.tables.find(key);
@@ -315,10 +314,6 @@ int32_t prepare_request(ScheduleCache& cache, Request* q)
         q->thr = it->second;
     } else {
         q->mode = kPT;
-        if (!rows_kernel_supports(q->Wn)) {
-            set_error("PT with %d temperatures is not supported", r.width);
-            return SG_EINVAL;
-        }
         const int K = r.width;
         std::vector<double> ladder(K);
         beta_schedule(K, r.beta0, r.beta1, 1, ladder.data());

@@ -170,8 +170,7 @@ int32_t launch_half_sweep_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
                              const ExchangeArgs* xch, unsigned* done, bool* fused,
                              cudaStream_t st);
-// sweep.cu: the bit-sliced sweep kernel, one launch per colour
-bool rows_kernel_supports(int Wn);
+// sweep.cu: the bit-sliced sweep kernel, one launch per colour (any word count)
 // SA variant keeps no energies (the run recomputes them at the end);
 // unit_j: every coupling of the group has |J| = 1.  With sweep_base the sweep index is
 // *sweep_base + sweep, read on the device, and thr_row is the whole [S][kThrRow] table.

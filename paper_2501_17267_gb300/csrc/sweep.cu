@@ -467,8 +467,6 @@ int32_t launch_rows(SweepArgs a, int I, bool unit_j, bool xch, bool* fused, cuda
 
 }  // namespace
 
-bool rows_kernel_supports(int Wn) { return Wn >= 1; }
-
 int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_row, bool unit_j, int I, int L, int Wn, int R,
