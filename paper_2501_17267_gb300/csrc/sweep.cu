@@ -22,6 +22,14 @@
 // update (kept in bit-sliced vertical counters, reduced through a warp bit transpose).
 // The colour-0 launch clears E; the block that finishes the colour-1 launch last for an
 // instance performs that instance's replica exchange (exchange.cuh).
+//
+// Consecutive launches overlap through programmatic dependent launch: every launch waits
+// for its predecessor to complete (griddepcontrol.wait) before it reads spins, energies or
+// the slot permutation, and only then lets its successor launch.  The successor's blocks
+// take the SMs its predecessor's blocks leave during their tail, so the launch gap and,
+// in a colour-1 launch, the threshold-table setup are hidden: that setup reads only the
+// slot permutation, last written by the exchange two launches back, which has completed
+// when the successor's launch is allowed.
 #include <stdint.h>
 #include <stdlib.h>
 
@@ -65,6 +73,11 @@ struct SweepArgs {
     const uint32_t* sweep_base;   // if set, the sweep index is *sweep_base + sweep
 };
 
+// Programmatic dependent launch (PTX griddepcontrol, sm_90 and later).  Both are no-ops
+// in a launch made without the programmatic-serialization attribute.
+__device__ __forceinline__ void wait_for_predecessor() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void allow_successor() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 __device__ __forceinline__ uint32_t valid_bits(int Rvalid, int w)
 {
     const int left = Rvalid - 32 * w;
@@ -92,7 +105,12 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
     const int H = L >> 1;
     const int LL = L * L;
     const RunKeys key = a.keys[inst];
-    const uint32_t sweep = a.sweep + (a.sweep_base ? *a.sweep_base : 0u);
+    // a colour-1 PT launch sets up its tables first (see the file comment); every other
+    // launch reads its predecessor's results from the start
+    if constexpr (!ENERGY) {
+        wait_for_predecessor();
+        allow_successor();
+    }
     uint32_t* __restrict__ s = a.spins + (size_t)inst * (size_t)LL * L * Wn;
     const uint8_t* __restrict__ j1 = UNITJ ? a.j1_ptrs[inst] : nullptr;
     const int nthreads = blockDim.x * blockDim.y;
@@ -110,7 +128,8 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
             for (int q = tid; q < Rp; q += nthreads) a.E[(size_t)inst * Rp + q] = 0;
     } else {
         // with a device sweep index, thr is the run's [S][kThrRow] schedule table
-        const uint32_t* row = a.sweep_base ? a.thr + (size_t)sweep * kThrRow : a.thr;
+        const uint32_t* row =
+            a.sweep_base ? a.thr + (size_t)(a.sweep + *a.sweep_base) * kThrRow : a.thr;
         for (int q = tid; q < kThrRow; q += nthreads) s_thr[q] = row[q];
     }
     if (tid < 8) s_tie_n[tid] = 0;
@@ -132,6 +151,11 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
         }
         __syncthreads();
     }
+    if constexpr (ENERGY) {
+        wait_for_predecessor();
+        allow_successor();
+    }
+    const uint32_t sweep = a.sweep + (a.sweep_base ? *a.sweep_base : 0u);
 
     const int g = threadIdx.x % G;
     const int j0 = threadIdx.x / G;
@@ -443,21 +467,37 @@ int32_t launch_rows(SweepArgs a, int I, bool unit_j, bool xch, bool* fused, cuda
     a.Lmagic = (uint32_t)((0x100000000ull + (uint64_t)a.L - 1) / (uint64_t)a.L);
     // one (site, word) item per thread and row: the whole colour half row of all words
     const bool pipe = unit_j && sh.G == a.Wn && (int)sh.block.x == sh.G * (a.L / 2);
+    // programmatic dependent launch (knob SG_PDL = 0 launches plainly)
+    static const bool pdl = [] {
+        const char* k = getenv("SG_PDL");
+        return !(k && atoi(k) == 0);
+    }();
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = sh.grid;
+    cfg.blockDim = sh.block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaError_t e;
     if (!unit_j) {
-        if (!energy) sweep_bits_kernel<PT, false, false, false, false><<<sh.grid, sh.block, 0, st>>>(a);
-        else if (xch) sweep_bits_kernel<PT, false, PT, PT, false><<<sh.grid, sh.block, 0, st>>>(a);
-        else sweep_bits_kernel<PT, false, PT, false, false><<<sh.grid, sh.block, 0, st>>>(a);
+        if (!energy) e = cudaLaunchKernelEx(&cfg, sweep_bits_kernel<PT, false, false, false, false>, a);
+        else if (xch) e = cudaLaunchKernelEx(&cfg, sweep_bits_kernel<PT, false, PT, PT, false>, a);
+        else e = cudaLaunchKernelEx(&cfg, sweep_bits_kernel<PT, false, PT, false, false>, a);
     } else if (pipe) {
-        if (!energy) sweep_bits_kernel<PT, true, false, false, true><<<sh.grid, sh.block, 0, st>>>(a);
-        else if (xch) sweep_bits_kernel<PT, true, PT, PT, true><<<sh.grid, sh.block, 0, st>>>(a);
-        else sweep_bits_kernel<PT, true, PT, false, true><<<sh.grid, sh.block, 0, st>>>(a);
+        if (!energy) e = cudaLaunchKernelEx(&cfg, sweep_bits_kernel<PT, true, false, false, true>, a);
+        else if (xch) e = cudaLaunchKernelEx(&cfg, sweep_bits_kernel<PT, true, PT, PT, true>, a);
+        else e = cudaLaunchKernelEx(&cfg, sweep_bits_kernel<PT, true, PT, false, true>, a);
     } else {
-        if (!energy) sweep_bits_kernel<PT, true, false, false, false><<<sh.grid, sh.block, 0, st>>>(a);
-        else if (xch) sweep_bits_kernel<PT, true, PT, PT, false><<<sh.grid, sh.block, 0, st>>>(a);
-        else sweep_bits_kernel<PT, true, PT, false, false><<<sh.grid, sh.block, 0, st>>>(a);
+        if (!energy) e = cudaLaunchKernelEx(&cfg, sweep_bits_kernel<PT, true, false, false, false>, a);
+        else if (xch) e = cudaLaunchKernelEx(&cfg, sweep_bits_kernel<PT, true, PT, PT, false>, a);
+        else e = cudaLaunchKernelEx(&cfg, sweep_bits_kernel<PT, true, PT, false, false>, a);
     }
     if (fused) *fused = energy && xch;
-    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaGetLastError();
     if (e != cudaSuccess) {
         set_error("sweep launch failed: %s", cudaGetErrorString(e));
         return SG_ECUDA;
