@@ -111,6 +111,9 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
         wait_for_predecessor();
         allow_successor();
     }
+    // the device sweep index is advanced between graph chunks, never between the two
+    // colours of a sweep, so a colour-1 launch may read it before its wait too
+    const uint32_t sweep = a.sweep + (a.sweep_base ? *a.sweep_base : 0u);
     uint32_t* __restrict__ s = a.spins + (size_t)inst * (size_t)LL * L * Wn;
     const uint8_t* __restrict__ j1 = UNITJ ? a.j1_ptrs[inst] : nullptr;
     const int nthreads = blockDim.x * blockDim.y;
@@ -128,8 +131,7 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
             for (int q = tid; q < Rp; q += nthreads) a.E[(size_t)inst * Rp + q] = 0;
     } else {
         // with a device sweep index, thr is the run's [S][kThrRow] schedule table
-        const uint32_t* row =
-            a.sweep_base ? a.thr + (size_t)(a.sweep + *a.sweep_base) * kThrRow : a.thr;
+        const uint32_t* row = a.sweep_base ? a.thr + (size_t)sweep * kThrRow : a.thr;
         for (int q = tid; q < kThrRow; q += nthreads) s_thr[q] = row[q];
     }
     if (tid < 8) s_tie_n[tid] = 0;
@@ -155,7 +157,6 @@ __global__ void __launch_bounds__(256, PT && !ENERGY ? SG_SWEEP_MINB : SG_SWEEP_
         wait_for_predecessor();
         allow_successor();
     }
-    const uint32_t sweep = a.sweep + (a.sweep_base ? *a.sweep_base : 0u);
 
     const int g = threadIdx.x % G;
     const int j0 = threadIdx.x / G;
