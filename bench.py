@@ -555,7 +555,8 @@ def fragment_line(sg, args, torch, clocks_cls, local):
                 "peak_source": f"derived: {sms} SMs x {WIDE_MULS_PER_SM_CLOCK} multiplies per clock at {sm_mhz:.0f} MHz",
                 "attempts_per_s": rate, "kernel": "fragment_wave_kernel", "traffic": None,
                 "launch_ms": sw["device_ms"] / sw["launches"], "share_of_step": sw["device_ms"] / ms,
-                "note": "reads updated one by one (fragments may hold |J| = 2 or 0 bonds and cube boundaries); "
+                "note": "bond terms of the 32 reads counted bit-sliced, weighted by |J| (fragments may hold "
+                        "|J| = 2 or 0 bonds and cube boundaries); reads with x < 0 take their draw one by one; "
                         "muls_per_attempt is the most the draws can cost"}
     cpu = None
     if not args.no_cpu:

@@ -5,10 +5,13 @@
 // mod l.  The fragment of such a spin is the cube of side l centred on it; with L a
 // multiple of l the fragments of one wave are disjoint, so one launch anneals all of
 // them.  A warp owns one fragment: its 32 reads are the 32 bits of one word per cube
-// site, kept in shared memory for the whole anneal.  Sites fixed by earlier waves hold
-// all-equal words and are never updated; only bonds inside the cube count.  Bonds may
-// have |J| = 2 or 0, so each read is updated on its own (a fragment is at most 343
-// sites).  The read of lowest cube energy fixes the centre spin in global memory.
+// site, kept in shared memory for the whole anneal, beside the site's couplings (those
+// of bonds leaving the cube cleared) and a list of the free sites of each colour.  Sites
+// fixed by earlier waves hold all-equal words and are never updated.  Bonds may have
+// |J| = 2 or 0: a site's positive bond terms are counted for all 32 reads at once in bit
+// planes weighted by |J|, which gives x = s_i h_i of every read; only the reads with
+// x < 0 take their draw and threshold one by one.  The read of lowest cube energy fixes
+// the centre spin in global memory.
 #include <stdint.h>
 #include <stdio.h>
 
@@ -41,6 +44,8 @@ __device__ __forceinline__ int coupling(uint2 r, int q)
 __global__ void __launch_bounds__(kWarps * 32) fragment_wave_kernel(const FragArgs a, int wave)
 {
     __shared__ uint32_t s_words[kWarps][kVMax];  // bit r: read r's spin is -1
+    __shared__ uint2 s_rec[kWarps][kVMax];       // couplings of the bonds inside the cube (others 0)
+    __shared__ uint16_t s_free[kWarps][2][(kVMax + 1) / 2];  // free sites of each colour
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int inst = blockIdx.y;
     const int L = a.L, l = a.l, h = (l - 1) / 2, V = l * l * l;
@@ -54,6 +59,7 @@ __global__ void __launch_bounds__(kWarps * 32) fragment_wave_kernel(const FragAr
     const uint2* __restrict__ j6 = a.j6_ptrs[inst];
     int8_t* __restrict__ sp = a.spins + (size_t)inst * L * L * L;
     uint32_t* words = s_words[warp];
+    uint2* recs = s_rec[warp];
 
     auto site_of = [&](int q, int* x, int* y, int* z) {
         const int dx = q % l, dy = (q / l) % l, dz = q / (l * l);
@@ -64,65 +70,111 @@ __global__ void __launch_bounds__(kWarps * 32) fragment_wave_kernel(const FragAr
     // fixed by an earlier wave: its residue class precedes this wave's
     auto fixed = [&](int x, int y, int z) { return (x % l) + l * ((y % l) + l * (z % l)) < wave; };
 
-    for (int q = lane; q < V; q += 32) {
-        int x, y, z;
-        site_of(q, &x, &y, &z);
-        const int i = x + L * (y + L * z);
-        uint32_t word = 0;
-        if (fixed(x, y, z)) {
-            word = sp[i] < 0 ? 0xFFFFFFFFu : 0u;
-        } else {
-            for (int g = 0; g < 8; ++g) {
-                const Philox4 r = philox4x32_10(centre, kSweepInit, (uint32_t)(8 * q + g), kDomainFragment, key.k0,
-                                                key.k1);
+    // cube sites: couplings of the bonds inside the cube, initial words, and the list of
+    // the free sites of each colour (compacted by ballot, warp-uniform counts)
+    int nfree[2] = {0, 0};
+    for (int base = 0; base < V; base += 32) {
+        const int q = base + lane;
+        bool free_site = false;
+        int colour = 0;
+        if (q < V) {
+            int x, y, z;
+            site_of(q, &x, &y, &z);
+            const int i = x + L * (y + L * z);
+            const int dd[3] = {q % l, (q / l) % l, q / (l * l)};
+            uint2 r = j6[i];
 #pragma unroll
-                for (int m = 0; m < 4; ++m) word |= (r.v[m] >> 31) << (4 * g + m);
+            for (int d = 0; d < 3; ++d) {
+                const int up = 2 * d, dn = 2 * d + 1;  // record bytes of the +d and -d bonds
+                if (dd[d] + 1 >= l) (up < 4 ? r.x : r.y) &= ~(0xFFu << (8 * (up & 3)));
+                if (dd[d] == 0) (dn < 4 ? r.x : r.y) &= ~(0xFFu << (8 * (dn & 3)));
             }
+            recs[q] = r;
+            uint32_t word = 0;
+            if (fixed(x, y, z)) {
+                word = sp[i] < 0 ? 0xFFFFFFFFu : 0u;
+            } else {
+                free_site = true;
+                colour = (x + y + z) & 1;
+                for (int g = 0; g < 8; ++g) {
+                    const Philox4 u = philox4x32_10(centre, kSweepInit, (uint32_t)(8 * q + g), kDomainFragment,
+                                                    key.k0, key.k1);
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) word |= (u.v[m] >> 31) << (4 * g + m);
+                }
+            }
+            words[q] = word;
         }
-        words[q] = word;
+#pragma unroll
+        for (int c = 0; c < 2; ++c) {
+            const bool mine = free_site && colour == c;
+            const unsigned bal = __ballot_sync(0xFFFFFFFFu, mine);
+            if (mine) s_free[warp][c][nfree[c] + __popc(bal & ((1u << lane) - 1u))] = (uint16_t)q;
+            nfree[c] += __popc(bal);
+        }
     }
     __syncwarp();
 
+    // One site, all 32 reads: with p_k the reads whose bond term J_k s_i s_k is positive,
+    // x = s_i h_i = 2P - M for P = sum |J_k| p_k (kept as bit planes P0..P3) and
+    // M = sum |J_k|.  x >= 0 accepts; the others compare their draw with thr[-x].
     for (int sw = 0; sw < a.S; ++sw) {
         const uint32_t* thr = a.thr + (size_t)sw * kThrRow;
         for (int colour = 0; colour < 2; ++colour) {
-            for (int q = lane; q < V; q += 32) {
-                int x, y, z;
-                site_of(q, &x, &y, &z);
-                if (((x + y + z) & 1) != colour || fixed(x, y, z)) continue;
-                const uint2 rec = j6[x + L * (y + L * z)];
-                const int dd[3] = {q % l, (q / l) % l, q / (l * l)};
-                uint32_t nw[6];
-                int J[6];
-#pragma unroll
-                for (int d = 0; d < 3; ++d) {
-                    const int step = d == 0 ? 1 : d == 1 ? l : l * l;
-                    const bool up = dd[d] + 1 < l, dn = dd[d] > 0;  // bond inside the cube
-                    J[2 * d] = up ? coupling(rec, 2 * d) : 0;
-                    J[2 * d + 1] = dn ? coupling(rec, 2 * d + 1) : 0;
-                    nw[2 * d] = up ? words[q + step] : 0u;
-                    nw[2 * d + 1] = dn ? words[q - step] : 0u;
-                }
+            for (int e = lane; e < nfree[colour]; e += 32) {
+                const int q = s_free[warp][colour][e];
+                const uint2 rec = recs[q];
                 const uint32_t self = words[q];
-                uint32_t flip = 0;
+                uint32_t P0 = 0, P1 = 0, P2 = 0, P3 = 0;
+                int M = 0;
+#pragma unroll
+                for (int k = 0; k < 6; ++k) {
+                    const int J = coupling(rec, k);
+                    if (J == 0) continue;  // no bond (or one leaving the cube)
+                    const int step = k < 2 ? 1 : k < 4 ? l : l * l;
+                    const uint32_t eq = ~(self ^ words[(k & 1) ? q - step : q + step]);
+                    const uint32_t p = J > 0 ? eq : ~eq;
+                    if (J == 1 || J == -1) {  // add p at weight 1
+                        const uint32_t c1 = P0 & p;
+                        P0 ^= p;
+                        const uint32_t c2 = P1 & c1;
+                        P1 ^= c1;
+                        P3 ^= P2 & c2;
+                        P2 ^= c2;
+                        M += 1;
+                    } else {  // |J| = 2: add p at weight 2
+                        const uint32_t c2 = P1 & p;
+                        P1 ^= p;
+                        P3 ^= P2 & c2;
+                        P2 ^= c2;
+                        M += 2;
+                    }
+                }
+                // need: x < 0, i.e. P < T = ceil(M / 2) (borrow of P - T, LSB first)
+                const int T = (M + 1) >> 1;
+                uint32_t need = 0;
+                {
+                    const uint32_t Pj[4] = {P0, P1, P2, P3};
+#pragma unroll
+                    for (int j = 0; j < 4; ++j) {
+                        const uint32_t tm = ((T >> j) & 1) ? 0xFFFFFFFFu : 0u;
+                        need = (~Pj[j] & tm) | (~(Pj[j] ^ tm) & need);
+                    }
+                }
+                uint32_t flip = ~need;
                 for (int g = 0; g < 8; ++g) {  // reads 4g .. 4g + 3
-                    int xs[4];
-                    bool need = false;
+                    const uint32_t nm = (need >> (4 * g)) & 0xFu;
+                    if (!nm) continue;
+                    const Philox4 u =
+                        philox4x32_10(centre, (uint32_t)sw, (uint32_t)(8 * q + g), kDomainFragment, key.k0, key.k1);
 #pragma unroll
                     for (int m = 0; m < 4; ++m) {
+                        if (!((nm >> m) & 1u)) continue;
                         const int b = 4 * g + m;
-                        int hf = 0;
-#pragma unroll
-                        for (int k = 0; k < 6; ++k) hf += J[k] * (((nw[k] >> b) & 1u) ? -1 : 1);
-                        xs[m] = (((self >> b) & 1u) ? -1 : 1) * hf;
-                        need |= xs[m] < 0;
+                        const int Pb = (int)(((P0 >> b) & 1u) | (((P1 >> b) & 1u) << 1) | (((P2 >> b) & 1u) << 2) |
+                                             (((P3 >> b) & 1u) << 3));
+                        if (u.v[m] < thr[M - 2 * Pb]) flip |= 1u << b;
                     }
-                    Philox4 u{};
-                    if (need)
-                        u = philox4x32_10(centre, (uint32_t)sw, (uint32_t)(8 * q + g), kDomainFragment, key.k0, key.k1);
-#pragma unroll
-                    for (int m = 0; m < 4; ++m)
-                        if (xs[m] >= 0 || u.v[m] < thr[-xs[m]]) flip |= 1u << (4 * g + m);
                 }
                 words[q] = self ^ flip;
             }
@@ -135,7 +187,7 @@ __global__ void __launch_bounds__(kWarps * 32) fragment_wave_kernel(const FragAr
     for (int q = 0; q < V; ++q) {
         int x, y, z;
         site_of(q, &x, &y, &z);
-        const uint2 rec = j6[x + L * (y + L * z)];
+        const uint2 rec = recs[q];
         const int dd[3] = {q % l, (q / l) % l, q / (l * l)};
         const int sq = ((words[q] >> lane) & 1u) ? -1 : 1;
 #pragma unroll
