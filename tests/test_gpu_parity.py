@@ -199,6 +199,18 @@ def test_pt_several_words(sg, L, K, S):
     _pt_compare(sg, inst, J3, egs, K, S, 0.2, 3.0, seed=13, iid=1)
 
 
+def test_largest_lattice_side(sg):
+    """L = 256, the largest side the kernels accept (16.8 M sites, 65536 rows of 128 sites
+    per colour; each thread walks about a hundred rows): SA with one replica for two
+    sweeps and PT with two temperatures for one sweep, every spin checked."""
+    inst = sg.Instance.create(256, 9100)
+    J3, _, egs = inst.get()
+    _sa_compare(sg, inst, J3, egs, 1, 2, 0.1, 3.0, seed=3, iid=1)
+    _pt_compare(sg, inst, J3, egs, 2, 1, 0.2, 3.0, seed=3, iid=1)
+    with pytest.raises(sg.SGError):
+        sg.Instance.create(258, 1)
+
+
 def test_sa_rows_wider_than_a_block(sg):
     """L = 58 with 288 replicas: a colour half row holds 29 sites x 9 words, more than
     one 256-thread block row, so threads walk several sites per row (no prefetch)."""
