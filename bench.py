@@ -82,6 +82,20 @@ def _roof(rate, bytes_per_attempt, sms, sm_mhz, peak, peak_kind, **extra):
     return r
 
 
+def _rng_roof(sg, rate, attempts_per_block):
+    """The measured counterpart of the multiply roof: the device's own Philox4x32-10
+    rate (sg_philox_rate, drawing alone, taken after the timed region) times the attempts
+    one block serves."""
+    try:
+        blocks = sg.philox_rate()
+    except Exception as e:  # noqa: BLE001 -- reported, not fatal
+        return {"error": str(e)}
+    top = attempts_per_block * blocks
+    return {"philox_blocks_per_s": blocks, "attempts_per_block": attempts_per_block,
+            "attempts_per_s": top, "frac": rate / top,
+            "source": "measured: Philox4x32-10 alone on this GPU (sg_philox_rate)"}
+
+
 L2_FLUSH_BYTES = 256 << 20  # twice the 129 MB L2
 
 
@@ -431,7 +445,8 @@ def batched_line(sg, args, torch, clocks_cls, local):
         roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), 2.0 / 8.0 + 3.0 / w.replicas, sms, sm_mhz, peak,
                      peak_kind, traffic=None,
                      kernel="persistent batch kernel (one plane per block, or per thread-block cluster: autotuned)",
-                     launch_ms=sw["device_ms"] / max(sw["launches"], 1))
+                     launch_ms=sw["device_ms"] / max(sw["launches"], 1),
+                     rng_roof=_rng_roof(sg, sw["units"] / (sw["device_ms"] / 1000.0), 16))
     value = attempts * args.steps / (ms / 1000.0)
     eps = [float(e) for o in out for e in o["eps"][:4]]
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -486,7 +501,8 @@ def sa_line(sg, args, torch, clocks_cls, local):
                      peak_kind, traffic=None,
                      kernel="sa_cluster_kernel" if sw["launches"] <= 4 * steps else "sweep_bits_kernel<SA>",
                      launch_ms=sw["device_ms"] / sw["launches"], share_of_step=sw["device_ms"] / ms,
-                     note="working set 0.5 MB of spin words: L2-resident, so HBM is not what limits it")
+                     note="working set 0.5 MB of spin words: L2-resident, so HBM is not what limits it",
+                     rng_roof=_rng_roof(sg, sw["units"] / (sw["device_ms"] / 1000.0), 16))
     eps = out["eps"]
     return {"metric": METRIC, "value": attempts * steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1,
             "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / steps,
@@ -557,7 +573,8 @@ def fragment_line(sg, args, torch, clocks_cls, local):
                 "launch_ms": sw["device_ms"] / sw["launches"], "share_of_step": sw["device_ms"] / ms,
                 "note": "bond terms of the 32 reads counted bit-sliced, weighted by |J| (fragments may hold "
                         "|J| = 2 or 0 bonds and cube boundaries); reads with x < 0 take their draw one by one; "
-                        "muls_per_attempt is the most the draws can cost"}
+                        "muls_per_attempt is the most the draws can cost",
+                "rng_roof": _rng_roof(sg, rate, 4)}
     cpu = None
     if not args.no_cpu:
         from oracle import oracle as o
@@ -726,7 +743,8 @@ def main():
                      traffic_unit="DRAM bytes per launch (ncu)",
                      algorithmic_bytes_per_launch=attempts_per_launch * BYTES_PER_ATTEMPT,
                      kernel="sweep_bits_kernel<PT>", launch_ms=1000 * per_launch_s,
-                     attempts_per_launch=attempts_per_launch, share_of_step=sw["device_ms"] / ms)
+                     attempts_per_launch=attempts_per_launch, share_of_step=sw["device_ms"] / ms,
+                     rng_roof=_rng_roof(sg, attempts_per_launch / per_launch_s, 16))
 
     # end to end: host couplings in, results out, inside the timed region
     e2e = None

@@ -368,6 +368,19 @@ int32_t sg_stats_enable(int32_t timing);
 /* Copy the process-wide counters into *out; reset = 1 zeroes them afterwards. */
 int32_t sg_stats_read(sg_kernel_stats* out, int32_t reset);
 
+/* Generator throughput: the rate, in blocks per second, at which this device
+ * produces Philox4x32-10 blocks (Salmon, Moraes, Dror, Shaw, SC'11) when drawing is
+ * all it does.  Every thread of 8 x (SM count) blocks of 256 threads draws
+ * blocks_per_thread blocks (even, >= 2), two independent ones at a time, as a sweep
+ * thread draws its planes.  The Metropolis draws of the SA / PT sweeps (App. D.1,
+ * D.2) take two blocks per word of 32 replicas, so 16 x this rate bounds the attempt
+ * rate of the sweeps' integer work.  One warm-up and one timed launch on `stream`
+ * (a cudaStream_t, NULL for the default stream), timed with CUDA events; returns
+ * once the timed launch has completed.  Allocates 4 bytes per thread, stream-ordered,
+ * freed before returning.
+ * Errors: SG_EINVAL (blocks_per_thread odd or < 2, NULL output), SG_ECUDA. */
+int32_t sg_philox_rate(int32_t blocks_per_thread, double* blocks_per_second, void* stream);
+
 /* ------------------------------------------------------------------------ */
 /* Misc.                                                                     */
 /* ------------------------------------------------------------------------ */

@@ -114,6 +114,7 @@ _SIGS = {
     "sg_version": [],
     "sg_stats_enable": [ctypes.c_int32],
     "sg_stats_read": [ctypes.POINTER(KernelStats), ctypes.c_int32],
+    "sg_philox_rate": [ctypes.c_int32, ctypes.POINTER(ctypes.c_double), _P],
     "sg_server_create": [ctypes.POINTER(ServerConfig), ctypes.POINTER(_P)],
     "sg_submit": [_P, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)],
     "sg_poll": [_P, ctypes.c_uint64, ctypes.c_int32, ctypes.POINTER(Result)],
@@ -383,6 +384,14 @@ def stats_read(reset: bool = False) -> dict:
     _check(_lib.sg_stats_read(ctypes.byref(st), int(bool(reset))))
     return {k: {"launches": int(st.launches[i]), "device_ms": float(st.device_ms[i]),
                 "units": int(st.units[i])} for i, k in enumerate(KERNEL_KINDS)}
+
+
+def philox_rate(blocks_per_thread: int = 4096, stream=None) -> float:
+    """Philox4x32-10 blocks per second this device produces when drawing is all it does
+    (16 x this bounds the sweeps' attempt rate: two blocks per word of 32 replicas)."""
+    out = ctypes.c_double()
+    _check(_lib.sg_philox_rate(int(blocks_per_thread), ctypes.byref(out), _stream_handle(stream)))
+    return out.value
 
 
 def energy_noalloc(L: int, J3_dev, spins_dev, E_dev, stream=None):

@@ -74,3 +74,16 @@ def test_dependent_launch_changes_no_result(tmp_path):
             ospins, oE = o.sa_run(L, J3, seed, iid, S, 0.1, 3.0, True, R=width)
             assert np.array_equal(plain[f"{n}_spins"], ospins)
             assert np.array_equal(plain[f"{n}_E"], oE)
+
+
+def test_generator_rate_is_measured():
+    """sg_philox_rate: a positive, finite block rate; invalid arguments rejected."""
+    from paper_2501_17267_gb300 import build
+    build.build()
+    from paper_2501_17267_gb300 import sg
+    rate = sg.philox_rate(256)
+    assert np.isfinite(rate) and rate > 1e9
+    for bad in (0, 1, 3, -2):
+        with pytest.raises(sg.SGError) as e:
+            sg.philox_rate(bad)
+        assert e.value.code == sg.SG_EINVAL
