@@ -190,8 +190,9 @@ def run_reference(args, rank):
         walls.append(w)
     attempts = WORK.instances * WORK.temps * WORK.L ** 3 * args.ref_sweeps * args.steps
     value = attempts / sum(walls)
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup,
+    # n_gpus is the launch's N, as for the other arm; the oracle itself uses host cores only
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "gpus_used": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": 1000 * sum(walls) / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "u32", "data": "synthetic",
             "config": _config(),
