@@ -25,6 +25,7 @@ import statistics
 import subprocess
 import sys
 import time
+from concurrent.futures import ProcessPoolExecutor
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
@@ -34,7 +35,8 @@ from paper_2501_17267_gb300 import workloads as wl  # noqa: E402
 WORK = wl.PT_L64
 METRIC = "Metropolis spin-flip attempts/s"
 UNIT = "attempts/s"
-# spin bit read + written once per sweep (2/8 B), 3 coupling bytes per site shared by R replicas
+# what the bit-packed sweep kernel moves per attempt: a spin bit read and written once per
+# sweep (2/8 B), 3 coupling bytes per site shared by R replicas
 BYTES_PER_ATTEMPT = 2.0 / 8.0 + 3.0 / WORK.temps
 
 
@@ -48,52 +50,56 @@ def _peaks():
         return 6800.0, "fallback", 2070.0
 
 
-# Roofs of one attempt.  HBM: one spin bit read and one written per sweep plus 3/R B of
-# couplings (bytes_per_attempt).  Integer: the eight leading-byte bit planes of a word of
-# 32 replicas come from two Philox4x32-10 blocks of 20 32x32->64-bit multiplies each,
-# i.e. 1.25 multiplies per attempt (the low 24 bits are drawn for 1/256 of the draws);
-# the SM runs 32 such multiplies per clock.  With bit-packed spins the multiply roof,
-# SMs * 32 / 1.25 attempts per clock, lies below the HBM roof and binds.
-MULS_PER_ATTEMPT = 1.25
+# Roofs of one attempt.  The sweeps are integer work whose fixed core is the draws: the
+# eight leading-byte bit planes of a word of 32 replicas come from two Philox4x32-10
+# blocks of 20 32x32->64-bit multiplies each (the low 24 bits are drawn for 1/256 of the
+# draws only), so 16 attempts per block.  The binding roof is the rate at which this GPU
+# produces Philox blocks when drawing is all it does -- measured by sg_philox_rate -- and
+# `frac` is the kernel's multiply rate over that measured rate.  The nominal figure
+# (SMs x 32 multiplies per clock) is kept beside it for context.  HBM: the spin bytes
+# per attempt as the int8 layout would move them (1 B read + 1 B written + 3/R B of
+# couplings) and as the bit-packed kernel moves them (1/8 + 1/8 + 3/R B); the 55 MB
+# working set of the PT workload stays in L2 either way.
+MULS_PER_BLOCK = 20
 WIDE_MULS_PER_SM_CLOCK = 32
+ATTEMPTS_PER_BLOCK = 16
 
 
-def _roof(rate, bytes_per_attempt, sms, sm_mhz, peak, peak_kind, **extra):
-    """The roofline object for a kernel running `rate` attempts/s: bound by whichever of
-    the two roofs allows fewer attempts per second -- the multiply pipe (Philox draws;
-    derived from the SM count and clock) or HBM (algorithmic bytes against the measured
-    copy bandwidth) -- with the other roof beside it."""
-    gbs = rate * bytes_per_attempt / 1e9
-    tmul = rate * MULS_PER_ATTEMPT / 1e12
-    mul_peak = sms * WIDE_MULS_PER_SM_CLOCK * sm_mhz * 1e6 / 1e12
-    hbm = {"bound": "hbm", "achieved": gbs, "peak": peak, "unit": "GB/s", "frac": gbs / peak,
-           "peak_source": peak_kind, "bytes_per_attempt": bytes_per_attempt}
-    alu = {"bound": "alu", "achieved": tmul, "peak": mul_peak, "unit": "T 32x32->64-bit multiplies/s",
-           "frac": tmul / mul_peak, "muls_per_attempt": MULS_PER_ATTEMPT,
-           "peak_source": f"derived: {sms} SMs x {WIDE_MULS_PER_SM_CLOCK} multiplies per clock "
-                          f"at {sm_mhz:.0f} MHz"}
-    alu_attempts = mul_peak * 1e12 / MULS_PER_ATTEMPT
-    hbm_attempts = peak * 1e9 / bytes_per_attempt
-    main, other = (alu, hbm) if alu_attempts <= hbm_attempts else (hbm, alu)
-    r = dict(main)
-    r["other_roof"] = other
-    r["attempts_per_s"] = rate
+def hbm_views(replicas):
+    return {"int8_layout": 2.0 + 3.0 / replicas, "bit_packed": 2.0 / 8.0 + 3.0 / replicas}
+
+
+def _roof(rate, attempts_per_block, views, blocks_per_s, sms, sm_mhz, hbm_peak, hbm_kind, **extra):
+    """The roofline object of a sweep kernel running `rate` attempts/s: its multiply rate
+    against the measured Philox block rate (blocks_per_s; the nominal peak stands in,
+    marked "derived", when the measurement is missing), with the HBM views beside it."""
+    muls = MULS_PER_BLOCK / attempts_per_block
+    achieved = rate * muls / 1e12
+    derived = sms * WIDE_MULS_PER_SM_CLOCK * sm_mhz * 1e6 / 1e12
+    if blocks_per_s:
+        peak = blocks_per_s * MULS_PER_BLOCK / 1e12
+        src = "measured: Philox4x32-10 alone on this GPU (sg_philox_rate), after the timed region"
+    else:
+        peak = derived
+        src = f"derived: {sms} SMs x {WIDE_MULS_PER_SM_CLOCK} multiplies per clock at {sm_mhz:.0f} MHz"
+    r = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "T 32x32->64-bit multiplies/s",
+         "frac": achieved / peak, "peak_source": src, "muls_per_attempt": muls, "attempts_per_s": rate,
+         "peak_attempts_per_s": peak * 1e12 / muls,
+         "nominal_peak": {"value": derived, "frac": achieved / derived,
+                          "source": f"{sms} SMs x {WIDE_MULS_PER_SM_CLOCK} multiplies per clock at {sm_mhz:.0f} MHz"},
+         "hbm_views": {name: {"bytes_per_attempt": b, "achieved_gbs": rate * b / 1e9, "peak_gbs": hbm_peak,
+                              "frac": rate * b / 1e9 / hbm_peak, "peak_source": hbm_kind}
+                       for name, b in views.items()}}
     r.update(extra)
     return r
 
 
-def _rng_roof(sg, rate, attempts_per_block):
-    """The measured counterpart of the multiply roof: the device's own Philox4x32-10
-    rate (sg_philox_rate, drawing alone, taken after the timed region) times the attempts
-    one block serves."""
+def _philox_blocks_per_s(sg):
+    """The device's Philox4x32-10 block rate when drawing is all it does, or None."""
     try:
-        blocks = sg.philox_rate()
-    except Exception as e:  # noqa: BLE001 -- reported, not fatal
-        return {"error": str(e)}
-    top = attempts_per_block * blocks
-    return {"philox_blocks_per_s": blocks, "attempts_per_block": attempts_per_block,
-            "attempts_per_s": top, "frac": rate / top,
-            "source": "measured: Philox4x32-10 alone on this GPU (sg_philox_rate)"}
+        return sg.philox_rate()
+    except Exception:  # noqa: BLE001 -- the roofline then falls back to the nominal peak
+        return None
 
 
 L2_FLUSH_BYTES = 256 << 20  # twice the 129 MB L2
@@ -143,10 +149,10 @@ def oracle_sample(sweeps: int, workers: int):
     """The oracle, as it stands, on all 16 instances for `sweeps` sweeps, one process
     per instance on `workers` host cores.  Wall time includes each run's initial
     state and energy evaluation."""
-    ctx = mp.get_context("spawn")
     t = time.perf_counter()
-    with ctx.Pool(workers) as pool:
-        pool.map(_oracle_job, [(k, sweeps) for k in range(WORK.instances)])
+    # an executor, not a Pool: a worker that dies raises here instead of hanging the run
+    with ProcessPoolExecutor(workers, mp_context=mp.get_context("spawn")) as ex:
+        list(ex.map(_oracle_job, [(k, sweeps) for k in range(WORK.instances)]))
     wall = time.perf_counter() - t
     attempts = WORK.instances * WORK.temps * WORK.L ** 3 * sweeps
     return attempts / wall, wall
@@ -160,18 +166,39 @@ def cpu_baseline(sweeps: int):
     return {"value": rate, "unit": UNIT, "cores": workers, "kind": "oracle",
             "sample": f"all {WORK.instances} instances, first {sweeps} sweeps of the {WORK.sweeps} "
                       f"(L={WORK.L}, {WORK.temps} temperatures), one spawn process per instance; "
-                      f"{wall:.1f} s wall incl. initial state + energy",
+                      f"{wall:.1f} s wall incl. initial state + energy; rate extrapolated linearly in "
+                      f"sweeps (cost per sweep is constant).  {sweeps} rather than 10^2 sweeps keeps the "
+                      f"default run within minutes; the oracle's 101-sweep runs of all 16 instances are "
+                      f"the parity test's",
             "cpu": _cpu_model()}
 
 
+# CPU part numbers of the Arm cores GPU hosts carry, for hosts whose tools print only the part
+_ARM_PARTS = {"0xd4f": "Neoverse-V2", "0xd40": "Neoverse-V1", "0xd0c": "Neoverse-N1", "0xd49": "Neoverse-N2"}
+
+
 def _cpu_model():
+    """The host CPU's model name (lscpu, else /proc/cpuinfo; an Arm part number is named)."""
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    part = None
     try:
         with open("/proc/cpuinfo") as f:
             for line in f:
-                if line.lower().startswith(("model name", "cpu part")):
+                low = line.lower()
+                if low.startswith("model name"):
                     return line.split(":", 1)[1].strip()
+                if low.startswith("cpu part") and part is None:
+                    part = line.split(":", 1)[1].strip().lower()
     except Exception:
         pass
+    if part:
+        return _ARM_PARTS.get(part, f"Arm CPU part {part}")
     return "unknown"
 
 
@@ -304,6 +331,24 @@ def _pcts(xs):
             "p99": float(np.percentile(a, 99))}
 
 
+def _pcts_censored(reached, n_total):
+    """Percentiles of the time to target over ALL n_total requests, the ones stopped at
+    the sweep cap counted as never reaching it (+infinity): nearest rank on the sorted
+    times; a percentile that falls among the censored requests is null, marked in
+    `censored`."""
+    import math
+    xs = sorted(reached)
+    out = {"censored_fraction": 1 - len(xs) / max(n_total, 1), "censored": []}
+    for name, p in (("p50", 0.50), ("p95", 0.95), ("p99", 0.99)):
+        k = max(1, math.ceil(p * n_total)) - 1  # 0-based nearest rank
+        if n_total and k < len(xs):
+            out[name] = float(xs[k])
+        else:
+            out[name] = None
+            out["censored"].append(name)
+    return out
+
+
 def run_served(sg, w, stream, sa_cap, pt_cap, chunk, max_active, budget):
     """The stream through the continuously batched server: each request is submitted at
     its arrival time; latency = submit lateness + the server's submit-to-done time."""
@@ -328,15 +373,24 @@ def run_served(sg, w, stream, sa_cap, pt_cap, chunk, max_active, budget):
     by_kind = {}
     for kind in ("SA", "PT"):
         ks = [(x, r) for x, r, it in zip(lat, res, stream) if it["kind"] == kind]
-        by_kind[kind] = {"requests": len(ks), "tte_s": _pcts([x for x, r in ks if r["reached"]]),
+        by_kind[kind] = {"requests": len(ks),
+                         "tte_s": _pcts_censored([x for x, r in ks if r["status"] == 0 and r["reached"]], len(ks)),
                          "censored": sum(1 for x, r in ks if not r["reached"]) / max(len(ks), 1)}
     return {"requests": len(stream), "errors": sum(1 for r in res if r["status"] != 0),
-            "tte_s": _pcts(reached), "latency_all_s": _pcts(lat),
+            "tte_s": _pcts_censored(reached, len(stream)),
+            "tte_reached_only_s": _pcts(reached),
+            "stop_s": _pcts(lat),
             "censored_fraction": 1 - len(reached) / max(len(stream), 1),
             "throughput_req_s": len(stream) / makespan if makespan else None,
             "attempts_per_s": attempts / makespan if makespan else None,
             "makespan_s": makespan, "max_submit_late_s": max(late) if late else 0.0,
-            "queue_s": _pcts([r["queue_s"] for r in res]), "by_kind": by_kind}
+            "queue_s": _pcts([r["queue_s"] for r in res]), "service_s": _pcts([r["run_s"] for r in res]),
+            "by_kind": by_kind,
+            "definitions": "tte_s: time from arrival to eps <= target over all requests, the ones stopped "
+                           "at the sweep cap counted as not reached (a percentile among them is null); "
+                           "tte_reached_only_s: the same over the requests that reached it; stop_s: arrival "
+                           "to done, reached or capped; queue_s: submit to admitted; service_s: admitted "
+                           "to done, in the mix"}
 
 
 def run_one_at_a_time(sg, w, stream, sa_cap, pt_cap, limit_s):
@@ -344,10 +398,11 @@ def run_one_at_a_time(sg, w, stream, sa_cap, pt_cap, limit_s):
     through the one-shot calls with one instance per launch -- SA as successive sg_sa_run
     restarts (instance_id = restart) checked after each, PT as one sg_pt_run of the cap.
     Requests not finished within limit_s count as unfinished, their latency bounded below
-    by limit_s - arrival."""
+    by limit_s - arrival.  service_s is each request's own processing time on the
+    otherwise idle GPU; wait_s is how long it waited for the requests before it."""
     import numpy as np
     t0 = time.perf_counter()
-    lat, reached, unfinished = [], [], 0
+    lat, reached, unfinished, service, wait = [], [], 0, [], []
     for it in stream:
         now = time.perf_counter() - t0
         if now > limit_s:
@@ -356,6 +411,7 @@ def run_one_at_a_time(sg, w, stream, sa_cap, pt_cap, limit_s):
             continue
         if it["t"] > now:
             time.sleep(it["t"] - now)
+        start = time.perf_counter() - t0
         inst = sg.Instance.create(it["L"], it["seed"], w.class_prob, True)
         target = inst.e_gs + int(np.floor(w.eps_target * abs(inst.e_gs)))
         ok = False
@@ -372,12 +428,16 @@ def run_one_at_a_time(sg, w, stream, sa_cap, pt_cap, limit_s):
             r = sg.pt_run(inst, w.pt_temps, pt_cap, w.pt_beta_min, w.pt_beta_max, seed=it["run_seed"])
             ok = r["minE"] <= target
         inst.close()
-        x = time.perf_counter() - t0 - it["t"]
+        end = time.perf_counter() - t0
+        x = end - it["t"]
         lat.append(x)
+        service.append(end - start)
+        wait.append(start - it["t"])
         if ok:
             reached.append(x)
     return {"requests": len(stream), "unfinished_at_limit": unfinished, "limit_s": limit_s,
-            "tte_s": _pcts(reached), "latency_all_s": _pcts(lat),
+            "tte_s": _pcts_censored(reached, len(stream)), "tte_reached_only_s": _pcts(reached),
+            "stop_s": _pcts(lat), "service_s": _pcts(service), "wait_s": _pcts(wait),
             "censored_fraction": 1 - len(reached) / max(len(stream), 1)}
 
 
@@ -443,11 +503,10 @@ def batched_line(sg, args, torch, clocks_cls, local):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     roof = None
     if sw["device_ms"] > 0:
-        roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), 2.0 / 8.0 + 3.0 / w.replicas, sms, sm_mhz, peak,
-                     peak_kind, traffic=None,
+        roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), ATTEMPTS_PER_BLOCK, hbm_views(w.replicas),
+                     _philox_blocks_per_s(sg), sms, sm_mhz, peak, peak_kind, traffic=None,
                      kernel="persistent batch kernel (one plane per block, or per thread-block cluster: autotuned)",
-                     launch_ms=sw["device_ms"] / max(sw["launches"], 1),
-                     rng_roof=_rng_roof(sg, sw["units"] / (sw["device_ms"] / 1000.0), 16))
+                     launch_ms=sw["device_ms"] / max(sw["launches"], 1))
     value = attempts * args.steps / (ms / 1000.0)
     eps = [float(e) for o in out for e in o["eps"][:4]]
     return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
@@ -498,12 +557,11 @@ def sa_line(sg, args, torch, clocks_cls, local):
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     roof = None
     if sw["launches"] and sw["device_ms"] > 0:
-        roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), 2.0 / 8.0 + 3.0 / w.replicas, sms, sm_mhz, peak,
-                     peak_kind, traffic=None,
+        roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), ATTEMPTS_PER_BLOCK, hbm_views(w.replicas),
+                     _philox_blocks_per_s(sg), sms, sm_mhz, peak, peak_kind, traffic=None,
                      kernel="sa_cluster_kernel" if sw["launches"] <= 4 * steps else "sweep_bits_kernel<SA>",
                      launch_ms=sw["device_ms"] / sw["launches"], share_of_step=sw["device_ms"] / ms,
-                     note="working set 0.5 MB of spin words: L2-resident, so HBM is not what limits it",
-                     rng_roof=_rng_roof(sg, sw["units"] / (sw["device_ms"] / 1000.0), 16))
+                     note="working set 0.5 MB of spin words: L2-resident, so HBM is not what limits it")
     eps = out["eps"]
     return {"metric": METRIC, "value": attempts * steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1,
             "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / steps,
@@ -520,8 +578,8 @@ def sa_line(sg, args, torch, clocks_cls, local):
 # ---------------------------------------------------------------- fragment meta-heuristic leg
 
 FRAG = dict(L=50, l=5, sweeps=20, beta0=0.5, beta1=6.0, instances=20)
-# a fragment site's draws: one Philox4x32-10 block (20 multiplies) serves 4 reads, at most
-FRAG_MULS_PER_ATTEMPT = 5.0
+# a fragment site's draws: one Philox4x32-10 block serves 4 reads, at most
+FRAG_ATTEMPTS_PER_BLOCK = 4
 
 
 def fragment_line(sg, args, torch, clocks_cls, local):
@@ -565,17 +623,13 @@ def fragment_line(sg, args, torch, clocks_cls, local):
     roof = None
     if sw["launches"] and sw["device_ms"] > 0:
         rate = sw["units"] / (sw["device_ms"] / 1000.0)
-        mul_peak = sms * WIDE_MULS_PER_SM_CLOCK * sm_mhz * 1e6 / 1e12
-        tmul = rate * FRAG_MULS_PER_ATTEMPT / 1e12
-        roof = {"bound": "alu", "achieved": tmul, "peak": mul_peak, "unit": "T 32x32->64-bit multiplies/s",
-                "frac": tmul / mul_peak, "muls_per_attempt": FRAG_MULS_PER_ATTEMPT,
-                "peak_source": f"derived: {sms} SMs x {WIDE_MULS_PER_SM_CLOCK} multiplies per clock at {sm_mhz:.0f} MHz",
-                "attempts_per_s": rate, "kernel": "fragment_wave_kernel", "traffic": None,
-                "launch_ms": sw["device_ms"] / sw["launches"], "share_of_step": sw["device_ms"] / ms,
-                "note": "bond terms of the 32 reads counted bit-sliced, weighted by |J| (fragments may hold "
-                        "|J| = 2 or 0 bonds and cube boundaries); reads with x < 0 take their draw one by one; "
-                        "muls_per_attempt is the most the draws can cost",
-                "rng_roof": _rng_roof(sg, rate, 4)}
+        # a fragment site's draws: one Philox block serves four reads, at most
+        roof = _roof(rate, FRAG_ATTEMPTS_PER_BLOCK, {}, _philox_blocks_per_s(sg), sms, sm_mhz, peak, peak_kind,
+                     kernel="fragment_wave_kernel", traffic=None, launch_ms=sw["device_ms"] / sw["launches"],
+                     share_of_step=sw["device_ms"] / ms,
+                     note="bond terms of the 32 reads counted bit-sliced, weighted by |J| (fragments may hold "
+                          "|J| = 2 or 0 bonds and cube boundaries); reads with x < 0 take their draw one by one; "
+                          "muls_per_attempt is the most the draws can cost")
     cpu = None
     if not args.no_cpu:
         from oracle import oracle as o
@@ -605,7 +659,7 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sweeps", type=int, default=WORK.sweeps,
                     help="sweeps per run (default: the workload's 10^4)")
-    ap.add_argument("--cpu-sweeps", type=int, default=4)
+    ap.add_argument("--cpu-sweeps", type=int, default=10)
     ap.add_argument("--ref-sweeps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -614,6 +668,8 @@ def main():
                          "serving stream alone; batched: 512 uneven SA instances in one launch; "
                          "sa: SA throughput at L=16 with 1024 replicas")
     ap.add_argument("--no-serve", action="store_true", help="skip the serving leg of the pt line")
+    ap.add_argument("--no-sub", action="store_true",
+                    help="skip the SA L=16 and batched sub-lines of the pt line")
     ap.add_argument("--serve-seconds", type=float, default=None,
                     help="arrival window (default: 10 s in the pt line, the workload's 60 s alone)")
     ap.add_argument("--serve-baseline-seconds", type=float, default=None,
@@ -677,7 +733,10 @@ def main():
         if rank == 0:
             res = serving_leg(sg, args, wl.SERVING)
             sv = res["served"]
-            line = {"metric": "served TTe at eps <= 1% (p50)", "value": sv["tte_s"]["p50"], "unit": "s",
+            # p50 over all requests with the capped ones counted as not reached: null (and
+            # named in tte_s.censored) when more than half of the stream was capped
+            line = {"metric": "served TTe at eps <= 1% (p50 over all requests, capped = not reached)",
+                    "value": sv["tte_s"]["p50"], "unit": "s",
                     "n_gpus": 1, "steps": 1, "warmup": 0, "higher_is_better": False, "scaling": "weak",
                     "vs_baseline": None, "dtype": "u32", "data": "synthetic",
                     "config": {"workload": wl.SERVING.name, "rate_per_s": wl.SERVING.rate_per_s,
@@ -739,13 +798,13 @@ def main():
         per_launch_s = sw["device_ms"] / 1000.0 / sw["launches"]
         attempts_per_launch = sw["units"] / sw["launches"]
         rec = _traffic_record()
-        roof = _roof(attempts_per_launch / per_launch_s, BYTES_PER_ATTEMPT, sms, sm_mhz, peak, peak_kind,
+        roof = _roof(attempts_per_launch / per_launch_s, ATTEMPTS_PER_BLOCK, hbm_views(WORK.temps),
+                     _philox_blocks_per_s(sg), sms, sm_mhz, peak, peak_kind,
                      traffic=rec["traffic_bytes_per_launch"] if rec else None,
                      traffic_unit="DRAM bytes per launch (ncu)",
                      algorithmic_bytes_per_launch=attempts_per_launch * BYTES_PER_ATTEMPT,
                      kernel="sweep_bits_kernel<PT>", launch_ms=1000 * per_launch_s,
-                     attempts_per_launch=attempts_per_launch, share_of_step=sw["device_ms"] / ms,
-                     rng_roof=_rng_roof(sg, attempts_per_launch / per_launch_s, 16))
+                     attempts_per_launch=attempts_per_launch, share_of_step=sw["device_ms"] / ms)
 
     # end to end: host couplings in, results out, inside the timed region
     e2e = None
@@ -777,6 +836,13 @@ def main():
     serving = None
     if rank == 0 and not args.no_serve:
         serving = serving_leg(sg, args, wl.SERVING)
+    # the other throughput workloads, each timed the same way (own warm-up, L2 flush,
+    # clocks, launch statistics): SA at L = 16 with 1024 replicas, and the 512 uneven
+    # SA instances in one persistent launch
+    sub_lines = None
+    if rank == 0 and not args.no_sub:
+        sub_lines = {"sa_L16": sa_line(sg, args, torch, ClockSampler, local),
+                     "batched": batched_line(sg, args, torch, ClockSampler, local)}
     barrier()
 
     if rank == 0:
@@ -787,7 +853,7 @@ def main():
                 "dtype": "u32", "data": "synthetic", "config": _config(),
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "min_eps_mean": float(np.mean(mins)),
-                "kernel_stats": st, "serving": serving}
+                "kernel_stats": st, "serving": serving, "sub_lines": sub_lines}
         if S != WORK.sweeps:
             line["config"]["sweeps"] = S
             line["note"] = f"reduced sweeps ({S}) -- not the workload's number"

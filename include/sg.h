@@ -29,13 +29,16 @@
  *     bytes on every call, batch composition and GPU.  Every random number is word
  *     w of Philox4x32-10 (Salmon et al., SC'11) with key
  *     (seed_lo32, seed_hi32 ^ instance_id) at a counter that names its use:
- *       Metropolis draw of replica r at site i, sweep s: counter (i, s, r/4, 0), w = r%4
+ *       Metropolis draw of replica r at site i, sweep s: the 32-bit uniform
+ *         U = A * 2^24 + B, with g = r / 32, b = r % 32: bit j (j = 0..7) of the
+ *         leading byte A is bit b of word j % 4 at counter (i, s, 2g + j/4, 0), and
+ *         B is the top 24 bits of word r % 4 at counter (i, s, r/4, 4)
  *       initial spin of replica r at site i:             counter (i, 0xFFFFFFFF, r/4, 0), w = r%4,
  *                                                         spin = -1 iff bit 31 is set
  *       PT exchange of rungs (k, k+1) after sweep s:      counter (k, s, 0, 1), w = 0
  *   - A Metropolis attempt at site i computes x = s_i * sum_j J_ij s_j (flipping
- *     changes E by dE = -2x) and flips when x >= 0, or when the draw u satisfies
- *     u < floor(2^32 * exp(-beta * dE)).  Sites are swept in checkerboard order:
+ *     changes E by dE = -2x) and flips when x >= 0, or when the draw U satisfies
+ *     U < floor(2^32 * exp(-beta * dE)) (clamped to 2^32 - 1).  Sites are swept in checkerboard order:
  *     all sites with x+y+z even, then all with x+y+z odd.
  */
 #ifndef SG_H
@@ -321,24 +324,27 @@ int32_t sg_server_destroy(sg_server* srv);
  * GPU that loads the library holds this array until the process exits. */
 #define SG_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
 
-/* Same energies as sg_energy (Eq. 1), for callers that must not let a library
- * allocate device memory -- for example a server that owns the device-memory budget
- * through its own pool, or a latency-critical loop where cudaMalloc/cudaFree (which
- * can synchronise the device and can fail under fragmentation) is not allowed.
+/* The energies sg_energy computes, for callers that must not let a library allocate
+ * device memory -- for example a server that owns the device-memory budget through its
+ * own pool, or a latency-critical loop where cudaMalloc/cudaFree (which can synchronise
+ * the device and can fail under fragmentation) is not allowed.  The paper has no
+ * counterpart: this is an interface for such callers only.
  *   L          lattice side (even, 2 <= L <= SG_LMAX)
  *   J3_dev     device int8 [L^3][3] couplings (|J| <= SG_JMAX), read only
  *   spins_dev  device int8 [n_configs][L^3] configurations in {-1, +1}, read only
  *   E_dev      device int64 [n_configs], written
- * No cudaMalloc, cudaFree or allocating library routine is called.  All scratch lives
- * in one fixed array of SG_NOALLOC_SCRATCH_BYTES per device; a request that needs more
- * (about 9*L^3 + L^3 * 4*ceil(n_configs/32) bytes) fails with SG_EINVAL and a message.
- * The first call on a device looks up the array's device address (with that device
- * current); make that first call before any stream capture.  Every call shares the
- * array and it keeps the last call's contents (the call clears what must start at
- * zero): calls that overlap on the GPU -- on different streams or from different host
- * threads -- race on it, so serialise them.  The call enqueues on `stream` and
- * returns after it has completed.  Errors: SG_EINVAL (bad arguments, too large, a
- * spin not in {-1,+1}), SG_ECUDA. */
+ * All pointers are device memory of the current device.  No cudaMalloc, cudaFree or
+ * allocating library routine is called.  All scratch lives in one fixed array of
+ * SG_NOALLOC_SCRATCH_BYTES per device; a request that needs more (about
+ * 9*L^3 + L^3 * 4*ceil(n_configs/32) bytes) fails with SG_EINVAL and a message.
+ * The first call on a device is its set-up: it looks up the array's device address
+ * with that device current (loading the library's device code there); make that first
+ * call before any stream capture.  Every call repeats the lookup, so a device reset
+ * between calls is harmless.  Every call shares the array and it keeps the last call's
+ * contents (the call clears what must start at zero): calls that overlap on the GPU --
+ * on different streams or from different host threads -- race on it, so serialise
+ * them.  The call enqueues on `stream` and returns after it has completed.
+ * Errors: SG_EINVAL (bad arguments, too large, a spin not in {-1,+1}), SG_ECUDA. */
 int32_t sg_energy_noalloc(int32_t L, const int8_t* J3_dev, const int8_t* spins_dev,
                           int32_t n_configs, int64_t* E_dev, void* stream);
 

@@ -15,15 +15,18 @@ namespace sg {
 namespace {
 
 // The scratch.  Host code must not take this name as a device address: its device
-// address comes from cudaGetSymbolAddress, once per device (see scratch_on_device).
+// address comes from cudaGetSymbolAddress with the device current (scratch_on_device).
 static __device__ __align__(256) unsigned char g_noalloc_scratch[SG_NOALLOC_SCRATCH_BYTES];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 unsigned char* g_scratch_ptr[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device, looked up once per device
-// with that device current.
+// Device address of the scratch array on the current device.  The first call on a device
+// is the set-up: the lookup (which also loads this library's device code there) and the
+// cache entry.  Later calls repeat the lookup, which is cheap once the code is loaded, and
+// refresh the entry if the address moved -- after cudaDeviceReset, or under another
+// context -- so a stale address is never handed to a kernel.
 int32_t scratch_on_device(unsigned char** out)
 {
     int dev = 0;
@@ -32,19 +35,21 @@ int32_t scratch_on_device(unsigned char** out)
         set_error("device ordinal %d out of range", dev);
         return SG_EINVAL;
     }
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-        void* p = nullptr;
-        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            set_error("cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
-            return SG_ECUDA;
-        }
-        g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
+        set_error("cudaGetSymbolAddress(scratch) failed: %s", cudaGetErrorString(e));
+        return SG_ECUDA;
     }
+    std::lock_guard<std::mutex> lock(g_mu);
+    g_scratch_ptr[dev] = static_cast<unsigned char*>(p);
     *out = g_scratch_ptr[dev];
     return SG_OK;
 }
+
+// Stores the coupling-record pointer the energy kernel reads from device memory
+// (a kernel argument, so no host buffer is involved).
+__global__ void store_pointer(const uint2** slot, const uint2* value) { *slot = value; }
 
 size_t round_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
@@ -92,8 +97,8 @@ extern "C" int32_t sg_energy_noalloc(int32_t L, const int8_t* J3_dev, const int8
     // the array keeps the previous call's contents: clear the sums and the status word
     SG_TRY_CUDA(cudaMemsetAsync(E64, 0, 8 * (size_t)Rp, st));
     SG_TRY_CUDA(cudaMemsetAsync(bad, 0, sizeof(int), st));
-    const uint2* j6c = j6;
-    SG_TRY_CUDA(cudaMemcpyAsync(j6_ptr, &j6c, sizeof(j6c), cudaMemcpyHostToDevice, st));
+    store_pointer<<<1, 1, 0, st>>>(j6_ptr, j6);
+    SG_TRY_CUDA(cudaGetLastError());
     rc = launch_prepare_j6(J3_dev, j6, j1, L, st);
     if (rc != SG_OK) return rc;
     rc = launch_pack_spins(spins_dev, packed, L, Rp, n_configs, bad, st);

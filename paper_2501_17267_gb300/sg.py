@@ -394,13 +394,40 @@ def philox_rate(blocks_per_thread: int = 4096, stream=None) -> float:
     return out.value
 
 
+def _check_noalloc_args(L: int, J3_dev, spins_dev, E_dev) -> int:
+    """Validates the tensors of energy_noalloc before anything reaches the device; returns
+    the number of configurations.  Raises ValueError (not an assert, so it holds under -O)."""
+    import torch
+    if not isinstance(L, int) or L < 2 or L % 2 or L > 256:
+        raise ValueError(f"L must be an even int in [2, 256], got {L!r}")
+    N = L ** 3
+    named = (("J3_dev", J3_dev, torch.int8), ("spins_dev", spins_dev, torch.int8), ("E_dev", E_dev, torch.int64))
+    for name, t, dt in named:
+        if not _is_torch_cuda(t):
+            raise ValueError(f"{name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise ValueError(f"{name} must have dtype {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
+    dev = torch.cuda.current_device()
+    for name, t, _ in named:
+        if t.device.index != dev:
+            raise ValueError(f"{name} is on cuda:{t.device.index}, the current device is cuda:{dev}")
+    if J3_dev.numel() != 3 * N:
+        raise ValueError(f"J3_dev must hold L^3 x 3 = {3 * N} couplings, got {J3_dev.numel()}")
+    n = spins_dev.numel() // N
+    if n < 1 or spins_dev.numel() != n * N:
+        raise ValueError(f"spins_dev must hold a positive multiple of L^3 = {N} spins, got {spins_dev.numel()}")
+    if E_dev.numel() != n:
+        raise ValueError(f"E_dev must hold one energy per configuration ({n}), got {E_dev.numel()}")
+    return n
+
+
 def energy_noalloc(L: int, J3_dev, spins_dev, E_dev, stream=None):
-    """Energies of spins_dev (n, L^3) into E_dev (n,) int64, all torch CUDA tensors,
-    through the entry point that allocates no device memory (fixed scratch)."""
-    assert _is_torch_cuda(J3_dev) and _is_torch_cuda(spins_dev) and _is_torch_cuda(E_dev)
-    assert J3_dev.is_contiguous() and spins_dev.is_contiguous() and E_dev.is_contiguous()
-    n = spins_dev.numel() // (L ** 3)
-    assert E_dev.numel() == n
+    """Energies of spins_dev (n, L^3) into E_dev (n,) int64, all torch CUDA tensors on the
+    current device, through the entry point that allocates no device memory (for callers
+    that cannot let a library allocate: it uses a fixed scratch array instead)."""
+    n = _check_noalloc_args(L, J3_dev, spins_dev, E_dev)
     _check(_lib.sg_energy_noalloc(L, _P(J3_dev.data_ptr()), _P(spins_dev.data_ptr()), n,
                                   _P(E_dev.data_ptr()), _stream_handle(stream)))
 

@@ -31,33 +31,33 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
 
 
-def test_roof_picks_the_binding_roof():
+def test_roof_is_measured_generator_rate():
     import bench
-    # 152 SMs at 2070 MHz: 10.07 T multiplies/s = 8.05e12 attempts/s at 1.25 per attempt;
-    # HBM at 6800 GB/s and 0.344 B/attempt allows 1.98e13, so the multiply roof binds
-    r = bench._roof(2.0e12, 0.34375, 152, 2070.0, 6800.0, "measured")
-    assert r["bound"] == "alu" and r["other_roof"]["bound"] == "hbm"
-    assert r["peak"] == pytest.approx(152 * 32 * 2070e6 / 1e12)
-    assert r["frac"] == pytest.approx(2.0e12 * 1.25 / 1e12 / r["peak"])
-    assert r["other_roof"]["frac"] == pytest.approx(2.0e12 * 0.34375 / 1e9 / 6800.0)
-    # 3 B per attempt: HBM allows 2.27e12 attempts/s, below the multiply roof
-    assert bench._roof(1.0e12, 3.0, 152, 2070.0, 6800.0, "measured")["bound"] == "hbm"
+    # a sweep kernel at 2e12 attempts/s: 16 attempts per Philox block of 20 multiplies is
+    # 1.25 multiplies per attempt; against a measured 5.45e11 blocks/s (10.9 T multiplies/s)
+    r = bench._roof(2.0e12, 16, bench.hbm_views(32), 5.45e11, 152, 2070.0, 6800.0, "measured")
+    assert r["bound"] == "alu" and r["peak_source"].startswith("measured")
+    assert r["peak"] == pytest.approx(5.45e11 * 20 / 1e12)
+    assert r["achieved"] == pytest.approx(2.0e12 * 1.25 / 1e12)
+    assert r["frac"] == pytest.approx(2.0e12 / (16 * 5.45e11))
+    assert r["peak_attempts_per_s"] == pytest.approx(16 * 5.45e11)
+    assert r["nominal_peak"]["value"] == pytest.approx(152 * 32 * 2070e6 / 1e12)
+    v = r["hbm_views"]
+    assert v["int8_layout"]["bytes_per_attempt"] == pytest.approx(2 + 3 / 32)
+    assert v["bit_packed"]["bytes_per_attempt"] == pytest.approx(0.25 + 3 / 32)
+    assert v["bit_packed"]["frac"] == pytest.approx(2.0e12 * (0.25 + 3 / 32) / 1e9 / 6800.0)
+    # without the measurement the nominal peak stands in, and says so
+    d = bench._roof(2.0e12, 16, {}, None, 152, 2070.0, 6800.0, "measured")
+    assert d["peak_source"].startswith("derived") and d["peak"] == pytest.approx(d["nominal_peak"]["value"])
 
 
-def test_rng_roof_scales_the_measured_block_rate():
+def test_censored_percentiles_count_capped_requests_as_not_reached():
     import bench
-
-    class Fake:
-        @staticmethod
-        def philox_rate():
-            return 5.0e11
-
-    r = bench._rng_roof(Fake, 2.0e12, 16)
-    assert r["attempts_per_s"] == pytest.approx(8.0e12) and r["frac"] == pytest.approx(0.25)
-
-    class Broken:
-        @staticmethod
-        def philox_rate():
-            raise RuntimeError("no device")
-
-    assert "error" in bench._rng_roof(Broken, 1.0, 16)
+    # 10 requests, 6 reached: p50 is the 5th smallest time, p95 and p99 fall among the capped
+    r = bench._pcts_censored([6.0, 1.0, 5.0, 2.0, 4.0, 3.0], 10)
+    assert r["p50"] == 5.0 and r["p95"] is None and r["p99"] is None
+    assert r["censored"] == ["p95", "p99"] and r["censored_fraction"] == pytest.approx(0.4)
+    # more than half capped: the median itself is censored
+    assert bench._pcts_censored([1.0, 2.0], 10)["p50"] is None
+    full = bench._pcts_censored([float(x) for x in range(1, 101)], 100)
+    assert (full["p50"], full["p95"], full["p99"]) == (50.0, 95.0, 99.0)

@@ -61,19 +61,20 @@ def test_dependent_launch_changes_no_result(tmp_path):
     assert sorted(plain.files) == sorted(overlapped.files)
     for k in plain.files:
         assert np.array_equal(plain[k], overlapped[k]), k
-    # the plain launches against the oracle on the small PT and SA cases
-    for n in (0, 3):
-        kind, L, iseed, width, S, seed, iid = CASES[n]
-        J3 = plain[f"{n}_J3"]
-        if kind == "pt":
-            ref = o.pt_run(L, J3, seed, iid, width, S, 0.2, 3.0)
-            for k in ("spins", "E", "perm", "accepts"):
-                assert np.array_equal(plain[f"{n}_{k}"], ref[k]), k
-            assert int(plain[f"{n}_minE"]) == ref["minE"]
-        else:
-            ospins, oE = o.sa_run(L, J3, seed, iid, S, 0.1, 3.0, True, R=width)
-            assert np.array_equal(plain[f"{n}_spins"], ospins)
-            assert np.array_equal(plain[f"{n}_E"], oE)
+    # the plain launches against the oracle: both PT cases with one ladder (the L = 64,
+    # 32-temperature geometry included) and the SA case, the oracle runs side by side
+    from oracle import pool
+    pt_cases = (0, 1)
+    refs = pool.pt_runs([(CASES[n][1], plain[f"{n}_J3"], CASES[n][5], CASES[n][6], CASES[n][3], CASES[n][4],
+                          0.2, 3.0) for n in pt_cases])
+    for n, ref in zip(pt_cases, refs):
+        for k in ("spins", "E", "perm", "accepts"):
+            assert np.array_equal(plain[f"{n}_{k}"], ref[k]), (n, k)
+        assert int(plain[f"{n}_minE"]) == ref["minE"], n
+    kind, L, iseed, width, S, seed, iid = CASES[3]
+    ospins, oE = o.sa_run(L, plain["3_J3"], seed, iid, S, 0.1, 3.0, True, R=width)
+    assert np.array_equal(plain["3_spins"], ospins)
+    assert np.array_equal(plain["3_E"], oE)
 
 
 def test_generator_rate_is_measured():

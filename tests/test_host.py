@@ -121,3 +121,65 @@ def test_request_bytes_counts_state(sg):
     with pytest.raises(sg.SGError) as e:
         sg.request_bytes(sg.request(sg.SG_REQ_SA, 7, 1, 8, 0.1, 3.0, 0.0, 10))
     assert e.value.code == sg.SG_EINVAL
+
+
+class _FakeCudaTensor:
+    """Stands in for a CUDA tensor on a machine without a GPU: the binding may look at its
+    dtype, size, layout and device, never at its memory."""
+
+    def __init__(self, dtype, numel, device=0, contiguous=True):
+        import types
+        self.is_cuda = True
+        self.dtype = dtype
+        self._numel = numel
+        self._contiguous = contiguous
+        self.device = types.SimpleNamespace(index=device)
+
+    def numel(self):
+        return self._numel
+
+    def is_contiguous(self):
+        return self._contiguous
+
+    def data_ptr(self):
+        raise AssertionError("a rejected call must not reach the library")
+
+
+def test_noalloc_binding_rejects_bad_tensors_before_any_launch(sg, monkeypatch):
+    """energy_noalloc checks dtypes, sizes, layout and device of every tensor and raises
+    ValueError before anything reaches the device (a wrong dtype or a short buffer would
+    otherwise make the kernels read or write out of bounds)."""
+    import torch
+    monkeypatch.setattr(torch.cuda, "current_device", lambda: 0)
+    monkeypatch.setattr(sg._lib, "sg_energy_noalloc", lambda *a: pytest.fail("library called"))
+    L, n = 4, 3
+    N = L ** 3
+
+    def args(**over):
+        a = dict(J3=_FakeCudaTensor(torch.int8, 3 * N), spins=_FakeCudaTensor(torch.int8, n * N),
+                 E=_FakeCudaTensor(torch.int64, n))
+        a.update(over)
+        return a
+
+    bad = [
+        args(E=_FakeCudaTensor(torch.int32, n)),               # 4-byte energies
+        args(J3=_FakeCudaTensor(torch.int16, 3 * N)),          # wrong coupling dtype
+        args(spins=_FakeCudaTensor(torch.float32, n * N)),     # wrong spin dtype
+        args(J3=_FakeCudaTensor(torch.int8, 3 * N - 1)),       # short couplings
+        args(spins=_FakeCudaTensor(torch.int8, n * N + 1)),    # ragged spins
+        args(spins=_FakeCudaTensor(torch.int8, 0), E=_FakeCudaTensor(torch.int64, 0)),  # nothing
+        args(E=_FakeCudaTensor(torch.int64, n + 1)),           # energies of the wrong count
+        args(spins=_FakeCudaTensor(torch.int8, n * N, device=1)),  # not the current device
+        args(J3=_FakeCudaTensor(torch.int8, 3 * N, contiguous=False)),
+        args(E=np.zeros(n, dtype=np.int64)),                   # a host array
+    ]
+    for a in bad:
+        with pytest.raises(ValueError):
+            sg.energy_noalloc(L, a["J3"], a["spins"], a["E"])
+    for badL in (3, 0, 258):
+        with pytest.raises(ValueError):
+            a = args()
+            sg.energy_noalloc(badL, a["J3"], a["spins"], a["E"])
+    # the argument set the others were made from passes the checks
+    a = args()
+    assert sg._check_noalloc_args(L, a["J3"], a["spins"], a["E"]) == n
