@@ -367,6 +367,22 @@ static uint32_t metropolis_uniform(uint32_t k0, uint32_t k1, int64_t i, uint32_t
     return (a << 24) | (tail >> 8);
 }
 
+/* The draws of replicas reps[0..n_reps) at sites i0 .. i0+n_i-1 and sweeps
+ * s0 .. s0+n_s-1, out[((s - s0) * n_i + (i - i0)) * n_reps + k] = U of replica reps[k]:
+ * exposed so that tests can check the law of the draws (uniform, independent across
+ * replicas, sites and sweeps) without going through a run. */
+void or_metropolis_uniform_grid(uint64_t seed, uint32_t instance_id, int64_t i0, int n_i, uint32_t s0,
+                                int n_s, const int32_t* reps, int n_reps, uint32_t* out)
+{
+    uint32_t k0, k1;
+    run_key(seed, instance_id, &k0, &k1);
+    for (int s = 0; s < n_s; ++s)
+        for (int i = 0; i < n_i; ++i)
+            for (int k = 0; k < n_reps; ++k)
+                out[((int64_t)s * n_i + i) * n_reps + k] =
+                    metropolis_uniform(k0, k1, i0 + i, s0 + (uint32_t)s, reps[k]);
+}
+
 /* One Metropolis attempt at site i of replica rep during sweep `sweep`.
  * x = s_i h_i; flipping changes E by -2x.  Accept when x >= 0, else when the
  * draw u is below the threshold for dE = -2x.  Returns the energy change. */

@@ -47,6 +47,8 @@ uint32_t or_metropolis_threshold(double beta, int dE);
 uint32_t or_exchange_threshold(double dbeta, int64_t d);
 
 int8_t or_init_spin(uint64_t seed, uint32_t instance_id, int64_t i, int rep);
+void or_metropolis_uniform_grid(uint64_t seed, uint32_t instance_id, int64_t i0, int n_i, uint32_t s0,
+                                int n_s, const int32_t* reps, int n_reps, uint32_t* out);
 int or_sa_run(int L, const int8_t* J3, uint64_t seed, uint32_t instance_id,
               int S, double b0, double b1, int geometric,
               const int32_t* reps, int nreps, int8_t* spins_out, int64_t* E_out);

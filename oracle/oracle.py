@@ -68,6 +68,7 @@ def lib():
                 "or_metropolis_threshold": (u32, [dbl, i32]),
                 "or_exchange_threshold": (u32, [dbl, i64]),
                 "or_init_spin": (ctypes.c_int8, [u64, u32, i64, i32]),
+                "or_metropolis_uniform_grid": (None, [u64, u32, i64, i32, u32, i32, P, i32, P]),
                 "or_sa_run": (i32, [i32, P, u64, u32, i32, dbl, dbl, i32, P, i32, P, P]),
                 "or_pt_run": (i32, [i32, P, u64, u32, i32, i32, dbl, dbl, P, P, P, P, P]),
                 "or_fragment_run": (i32, [i32, P, i32, i32, dbl, dbl, u64, u32, P, P]),
@@ -180,6 +181,16 @@ def exchange_threshold(dbeta: float, d: int) -> int:
 
 def init_spin(seed: int, instance_id: int, i: int, rep: int) -> int:
     return int(lib().or_init_spin(seed, instance_id, i, rep))
+
+
+def metropolis_uniforms(seed: int, instance_id: int, i0: int, n_sites: int, s0: int, n_sweeps: int,
+                        reps) -> np.ndarray:
+    """The 32-bit draws U of the listed replicas at sites i0.. and sweeps s0..:
+    uint32 array (n_sweeps, n_sites, len(reps))."""
+    reps = np.ascontiguousarray(list(reps), dtype=np.int32)
+    out = np.zeros((n_sweeps, n_sites, len(reps)), dtype=np.uint32)
+    lib().or_metropolis_uniform_grid(seed, instance_id, i0, n_sites, s0, n_sweeps, _p(reps), len(reps), _p(out))
+    return out
 
 
 def sa_run(L: int, J3: np.ndarray, seed: int, instance_id: int, S: int, b0: float,

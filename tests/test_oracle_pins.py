@@ -46,6 +46,81 @@ def test_init_spins_are_balanced():
     assert not np.array_equal(s[0], s[1])
 
 
+def _pairwise_bounds(counts, M, p, z=6.0):
+    """Every off-diagonal entry of counts (pairs of replicas) within z binomial standard
+    deviations of M * p, the count two independent replicas give."""
+    off = counts[~np.eye(counts.shape[0], dtype=bool)]
+    mu, sd = M * p, math.sqrt(M * p * (1 - p))
+    return off.min() >= mu - z * sd and off.max() <= mu + z * sd
+
+
+def test_init_spins_independent_across_replicas():
+    """Initial spins of 64 replicas (two groups of 32) over 4096 sites: each pair of
+    replicas agrees on about half the sites, as independent uniform spins do.  A mistake
+    that hands two replicas the same Philox word (e.g. indexing by r % 16) makes them agree
+    everywhere."""
+    N, R = 4096, 64
+    s = np.array([[o.init_spin(11, 2, i, r) for r in range(R)] for i in range(N)])
+    agree = (s[:, :, None] == s[:, None, :]).sum(axis=0)
+    assert _pairwise_bounds(agree, N, 0.5)
+
+
+def test_draws_are_uniform_and_independent_across_replicas_sites_and_sweeps():
+    """The 32-bit draw U of each Metropolis attempt (App. D.1 asks for one uniform per
+    attempt) is assembled from bit planes shared by the 32 replicas of a group.  Over 64
+    sites x 64 sweeps and 64 replicas (two groups): leading bytes are uniform over 256
+    values; two replicas' leading bytes agree with probability 1/256, and their accept
+    decisions at threshold 2^31 coincide in M/4 attempts, as for independent draws; the
+    same holds between neighbouring sites and consecutive sweeps of one replica.  A
+    mistake that hands two replicas (or sites, or sweeps) the same bits fails here even
+    though each replica's own law stays uniform."""
+    R = 64
+    U = o.metropolis_uniforms(5, 9, 100, 64, 3, 64, range(R))  # (sweeps, sites, replicas)
+    flat = U.reshape(-1, R)
+    M = flat.shape[0]
+    A = (flat >> 24).astype(np.int64)
+    # uniform leading bytes, pooled over replicas (chi-square with 255 degrees of freedom)
+    hist = np.bincount(A.ravel(), minlength=256)
+    chi2 = ((hist - A.size / 256) ** 2 / (A.size / 256)).sum()
+    assert stats.chi2.sf(chi2, 255) > 1e-6
+    # each of the eight bit planes balanced in every replica
+    for j in range(8):
+        frac = ((A >> j) & 1).mean(axis=0)
+        assert np.abs(frac - 0.5).max() < 6 * math.sqrt(0.25 / M)
+    # pairs of replicas: equal leading bytes, joint acceptance at 2^31
+    eq = np.zeros((R, R), dtype=np.int64)
+    for r in range(R):
+        eq[r] = (A == A[:, r:r + 1]).sum(axis=0)
+    assert _pairwise_bounds(eq, M, 1 / 256)
+    D = (flat < 2 ** 31).astype(np.int64)
+    assert _pairwise_bounds(D.T @ D, M, 0.25)
+    # one replica at neighbouring sites and at consecutive sweeps
+    for a, b in ((U[:, 1:, :], U[:, :-1, :]), (U[1:, :, :], U[:-1, :, :])):
+        same = ((a >> 24) == (b >> 24)).reshape(-1, R).sum(axis=0)
+        n = a.shape[0] * a.shape[1]
+        assert np.abs(same - n / 256).max() < 6 * math.sqrt(n / 256)
+
+
+@pytest.mark.parametrize("beta", [0.2, 1.0, 3.0])
+def test_accept_rate_per_energy_step_matches_threshold(beta):
+    """Per replica and per energy increase dE = 2k (k = 2, 4, 6, and 8 .. 12 for |J| = 2),
+    the fraction of draws below the threshold is floor(2^32 exp(-beta dE)) / 2^32: the
+    Metropolis acceptance probability exp(-beta dE) (App. D.1), checked against an
+    independent decimal exp within binomial error."""
+    R = 64
+    U = o.metropolis_uniforms(21, 4, 7, 64, 40, 64, range(R)).reshape(-1, R)
+    M = U.shape[0]
+    decimal.getcontext().prec = 50
+    for k in (2, 4, 6, 8, 10, 12):
+        p = float((-decimal.Decimal(repr(beta)) * 2 * k).exp())
+        thr = o.metropolis_threshold(beta, 2 * k)
+        acc = (U < thr).mean(axis=0)
+        sd = math.sqrt(max(p * (1 - p), 1 / M) / M)
+        assert np.abs(acc - p).max() < 6 * sd + 1 / M
+        pooled = (U < thr).mean()
+        assert abs(pooled - p) < 6 * math.sqrt(max(p * (1 - p), 1 / U.size) / U.size) + 1 / U.size
+
+
 # --------------------------------------------------------------------------- cube geometry
 
 def test_cube_edges_are_the_twelve_unit_edges():
