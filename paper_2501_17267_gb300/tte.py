@@ -4,10 +4,13 @@ run on the GPU path.
 TTeps of an instance at a target gap eps: the smallest number of sweeps S at which the
 optimality gap (Eq. 2) averaged over `runs` independent SA runs (geometric beta
 schedule, one read each) is at or below eps.  The paper times that S in wall-clock
-seconds on a CPU; here the cost of a run is reported as its work, S sweeps of N sites
-(S * N attempts per run), which is what a CPU wall time measures up to a constant --
-on the GPU a single small run is bound by launch and barrier latency, not by its
-work, so its wall time would not show the method's scaling.
+seconds on a CPU.  Here the cost of a run is reported two ways: as its work, S sweeps
+of N sites (S * N attempts per run), which is what a CPU wall time measures up to a
+constant, and as the wall time of the runs at those S on this GPU -- one instance per
+call (its `runs` replicas together), and all instances of a size in one batched call
+(per instance) -- with the a L^(3 alpha) + b fit on each.  A small run on the GPU is
+bound by launch and barrier latency rather than by its work, so the time exponents
+differ from the work exponents.
 
 Steps (App. D.1):
   1. For each target eps, tune the beta range on L = 10 instances: for each instance
@@ -152,12 +155,44 @@ class ScalingPoint:
     L: int
     sweeps: list = field(default_factory=list)   # per instance (None: censored)
     cost: float = 0.0                              # mean of S * N over uncensored instances
-    wall_s: float = 0.0
+    wall_s: float = 0.0                            # the search for the sweep counts
+    time_one_s: float = float("nan")               # mean wall time of one instance's runs at its S
+    time_batched_s: float = float("nan")           # all instances at their S in one call, per instance
+
+
+def time_runs(sg, insts, sweeps, runs: int, beta_min: float, beta_max: float, seed: int, repeat: int = 3):
+    """Wall time of SA at each instance's sweep count (None: skipped) -- the time to the
+    target gap: (mean over instances of one sg_sa_run call of `runs` replicas, the call
+    of all of them together in one sg_sa_run_batch divided by their number); each the
+    best of `repeat` after one untimed call.  The calls return once their results are on
+    the host, so host timers measure what a caller waits."""
+    items = [(k, S) for k, S in enumerate(sweeps) if S]
+    if not items:
+        return float("nan"), float("nan")
+
+    def params(k, S):
+        return dict(replicas=runs, sweeps=int(S), beta0=beta_min, beta1=beta_max, schedule="geometric",
+                    seed=seed, instance_id=k)
+
+    def best(fn):
+        fn()
+        t = []
+        for _ in range(repeat):
+            t0 = time.perf_counter()
+            fn()
+            t.append(time.perf_counter() - t0)
+        return min(t)
+
+    one = [best(lambda k=k, S=S: sg.sa_run_batch([insts[k]], [params(k, S)])) for k, S in items]
+    batch = best(lambda: sg.sa_run_batch([insts[k] for k, _ in items], [params(k, S) for k, S in items]))
+    return float(np.mean(one)), batch / len(items)
 
 
 def scaling(sg, target: float, beta_min: float, beta_max: float, Ls=SCALING_L, n_inst: int = 20,
-            runs: int = 20, seed_base: int = 0, s_max: int = 1 << 17):
-    """Step 2 of App. D.1 at one target: mean cost per L and the fitted alpha."""
+            runs: int = 20, seed_base: int = 0, s_max: int = 1 << 17, timed: bool = False):
+    """Step 2 of App. D.1 at one target: mean cost per L and the fitted alpha.  timed:
+    also the wall times of the runs at the sweep counts found (time_runs), and the fit
+    is then a dict of (alpha, a, b) per cost: "work", "time_one_s", "time_batched_s"."""
     points = []
     for L in Ls:
         insts = [sg.Instance.create(L, seed_base + 1000 * L + k, F6, True) for k in range(n_inst)]
@@ -167,6 +202,8 @@ def scaling(sg, target: float, beta_min: float, beta_max: float, Ls=SCALING_L, n
         p = ScalingPoint(L=L, sweeps=S, wall_s=time.perf_counter() - t0)
         ok = [s for s in S if s]
         p.cost = float(np.mean([s * L ** 3 for s in ok])) if ok else float("nan")
+        if timed:
+            p.time_one_s, p.time_batched_s = time_runs(sg, insts, S, runs, beta_min, beta_max, seed_base + L)
         points.append(p)
         for i in insts:
             i.close()
@@ -174,7 +211,13 @@ def scaling(sg, target: float, beta_min: float, beta_max: float, Ls=SCALING_L, n
     good = [p for p in points if np.isfinite(p.cost)]
     if len(good) >= 3:
         fit = fit_alpha([p.L for p in good], [p.cost for p in good])
-    return points, fit
+    if not timed:
+        return points, fit
+    fits = {"work": fit}
+    for key in ("time_one_s", "time_batched_s"):
+        g = [p for p in points if np.isfinite(getattr(p, key))]
+        fits[key] = fit_alpha([p.L for p in g], [getattr(p, key) for p in g]) if len(g) >= 3 else None
+    return points, fits
 
 
 def main(argv=None):
@@ -207,12 +250,18 @@ def main(argv=None):
             out.append(row)
             continue
         row["beta_min"], row["beta_max"] = tuned["beta_min"], tuned["beta_max"]
-        points, fit = scaling(sg, eps, tuned["beta_min"], tuned["beta_max"], args.L, args.instances, args.runs)
+        points, fits = scaling(sg, eps, tuned["beta_min"], tuned["beta_max"], args.L, args.instances, args.runs,
+                               timed=True)
         row["points"] = [dict(L=p.L, mean_sweeps=float(np.mean([s for s in p.sweeps if s])) if any(p.sweeps) else None,
-                              censored=sum(1 for s in p.sweeps if not s), cost_attempts=p.cost, seconds=p.wall_s)
+                              censored=sum(1 for s in p.sweeps if not s), cost_attempts=p.cost,
+                              time_one_s=p.time_one_s, time_batched_per_instance_s=p.time_batched_s,
+                              search_seconds=p.wall_s)
                          for p in points]
-        if fit:
-            row["alpha"], row["a"], row["b"] = fit
+        if fits["work"]:
+            row["alpha"], row["a"], row["b"] = fits["work"]
+        for key in ("time_one_s", "time_batched_s"):
+            if fits[key]:
+                row[f"alpha_{key}"] = fits[key][0]
         out.append(row)
         print(json.dumps(row), flush=True)
     return out

@@ -107,3 +107,28 @@ def test_min_sweeps_on_the_gpu_is_the_first_passing_count():
             assert mean(s - 1) > target
     tuned = tte.tune_beta_range(runner, 3, target, bmin_grid=(0.3, 0.9), bmax_grid=(3.0, 5.0), s_max=1 << 10)
     assert 0.3 <= tuned["beta_min"] <= 0.9 and 3.0 <= tuned["beta_max"] <= 5.0
+
+
+def test_time_runs_times_each_instance_and_the_batch(monkeypatch):
+    """time_runs: one call per instance at its own sweep count (censored ones skipped), and
+    one batched call of all of them; the batched time is per instance."""
+    calls = []
+
+    class FakeSG:
+        @staticmethod
+        def sa_run_batch(insts, params):
+            calls.append([(i, p["sweeps"], p["instance_id"]) for i, p in zip(insts, params)])
+            return [{}] * len(insts)
+
+    clock = iter(float(t) for t in range(1000))
+    monkeypatch.setattr(tte.time, "perf_counter", lambda: next(clock))
+    one, batched = tte.time_runs(FakeSG, ["a", "b", "c"], [5, None, 9], runs=20, beta_min=1.0, beta_max=9.0,
+                                 seed=3, repeat=2)
+    # every timed call reads the clock twice, one unit apart
+    assert one == 1.0 and batched == 0.5
+    singles = [c for c in calls if len(c) == 1]
+    assert {c[0] for c in singles} == {("a", 5, 0), ("c", 9, 2)} and len(singles) == 2 * 3
+    assert [c for c in calls if len(c) == 2] == [[("a", 5, 0), ("c", 9, 2)]] * 3
+    # nothing to time when every instance was censored
+    o, b = tte.time_runs(FakeSG, ["a"], [None], 20, 1.0, 9.0, 3)
+    assert math.isnan(o) and math.isnan(b)
