@@ -252,6 +252,10 @@ int32_t run_sweep_graphs(int S, uint32_t* base, cudaStream_t st, LaunchLog& log,
 // Runs of at least this many sweeps go through graphs; shorter ones launch directly.
 constexpr int kGraphMinSweeps = 16;
 
+// Sweeps per launch of the thread-block-cluster PT kernel (state carried in device memory
+// between launches).
+constexpr int kClusterChunkSweeps = 2000;
+
 // Instances per launch group: the grid's y extent holds one instance per row.
 constexpr size_t kMaxGroup = 65535;
 
@@ -574,7 +578,22 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     xa.K = K;
     xa.sweep_base = nullptr;
     unsigned* done = d_done.as<unsigned>();
-    if (S >= kGraphMinSweeps) {
+    // K <= 32 with unit couplings: chunks of sweeps on thread-block clusters, one per
+    // instance, the lattice in shared memory (ptcluster.cu)
+    const int Ccl = unit_j && Wn == 1 && S > 0 ? pt_cluster_blocks(I, L, K) : 0;
+    if (Ccl > 0) {
+        bool aligned = true;
+        for (int a = 0; a < I; ++a) aligned &= (reinterpret_cast<uintptr_t>(jp[I + a]) & 15u) == 0;
+        const ExchangeTablesDev xd{d_xtab.as<uint32_t>(), d_xoff.as<uint32_t>(), d_xlen.as<uint32_t>(),
+                                   d_xtail.as<uint32_t>()};
+        for (int s0 = 0; s0 < S; s0 += kClusterChunkSweeps) {
+            const int s1 = std::min(S, s0 + kClusterChunkSweeps);
+            SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * N * K * (s1 - s0), st, [&] {
+                return launch_pt_cluster(spins, j1p, kp, d_thr.as<uint32_t>(), perm, inv, E, acc, minE, xd,
+                                         d_flag.as<int>() + 1, I, L, K, Ccl, s0, s1, aligned, st);
+            }));
+        }
+    } else if (S >= kGraphMinSweeps) {
         ExchangeArgs xg = xa;
         xg.sweep_base = d_base.as<uint32_t>();
         SG_RET(run_sweep_graphs(S, d_base.as<uint32_t>(), st, log, 2, (int64_t)I * N * K,
@@ -590,7 +609,7 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
                                     return SG_OK;
                                 }));
     }
-    for (int s = 0; s < (S >= kGraphMinSweeps ? 0 : S); ++s) {
+    for (int s = 0; s < (S >= kGraphMinSweeps || Ccl > 0 ? 0 : S); ++s) {
         bool fused = false;
         for (int c = 0; c < 2; ++c)
             SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * K, st, [&] {

@@ -391,3 +391,39 @@ def test_planes_in_shared_memory_equal_global(sg, monkeypatch, L, R, S):
     for other in (glob, rows):
         assert np.array_equal(smem["spins"], other["spins"]) and np.array_equal(smem["E"], other["E"])
     _sa_compare(sg, inst, J3, egs, R, S, 0.1, 3.0, seed=4, reps=[0, R // 2, R - 1])
+
+
+# --------------------------------------------------------------------------- PT on clusters
+
+@pytest.mark.parametrize("L,K,S,I", [(2, 3, 10, 1), (4, 5, 30, 2), (6, 32, 7, 1), (8, 8, 20, 1),
+                                     (12, 17, 10, 1), (16, 32, 15, 3), (64, 32, 5, 2)])
+def test_pt_cluster_kernel_equals_row_kernels_and_oracle(sg, monkeypatch, L, K, S, I):
+    """PT with every sweep of a chunk in one launch, one thread-block cluster per instance
+    holding the lattice in shared memory (exchange decided in every block from the
+    cluster's energy sums): identical to the row kernels and to the oracle.  One z-plane
+    per block (L = 2, 6), uneven half rows (L = 12), several instances, ragged K."""
+    insts = [sg.Instance.create(L, 8800 + 10 * L + k) for k in range(I)]
+    params = [dict(temps=K, sweeps=S, beta_min=0.2, beta_max=3.0, seed=41, instance_id=k) for k in range(I)]
+    monkeypatch.setenv("SG_PT_CLUSTER", "1")
+    a = sg.pt_run_batch(insts, params, spins="host")
+    monkeypatch.setenv("SG_PT_CLUSTER", "0")
+    b = sg.pt_run_batch(insts, params, spins="host")
+    for x, y in zip(a, b):
+        for k in ("spins", "E", "perm", "accepts"):
+            assert np.array_equal(x[k], y[k]), k
+        assert x["minE"] == y["minE"]
+    J3, _, egs = insts[-1].get()
+    _pt_compare(sg, insts[-1], J3, egs, K, S, 0.2, 3.0, seed=41, iid=I - 1, res=a[-1])
+
+
+def test_pt_cluster_kernel_chunks(sg, monkeypatch):
+    """A run longer than one cluster launch (chunks of 2000 sweeps, the state carried in
+    device memory between them) equals the row kernels."""
+    inst = sg.Instance.create(4, 8899)
+    monkeypatch.setenv("SG_PT_CLUSTER", "1")
+    a = sg.pt_run(inst, 6, 4100, 0.2, 3.0, seed=5, spins="host")
+    monkeypatch.setenv("SG_PT_CLUSTER", "0")
+    b = sg.pt_run(inst, 6, 4100, 0.2, 3.0, seed=5, spins="host")
+    for k in ("spins", "E", "perm", "accepts"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["minE"] == b["minE"]
