@@ -40,6 +40,8 @@ namespace cg = cooperative_groups;
 namespace sg {
 namespace {
 
+// 512 threads (128 registers, no spills): 768 or 1024 threads, and fetching the next item
+// before updating the current one, measured slower (spills)
 constexpr int kThreads = 512;
 constexpr int kWarps = kThreads / 32;
 constexpr int kTieCap = 48;      // queued tie entries per warp
@@ -67,6 +69,7 @@ struct PtcArgs {
     int* status;                    // SG_ETIMEOUT when a bounded wait gave up
     int L, K, C, s_begin, s_end;
     uint32_t Hmagic, Lmagic;        // ceil(2^32 / (L / 2)), ceil(2^32 / L)
+    int bulk;                       // slabs staged by bulk copies (else by plain loads)
     int bulk_signs;                 // the sign slab is 16-byte aligned: bulk copy (else plain loads)
 };
 
@@ -160,14 +163,18 @@ __global__ void __launch_bounds__(kThreads, 1) pt_cluster_kernel(const PtcArgs a
     // ---- stage the slab and its coupling signs in shared memory ----
     if (tid == 0) {
         s_fail = 0;
-        mbar_init(&s_bar, 1);
-        const uint32_t sp_bytes = (uint32_t)slab_words * 4u;
-        const uint32_t sg_bytes = a.bulk_signs ? (uint32_t)slab_words : 0u;
-        mbar_expect_tx(&s_bar, sp_bytes + sg_bytes);
-        bulk_load(slab, g, sp_bytes, &s_bar);
-        if (sg_bytes) bulk_load(sgn, j1, sg_bytes, &s_bar);
+        if (a.bulk) {
+            mbar_init(&s_bar, 1);
+            const uint32_t sp_bytes = (uint32_t)slab_words * 4u;
+            const uint32_t sg_bytes = a.bulk_signs ? (uint32_t)slab_words : 0u;
+            mbar_expect_tx(&s_bar, sp_bytes + sg_bytes);
+            bulk_load(slab, g, sp_bytes, &s_bar);
+            if (sg_bytes) bulk_load(sgn, j1, sg_bytes, &s_bar);
+        }
     }
-    if (!a.bulk_signs)
+    if (!a.bulk)
+        for (int q = tid; q < slab_words; q += kThreads) slab[q] = g[q];
+    if (!a.bulk || !a.bulk_signs)
         for (int q = tid; q < slab_words; q += kThreads) sgn[q] = j1[q];
     if (tid < 32) {
         s_rung[tid] = a.rung_of_slot[(size_t)inst * 32 + tid];
@@ -181,7 +188,7 @@ __global__ void __launch_bounds__(kThreads, 1) pt_cluster_kernel(const PtcArgs a
     if (tid < kWarps) s_tie_n[tid] = 0;
     if (tid == 0) s_min = a.minE[inst];
     __syncthreads();  // mbarrier initialised before any thread waits on it
-    if (!mbar_wait_bounded(&s_bar, 0)) s_fail = 1;
+    if (a.bulk && !mbar_wait_bounded(&s_bar, 0)) s_fail = 1;
     // The slot-to-rung map gives every slot its thresholds: per slot rows for ties, and
     // the 24 + 3 bit planes of the word (bit b = slot b) the bit-sliced compare reads.
     auto build_thresholds = [&]() {
@@ -401,7 +408,7 @@ __global__ void __launch_bounds__(kThreads, 1) pt_cluster_kernel(const PtcArgs a
     }
     // after a wait that gave up, copies may still be in flight into this block's shared
     // memory: wait once more (bounded) before the block leaves
-    if (fail) mbar_wait_bounded(&s_bar, 0);
+    if (fail && a.bulk) mbar_wait_bounded(&s_bar, 0);
     cluster.sync();  // no block leaves while another may still read its shared memory
 }
 
@@ -429,17 +436,26 @@ cudaLaunchConfig_t cluster_config(int L, int C, int I, cudaLaunchAttribute* attr
 }  // namespace
 
 // Blocks per cluster for a PT run of I instances of side L with K <= 32 temperatures and
-// unit couplings, or 0 when the row kernels should run it: the largest divisor C <= 8 of
-// L whose slab fits shared memory and for which all I clusters are resident at once (one
-// wave).  Knob SG_PT_CLUSTER = 0 turns the form off, = 1 takes it whenever a slab fits.
+// unit couplings, or 0 when the row kernels should run it.  C is the largest divisor
+// C <= 8 of L whose slab fits shared memory and for which all I clusters are resident at
+// once (one wave).  The cluster form is taken when its estimated time per sweep is below
+// the row kernels', from rates measured on a GB300 (K = 32, L = 8 ... 64, I = 1 ... 15):
+// a cluster sweeps about 7.9 attempts per SM clock with about 4 us of fixed cost per sweep
+// (barriers, exchange); the row kernels about 6.2 attempts per SM clock over the whole GPU
+// with about 10 us per sweep of launch cost.  So it wins for small lattices (L <= 24
+// always, L = 32 from a few instances) and, at L = 64, for 15 instances.  Knob
+// SG_PT_CLUSTER = 0 turns the form off, = 1 takes it whenever a slab fits.
 int pt_cluster_blocks(int I, int L, int K)
 {
     const char* e = getenv("SG_PT_CLUSTER");
     const int knob = e ? atoi(e) : -1;
-    if (knob == 0 || K > 32 || K < 1 || L < 2 || (L & 1)) return 0;
-    int dev = 0, smem = 0;
+    if (knob == 0 || K > 32 || K < 1 || L < 2 || (L & 1) || I < 1) return 0;
+    int dev = 0, smem = 0, sms = 1, clock_khz = 2070000;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev);
+    const double hz = 1e3 * (double)clock_khz;
     for (int C = 8; C >= 1; --C) {
         if (L % C) continue;
         const size_t bytes = dyn_smem(L, C);
@@ -457,7 +473,11 @@ int pt_cluster_blocks(int I, int L, int K)
             cudaGetLastError();
             continue;
         }
-        if (active >= I) return C;
+        if (active < I) continue;
+        const double work = (double)L * L * L * K;  // attempts per sweep of one instance
+        const double t_cluster = 4e-6 + work / (C * 7.9 * hz);
+        const double t_rows = 10e-6 + I * work / (sms * 6.2 * hz);
+        return t_cluster < 0.95 * t_rows ? C : 0;
     }
     return 0;
 }
@@ -493,6 +513,12 @@ int32_t launch_pt_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const Ru
     // the sign bytes of a slab start at z0 * L^2 bytes into the instance's array: a bulk
     // copy needs its address and size to be multiples of 16
     a.bulk_signs = bulk_signs && ((size_t)(L / C) * L * L) % 16 == 0;
+    // knob SG_PT_BULK = 0: plain loads instead of bulk copies (for comparison)
+    static const bool bulk = [] {
+        const char* k = getenv("SG_PT_BULK");
+        return !(k && atoi(k) == 0);
+    }();
+    a.bulk = bulk ? 1 : 0;
     const size_t smem = dyn_smem(L, C);
     if (cudaFuncSetAttribute(pt_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
         cudaSuccess) {

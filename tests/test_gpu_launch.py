@@ -46,7 +46,7 @@ np.savez(sys.argv[1], **out)
 
 def _run_child(tmp_path, pdl):
     path = str(tmp_path / f"pdl{pdl}.npz")
-    env = dict(os.environ, SG_PDL=str(pdl), SG_SA_CLUSTER="0")
+    env = dict(os.environ, SG_PDL=str(pdl), SG_SA_CLUSTER="0", SG_PT_CLUSTER="0")
     p = subprocess.run([sys.executable, "-c", _CHILD, path, repr(CASES)], cwd=ROOT, env=env,
                        capture_output=True, text=True, timeout=600)
     assert p.returncode == 0, p.stderr[-3000:]
