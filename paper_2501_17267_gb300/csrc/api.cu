@@ -252,9 +252,34 @@ int32_t run_sweep_graphs(int S, uint32_t* base, cudaStream_t st, LaunchLog& log,
 // Runs of at least this many sweeps go through graphs; shorter ones launch directly.
 constexpr int kGraphMinSweeps = 16;
 
-// Sweeps per launch of the thread-block-cluster PT kernel (state carried in device memory
-// between launches).
+// Sweeps per launch of the thread-block-cluster and cooperative PT kernels (state carried
+// in device memory between launches).
 constexpr int kClusterChunkSweeps = 2000;
+
+// Polls a bounded wait of the cooperative PT kernel makes before it gives up (about 64 ns
+// each, so several seconds); SG_WAIT_LIMIT overrides it (a test sets 1 to make a wait give
+// up on purpose).
+long long wait_limit()
+{
+    const char* e = getenv("SG_WAIT_LIMIT");
+    if (e && *e) {
+        const long long v = atoll(e);
+        if (v >= 0) return v;
+    }
+    return 1ll << 26;
+}
+
+// Whether a PT batch goes to the cooperative kernel.  Knob SG_PT_COOP = 0 / 1 turns it
+// off / on; otherwise it is off.
+bool pt_coop_wanted(int I, int L, int K)
+{
+    const char* e = getenv("SG_PT_COOP");
+    if (e && *e) return atoi(e) != 0;
+    (void)I;
+    (void)L;
+    (void)K;
+    return false;
+}
 
 // Instances per launch group: the grid's y extent holds one instance per row.
 constexpr size_t kMaxGroup = 65535;
@@ -578,10 +603,36 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     xa.K = K;
     xa.sweep_base = nullptr;
     unsigned* done = d_done.as<unsigned>();
-    // K <= 32 with unit couplings: chunks of sweeps on thread-block clusters, one per
-    // instance, the lattice in shared memory (ptcluster.cu)
-    const int Ccl = unit_j && Wn == 1 && S > 0 ? pt_cluster_blocks(I, L, K) : 0;
-    if (Ccl > 0) {
+    // K <= 32 with unit couplings: chunks of sweeps in one cooperative launch holding the
+    // batch in shared memory (ptcoop.cu), or on thread-block clusters, one per instance
+    // (ptcluster.cu)
+    int coop_blocks = 0;
+    size_t coop_smem = 0;
+    std::vector<int> cplan;
+    if (unit_j && Wn == 1 && S > 0 && pt_coop_wanted(I, L, K)) cplan = pt_coop_plan(I, L, K, &coop_blocks, &coop_smem);
+    const int Ccl = cplan.empty() && unit_j && Wn == 1 && S > 0 ? pt_cluster_blocks(I, L, K) : 0;
+    if (!cplan.empty()) {
+        DevBuf d_cflags, d_csums, d_cabort, d_cpub, d_cplan;
+        SG_RET(d_cflags.alloc(sizeof(int) * (size_t)coop_blocks, st));
+        SG_RET(d_csums.alloc(sizeof(int) * (size_t)I * 3 * 32, st));
+        SG_RET(d_cabort.alloc(sizeof(int), st));
+        SG_RET(d_cpub.alloc(sizeof(uint32_t) * (size_t)coop_blocks * 4 * L * (L / 2), st));
+        SG_RET(d_cplan.alloc(sizeof(int) * cplan.size(), st));
+        SG_TRY_CUDA(cudaMemcpyAsync(d_cplan.as<void>(), cplan.data(), sizeof(int) * cplan.size(),
+                                    cudaMemcpyHostToDevice, st));
+        const CoopScratch cs{d_cflags.as<int>(), d_csums.as<int>(), d_cabort.as<int>(), d_cpub.as<uint32_t>(),
+                             d_cplan.as<int>()};
+        const ExchangeTablesDev xd{d_xtab.as<uint32_t>(), d_xoff.as<uint32_t>(), d_xlen.as<uint32_t>(),
+                                   d_xtail.as<uint32_t>()};
+        const long long limit = wait_limit();
+        for (int s0 = 0; s0 < S; s0 += kClusterChunkSweeps) {
+            const int s1 = std::min(S, s0 + kClusterChunkSweeps);
+            SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * N * K * (s1 - s0), st, [&] {
+                return launch_pt_coop(spins, j1p, kp, d_thr.as<uint32_t>(), perm, inv, E, acc, minE, xd,
+                                      d_flag.as<int>() + 1, cs, I, L, K, coop_blocks, coop_smem, s0, s1, limit, st);
+            }));
+        }
+    } else if (Ccl > 0) {
         bool aligned = true;
         for (int a = 0; a < I; ++a) aligned &= (reinterpret_cast<uintptr_t>(jp[I + a]) & 15u) == 0;
         const ExchangeTablesDev xd{d_xtab.as<uint32_t>(), d_xoff.as<uint32_t>(), d_xlen.as<uint32_t>(),
@@ -609,7 +660,7 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
                                     return SG_OK;
                                 }));
     }
-    for (int s = 0; s < (S >= kGraphMinSweeps || Ccl > 0 ? 0 : S); ++s) {
+    for (int s = 0; s < (S >= kGraphMinSweeps || Ccl > 0 || !cplan.empty() ? 0 : S); ++s) {
         bool fused = false;
         for (int c = 0; c < 2; ++c)
             SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * K, st, [&] {

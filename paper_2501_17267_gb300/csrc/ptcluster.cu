@@ -33,6 +33,7 @@
 
 #include "metropolis.cuh"
 #include "philox.cuh"
+#include "ptslab.cuh"
 #include "sg_internal.h"
 
 namespace cg = cooperative_groups;
@@ -40,15 +41,8 @@ namespace cg = cooperative_groups;
 namespace sg {
 namespace {
 
-// 512 threads (128 registers, no spills): 768 or 1024 threads, and fetching the next item
-// before updating the current one, measured slower (spills)
-constexpr int kThreads = 512;
-constexpr int kWarps = kThreads / 32;
-constexpr int kTieCap = 48;      // queued tie entries per warp
-constexpr int kTieResolve = 16;  // a warp decides its queue from this many (a row of a warp adds <= 32)
-constexpr int kThrStride = 17;   // per-slot threshold row stride in shared memory (bank spread)
-constexpr int kVBits = 8;        // per-thread energy counters: up to 42 items of at most 6
-constexpr int kFoldItems = 42;
+using pts::kThreads;
+using pts::kWarps;
 // bounded waits: iterations of mbarrier.try_wait (each may suspend the thread briefly)
 constexpr int kWaitSpins = 1 << 22;
 
@@ -121,24 +115,12 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
     return false;
 }
 
-__device__ __forceinline__ uint32_t valid_bits(int K)
-{
-    return K >= 32 ? 0xFFFFFFFFu : (1u << K) - 1u;
-}
-
 __global__ void __launch_bounds__(kThreads, 1) pt_cluster_kernel(const PtcArgs a)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ uint32_t s_thr[32 * kThrStride];  // per slot: thresholds of its rung, k = 0 .. 15
-    __shared__ uint4 s_tp4[8];  // threshold-byte plane j of k = 2, 4, 6 (bit b: slot b)
-    __shared__ uint4 s_lz;       // slots whose threshold of k = 2, 4, 6 has nonzero low 24 bits
-    __shared__ uint32_t s_rthr[32 * kThrRow];     // per rung (K <= 32): the threshold rows
-    __shared__ int s_E[32];                       // this block's energy sums of a colour-1 half sweep
-    __shared__ int s_Etot[2][32];                 // block 0: the cluster's sums, by sweep parity
-    __shared__ uint32_t s_acc[32];                // block 0: accepted swaps of rung pairs in this launch
-    __shared__ uint8_t s_rung[32], s_slot[32];
-    __shared__ int s_tie_n[kWarps];
-    __shared__ int s_min, s_fail;
+    __shared__ pts::Shared sh;
+    __shared__ int s_Etot[2][32];  // block 0: the cluster's sums, by sweep parity
+    __shared__ int s_fail;
     __shared__ __align__(8) uint64_t s_bar;
 
     cg::cluster_group cluster = cg::this_cluster();
@@ -151,12 +133,11 @@ __global__ void __launch_bounds__(kThreads, 1) pt_cluster_kernel(const PtcArgs a
     const int items = zc * L * H;  // sites of one colour in the slab
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const RunKeys key = a.keys[inst];
-    const uint32_t valid = valid_bits(K);
+    const uint32_t valid = pts::valid_bits(K);
 
     uint32_t* slab = reinterpret_cast<uint32_t*>(smem);
-    uint8_t* sgn = smem + (size_t)slab_words * 4;                 // [zc][L][L] sign bytes, logical order
+    uint8_t* sgn = smem + (size_t)slab_words * 4;  // [zc][L][L] sign bytes, logical order
     uint4* s_ties = reinterpret_cast<uint4*>(smem + (((size_t)slab_words * 5 + 15) & ~(size_t)15));
-    uint4* ties = s_ties + warp * kTieCap * 2;                     // per warp: {i, is, -, tie}, {c0, c1, word, -}
     uint32_t* g = a.spins + (size_t)inst * LL * L + (size_t)z0 * LL;
     const uint8_t* j1 = a.j1_ptrs[inst] + (size_t)z0 * LL;
 
@@ -176,41 +157,15 @@ __global__ void __launch_bounds__(kThreads, 1) pt_cluster_kernel(const PtcArgs a
         for (int q = tid; q < slab_words; q += kThreads) slab[q] = g[q];
     if (!a.bulk || !a.bulk_signs)
         for (int q = tid; q < slab_words; q += kThreads) sgn[q] = j1[q];
+    pts::load_state(sh, a.rung_of_slot + (size_t)inst * 32, a.slot_of_rung + (size_t)inst * K, a.thr, K,
+                    a.minE[inst], tid);
     if (tid < 32) {
-        s_rung[tid] = a.rung_of_slot[(size_t)inst * 32 + tid];
-        if (tid < K) s_slot[tid] = a.slot_of_rung[(size_t)inst * K + tid];
-        s_E[tid] = 0;
         s_Etot[0][tid] = 0;
         s_Etot[1][tid] = 0;
-        s_acc[tid] = 0;
     }
-    for (int q = tid; q < K * kThrRow; q += kThreads) s_rthr[q] = a.thr[q];
-    if (tid < kWarps) s_tie_n[tid] = 0;
-    if (tid == 0) s_min = a.minE[inst];
     __syncthreads();  // mbarrier initialised before any thread waits on it
     if (a.bulk && !mbar_wait_bounded(&s_bar, 0)) s_fail = 1;
-    // The slot-to-rung map gives every slot its thresholds: per slot rows for ties, and
-    // the 24 + 3 bit planes of the word (bit b = slot b) the bit-sliced compare reads.
-    auto build_thresholds = [&]() {
-        if (warp == 0) {
-            const uint32_t* row = s_rthr + (int)s_rung[lane] * kThrRow;
-#pragma unroll
-            for (int k = 0; k < kThrRow; ++k) s_thr[lane * kThrStride + k] = row[k];
-            const uint32_t t2 = row[2], t4 = row[4], t6 = row[6];
-#pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const uint32_t p2 = __ballot_sync(0xFFFFFFFFu, mp::threshold_plane_bit(t2, j) != 0u);
-                const uint32_t p4 = __ballot_sync(0xFFFFFFFFu, mp::threshold_plane_bit(t4, j) != 0u);
-                const uint32_t p6 = __ballot_sync(0xFFFFFFFFu, mp::threshold_plane_bit(t6, j) != 0u);
-                if (lane == 0) s_tp4[j] = make_uint4(p2, p4, p6, 0u);
-            }
-            const uint32_t l2 = __ballot_sync(0xFFFFFFFFu, (t2 & 0xFFFFFFu) != 0u);
-            const uint32_t l4 = __ballot_sync(0xFFFFFFFFu, (t4 & 0xFFFFFFu) != 0u);
-            const uint32_t l6 = __ballot_sync(0xFFFFFFFFu, (t6 & 0xFFFFFFu) != 0u);
-            if (lane == 0) s_lz = make_uint4(l2, l4, l6, 0u);
-        }
-    };
-    build_thresholds();
+    pts::build_thresholds(sh, warp, lane);
     // Every block's slab is in place (and every block's failure flag set) before any block
     // reads a neighbour's slab.
     cluster.sync();
@@ -222,22 +177,11 @@ __global__ void __launch_bounds__(kThreads, 1) pt_cluster_kernel(const PtcArgs a
     const uint32_t* up = cluster.map_shared_rank(slab, (r + 1) % C);
     const uint32_t* dn = cluster.map_shared_rank(slab, (r + C - 1) % C);
     int* Etot0 = cluster.map_shared_rank(&s_Etot[0][0], 0);
-
-    // ---- the sweeps ----
     const bool uniform = items % kThreads == 0;  // every lane of a warp has the same item count
-    uint32_t V[kVBits];
-    int nitems = 0;
-    uint32_t sweep = (uint32_t)a.s_begin;
 
-    // item q of a colour: its logical site i, slab position is, the words of the site and
-    // of its six neighbours (z neighbours in another block's slab at the slab's faces),
-    // its coupling sign bits and its eight leading-byte draw planes
-    struct Work {
-        uint32_t i;
-        int is;
-        uint32_t self, n[6], sbits, A[8];
-    };
-    auto fetch = [&](int q, int colour, Work& w) {
+    // item q of a colour: its site, its words (z neighbours in another block's slab at the
+    // slab's faces) and its draws
+    auto fetch = [&](int q, int colour, pts::Work& w, const pts::Updater& u) {
         const int rl = H == 1 ? q : (int)__umulhi((uint32_t)q, a.Hmagic);  // slab row
         const int j = q - rl * H;
         const int zl = (int)__umulhi((uint32_t)rl, a.Lmagic), y = rl - zl * L;
@@ -256,143 +200,44 @@ __global__ void __launch_bounds__(kThreads, 1) pt_cluster_kernel(const PtcArgs a
         w.n[4] = zl + 1 == zc ? up[y * L + pos] : slab[is + LL];
         w.n[5] = zl == 0 ? dn[(zc - 1) * LL + y * L + pos] : slab[is - LL];
         w.sbits = sgn[rowoff + 2 * j + par];
-        mp::lead_planes(w.i, sweep, 0u, key, w.A);
-    };
-    auto fold_thread = [&]() {  // this thread's counters into the block sums (rare)
-        for (int b = 0; b < 32; ++b) {
-            const int e = 6 * nitems - 2 * mp::vcount(V, b);
-            if (e) atomicAdd(&s_E[b], e);
-        }
-#pragma unroll
-        for (int j = 0; j < kVBits; ++j) V[j] = 0;
-        nitems = 0;
-    };
-    // decides the queued ties of this warp (a blind store of the word its owner stored;
-    // in a colour-1 half sweep a decided flip adds 2k to the slot's energy)
-    auto resolve_list = [&](bool energy) {
-        __syncwarp();
-        const int n = min(s_tie_n[warp], kTieCap);
-        for (int e = lane; e < n; e += 32) {
-            const uint4 t = ties[2 * e], u = ties[2 * e + 1];
-            const uint32_t acc =
-                mp::resolve_tie_bits(t.w, u.x, u.y, s_thr, kThrStride, t.x, sweep, 0u, key.k0, key.k1);
-            if (acc) {
-                slab[t.y] = u.z ^ acc;
-                if (energy)
-                    for (uint32_t m = acc; m; m &= m - 1u) {
-                        const int b = __ffs(m) - 1;
-                        const int c = 4 + (int)((u.x >> b) & 1u) + 2 * (int)((u.y >> b) & 1u);
-                        atomicAdd(&s_E[b], 2 * (2 * c - 6));
-                    }
-            }
-        }
-        __syncwarp();
-        if (lane == 0) s_tie_n[warp] = 0;
-        __syncwarp();
-    };
-    auto update = [&](Work& w, bool energy) {
-        uint32_t flip, tie, c0, c1, c2;
-        mp::update_word_unit_smem(w.self, w.n, w.sbits, valid, s_tp4, w.A, &flip, &tie, &c0, &c1, &c2);
-        {
-            const uint4 z = s_lz;
-            tie &= (c1 & z.z) | (~c1 & ((c0 & z.y) | (~c0 & z.x)));  // the others reject
-        }
-        if (tie) {
-            const int p = atomicAdd(&s_tie_n[warp], 1);
-            if (p < kTieCap) {
-                ties[2 * p] = make_uint4(w.i, (uint32_t)w.is, 0u, tie);
-                ties[2 * p + 1] = make_uint4(c0, c1, w.self ^ flip, 0u);
-            } else {  // queue full: decide here
-                const uint32_t acc =
-                    mp::resolve_tie_bits(tie, c0, c1, s_thr, kThrStride, w.i, sweep, 0u, key.k0, key.k1);
-                flip |= acc;
-            }
-        }
-        if (energy) {
-            mp::count_after_flip(flip, c0, c1, c2);
-            mp::vadd3(V, c0, c1, c2);
-            if (++nitems == kFoldItems) fold_thread();
-        }
-        if (flip) slab[w.is] = w.self ^ flip;
+        u.draws(w);
     };
     // one half sweep of `colour` over this block's slab: items q = tid, tid + kThreads, ...
-    auto half = [&](const int colour) {
-        const bool energy = colour == 1;
-        if (energy) {
-#pragma unroll
-            for (int j = 0; j < kVBits; ++j) V[j] = 0;
-            nitems = 0;
-        }
+    auto half = [&](const int colour, uint32_t sweep) {
+        pts::Updater u(sh, slab, s_ties, key, valid, sweep, tid, colour == 1);
         for (int q = tid; q < items; q += kThreads) {
-            Work w;
-            fetch(q, colour, w);
-            update(w, energy);
-            if (uniform) {
-                __syncwarp();
-                if (s_tie_n[warp] >= kTieResolve) resolve_list(energy);
-            }
+            pts::Work w;
+            fetch(q, colour, w, u);
+            u.update(w);
+            if (uniform) u.maybe_resolve();
         }
-        resolve_list(energy);
-        if (energy) {
-            // lane b collects slot b of every lane through a bit transpose per plane
-            uint32_t T[kVBits];
-#pragma unroll
-            for (int jb = 0; jb < kVBits; ++jb) T[jb] = mp::warp_transpose(V[jb], lane);
-            const int n = __reduce_add_sync(0xFFFFFFFFu, nitems);
-            int cnt = 0;
-#pragma unroll
-            for (int jb = 0; jb < kVBits; ++jb) cnt += __popc(T[jb]) << jb;
-            const int e = 6 * n - 2 * cnt;
-            if (e) atomicAdd(&s_E[lane], e);
+        u.resolve();
+        if (colour == 1) {
+            u.energy_to_block();
             __syncthreads();
             if (tid < 32) {  // the block's sums into block 0's buffer of this sweep's parity
-                atomicAdd(&Etot0[(sweep & 1u) * 32 + tid], s_E[tid]);
-                s_E[tid] = 0;
+                atomicAdd(&Etot0[(sweep & 1u) * 32 + tid], sh.E[tid]);
+                sh.E[tid] = 0;
             }
         }
     };
 
     if (!fail) {
-        for (; (int)sweep < a.s_end; ++sweep) {
-            half(0);
+        for (uint32_t sweep = (uint32_t)a.s_begin; (int)sweep < a.s_end; ++sweep) {
+            half(0, sweep);
             cluster.sync();  // colour 0 complete in every slab
             // block 0 clears the other parity's buffer: every block read it after the
             // previous sweep, before the barrier above
             if (r == 0 && tid < 32) s_Etot[(sweep + 1u) & 1u][tid] = 0;
-            half(1);
+            half(1, sweep);
             cluster.sync();  // colour 1 and the energy sums complete
             // the exchange, decided by every block from the cluster's sums (App. D.2)
             if (warp == 0) {
                 const int Eq = Etot0[(sweep & 1u) * 32 + lane];
-                const int k = 2 * lane + (int)(sweep & 1u);
-                const bool pair = k + 1 < K;
-                const int sa = pair ? s_slot[k] : 0, sb = pair ? s_slot[k + 1] : 0;
-                const int Ea = __shfl_sync(0xFFFFFFFFu, Eq, sa), Eb = __shfl_sync(0xFFFFFFFFu, Eq, sb);
-                if (pair) {
-                    const int64_t d = (int64_t)Ea - (int64_t)Eb;
-                    bool accept = d <= 0;
-                    if (!accept) {
-                        const uint32_t u =
-                            philox4x32_10((uint32_t)k, sweep, 0u, kDomainExchange, key.k0, key.k1).v[0];
-                        const uint32_t T =
-                            d <= (int64_t)a.xlen[k] ? a.xtab[a.xoff[k] + (uint32_t)(d - 1)] : a.xtail[k];
-                        accept = u < T;
-                    }
-                    if (accept) {
-                        s_rung[sa] = (uint8_t)(k + 1);
-                        s_rung[sb] = (uint8_t)k;
-                        s_slot[k] = (uint8_t)sb;
-                        s_slot[k + 1] = (uint8_t)sa;
-                        if (r == 0) s_acc[k] += 1u;
-                    }
-                }
-                int m = lane < K ? Eq : 0x7FFFFFFF;
-                m = __reduce_min_sync(0xFFFFFFFFu, m);
-                if (lane == 0 && m < s_min) s_min = m;
+                pts::exchange(sh, Eq, sweep, K, key, a.xtab, a.xoff, a.xlen, a.xtail, r == 0, lane);
                 if (r == 0 && (int)sweep + 1 == a.s_end) a.E[(size_t)inst * 32 + lane] = Eq;
-                __syncwarp();
             }
-            build_thresholds();
+            pts::build_thresholds(sh, warp, lane);
             __syncthreads();
         }
     }
@@ -400,12 +245,9 @@ __global__ void __launch_bounds__(kThreads, 1) pt_cluster_kernel(const PtcArgs a
     // ---- write back ----
     if (!fail)
         for (int q = tid; q < slab_words; q += kThreads) g[q] = slab[q];
-    if (r == 0 && !fail && tid < 32) {
-        a.rung_of_slot[(size_t)inst * 32 + tid] = s_rung[tid];
-        if (tid < K) a.slot_of_rung[(size_t)inst * K + tid] = s_slot[tid];
-        if (tid + 1 < K) a.accepts[(size_t)inst * (K - 1) + tid] += (unsigned long long)s_acc[tid];
-        if (tid == 0) a.minE[inst] = s_min;
-    }
+    if (r == 0 && !fail && warp == 0)
+        pts::store_state(sh, a.rung_of_slot + (size_t)inst * 32, a.slot_of_rung + (size_t)inst * K,
+                         a.accepts + (size_t)inst * (K - 1), a.minE + inst, K, lane);
     // after a wait that gave up, copies may still be in flight into this block's shared
     // memory: wait once more (bounded) before the block leaves
     if (fail && a.bulk) mbar_wait_bounded(&s_bar, 0);
@@ -415,7 +257,7 @@ __global__ void __launch_bounds__(kThreads, 1) pt_cluster_kernel(const PtcArgs a
 size_t dyn_smem(int L, int C)
 {
     const size_t slab_words = (size_t)(L / C) * L * L;
-    return ((slab_words * 5 + 15) & ~(size_t)15) + (size_t)kWarps * kTieCap * 2 * sizeof(uint4);
+    return ((slab_words * 5 + 15) & ~(size_t)15) + pts::kTieBytes;
 }
 
 cudaLaunchConfig_t cluster_config(int L, int C, int I, cudaLaunchAttribute* attr)

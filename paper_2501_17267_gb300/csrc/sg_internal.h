@@ -217,6 +217,23 @@ struct ExchangeTablesDev {
     const uint32_t *tab, *off, *len, *tail;
 };
 int pt_cluster_blocks(int I, int L, int K);
+// ptcoop.cu: the same on one cooperative grid, each instance's rows split into row blocks
+// held in shared memory (one block per SM).  pt_coop_plan gives the per-block plan
+// (instance, rank, first row, rows; then per instance first block and block count; then
+// the largest row count), the block count and the shared memory per block, or an empty plan.
+struct CoopScratch {
+    int* flags;     // [blocks]
+    int* sums;      // [I][3][32]
+    int* abort;     // [1]
+    uint32_t* pub;  // [blocks][2][2][L][L/2]
+    const int* plan;
+};
+std::vector<int> pt_coop_plan(int I, int L, int K, int* blocks, size_t* smem_bytes);
+int32_t launch_pt_coop(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKeys* keys, const uint32_t* thr,
+                       uint8_t* rung_of_slot, uint8_t* slot_of_rung, int32_t* E, unsigned long long* accepts,
+                       int32_t* minE, const ExchangeTablesDev& xt, int* status, const CoopScratch& cs, int I,
+                       int L, int K, int blocks, size_t smem_bytes, int s_begin, int s_end, long long wait_limit,
+                       cudaStream_t st);
 int32_t launch_pt_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKeys* keys, const uint32_t* thr,
                           uint8_t* rung_of_slot, uint8_t* slot_of_rung, int32_t* E, unsigned long long* accepts,
                           int32_t* minE, const ExchangeTablesDev& xt, int* status, int I, int L, int K, int C,

@@ -427,3 +427,61 @@ def test_pt_cluster_kernel_chunks(sg, monkeypatch):
     for k in ("spins", "E", "perm", "accepts"):
         assert np.array_equal(a[k], b[k]), k
     assert a["minE"] == b["minE"]
+
+
+# --------------------------------------------------------------------------- PT on one cooperative grid
+
+@pytest.mark.parametrize("L,K,S,I", [(8, 8, 20, 1), (16, 32, 12, 3), (32, 17, 10, 4), (48, 32, 4, 8),
+                                     (64, 32, 3, 1), (64, 32, 5, 16)])
+def test_pt_coop_kernel_equals_row_kernels_and_oracle(sg, monkeypatch, L, K, S, I):
+    """PT with every sweep of a chunk in one cooperative launch, each instance's rows split
+    into row blocks held in shared memory with one-plane halos exchanged through device
+    memory (flags between neighbouring blocks, a per-instance barrier before the
+    exchange): identical to the row kernels and to the oracle.  One block of 8 rows per
+    plane pair (L = 8), ragged K, the 16 x L = 64 batch on all SMs (9 or 10 blocks per
+    instance), one instance on 64 blocks."""
+    insts = [sg.Instance.create(L, 8900 + 10 * L + k) for k in range(I)]
+    params = [dict(temps=K, sweeps=S, beta_min=0.2, beta_max=3.0, seed=43, instance_id=k) for k in range(I)]
+    monkeypatch.setenv("SG_PT_COOP", "1")
+    a = sg.pt_run_batch(insts, params, spins="host")
+    monkeypatch.setenv("SG_PT_COOP", "0")
+    monkeypatch.setenv("SG_PT_CLUSTER", "0")
+    b = sg.pt_run_batch(insts, params, spins="host")
+    for x, y in zip(a, b):
+        for k in ("spins", "E", "perm", "accepts"):
+            assert np.array_equal(x[k], y[k]), k
+        assert x["minE"] == y["minE"]
+    J3, _, egs = insts[-1].get()
+    _pt_compare(sg, insts[-1], J3, egs, K, S, 0.2, 3.0, seed=43, iid=I - 1, res=a[-1])
+
+
+def test_pt_coop_kernel_chunks(sg, monkeypatch):
+    """A run longer than one cooperative launch (chunks of 2000 sweeps) equals the row kernels."""
+    inst = sg.Instance.create(8, 8998)
+    monkeypatch.setenv("SG_PT_COOP", "1")
+    a = sg.pt_run(inst, 6, 4100, 0.2, 3.0, seed=5, spins="host")
+    monkeypatch.setenv("SG_PT_COOP", "0")
+    monkeypatch.setenv("SG_PT_CLUSTER", "0")
+    b = sg.pt_run(inst, 6, 4100, 0.2, 3.0, seed=5, spins="host")
+    for k in ("spins", "E", "perm", "accepts"):
+        assert np.array_equal(a[k], b[k]), k
+    assert a["minE"] == b["minE"]
+
+
+def test_pt_coop_wait_that_gives_up_reports_timeout(sg, monkeypatch):
+    """Every wait of the cooperative kernel is bounded: with the poll limit set to 0 a wait
+    gives up at once, the blocks stop, and the call returns SG_ETIMEOUT; the context stays
+    usable and the next run (normal limit) is correct."""
+    insts = [sg.Instance.create(64, 8990 + k) for k in range(16)]
+    params = [dict(temps=32, sweeps=20, beta_min=0.2, beta_max=3.0, seed=3, instance_id=k) for k in range(16)]
+    monkeypatch.setenv("SG_PT_COOP", "1")
+    monkeypatch.setenv("SG_WAIT_LIMIT", "0")
+    with pytest.raises(sg.SGError) as e:
+        sg.pt_run_batch(insts, params)
+    assert e.value.code == sg.SG_ETIMEOUT
+    monkeypatch.delenv("SG_WAIT_LIMIT")
+    a = sg.pt_run_batch(insts, params)
+    monkeypatch.setenv("SG_PT_COOP", "0")
+    b = sg.pt_run_batch(insts, params)
+    for x, y in zip(a, b):
+        assert np.array_equal(x["E"], y["E"]) and x["minE"] == y["minE"]
