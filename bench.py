@@ -659,6 +659,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--sweeps", type=int, default=WORK.sweeps,
                     help="sweeps per run (default: the workload's 10^4)")
+    ap.add_argument("--instances", type=int, default=WORK.instances,
+                    help="instances per rank (default: the workload's 16; fewer only for profiling)")
     ap.add_argument("--cpu-sweeps", type=int, default=10)
     ap.add_argument("--ref-sweeps", type=int, default=1)
     ap.add_argument("--no-cpu", action="store_true")
@@ -750,7 +752,7 @@ def main():
 
     S = args.sweeps
     from paper_2501_17267_gb300 import ranks
-    mine = ranks.rank_units(rank, WORK.instances)  # this rank's instances (weak scaling)
+    mine = ranks.rank_units(rank, args.instances)  # this rank's instances (weak scaling)
     insts = [sg.Instance.create(WORK.L, WORK.instance_seed(g), WORK.class_prob, True) for g in mine]
     params = [dict(temps=WORK.temps, sweeps=S, beta_min=WORK.beta_min, beta_max=WORK.beta_max,
                    seed=WORK.run_seed, instance_id=g) for g in mine]
@@ -783,7 +785,7 @@ def main():
     st = sg.stats_read(reset=True)
     ms = ev0.elapsed_time(ev1)
     ms_max = ranks.max_over_ranks(ms, device="cuda")
-    attempts_per_step = WORK.instances * WORK.temps * WORK.L ** 3 * S
+    attempts_per_step = len(mine) * WORK.temps * WORK.L ** 3 * S
     value = ranks.job_rate(attempts_per_step, world, args.steps, ms_max)
     launches = sum(v["launches"] for v in st.values())
 
@@ -830,8 +832,8 @@ def main():
         e_max = ranks.max_over_ranks(e_s, device="cuda")
         K = WORK.temps
         e2e = {"value": ranks.job_rate(attempts_per_step, world, args.steps, 1000.0 * e_max), "unit": UNIT,
-               "h2d_bytes_per_step": WORK.instances * 3 * WORK.L ** 3,
-               "d2h_bytes_per_step": WORK.instances * (8 * K + 4 * K + 8 * (K - 1) + 8 + 8)}
+               "h2d_bytes_per_step": len(mine) * 3 * WORK.L ** 3,
+               "d2h_bytes_per_step": len(mine) * (8 * K + 4 * K + 8 * (K - 1) + 8 + 8)}
 
     serving = None
     if rank == 0 and not args.no_serve:
@@ -854,9 +856,11 @@ def main():
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": launches,
                 "clocks": clk, "min_eps_mean": float(np.mean(mins)),
                 "kernel_stats": st, "serving": serving, "sub_lines": sub_lines}
-        if S != WORK.sweeps:
+        if S != WORK.sweeps or args.instances != WORK.instances:
             line["config"]["sweeps"] = S
-            line["note"] = f"reduced sweeps ({S}) -- not the workload's number"
+            line["config"]["instances"] = args.instances
+            line["note"] = (f"reduced work ({args.instances} instances, {S} sweeps) -- not the workload's "
+                            f"{WORK.instances} x {WORK.sweeps}")
         print(json.dumps(line), flush=True)
     if world > 1:
         torch.distributed.destroy_process_group()

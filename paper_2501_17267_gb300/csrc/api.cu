@@ -256,9 +256,9 @@ constexpr int kGraphMinSweeps = 16;
 // in device memory between launches).
 constexpr int kClusterChunkSweeps = 2000;
 
-// Polls a bounded wait of the cooperative PT kernel makes before it gives up (about 64 ns
-// each, so several seconds); SG_WAIT_LIMIT overrides it (a test sets 1 to make a wait give
-// up on purpose).
+// Polls a bounded wait of the cooperative PT kernel makes before it gives up (each a read
+// through L2, well under a microsecond, so several seconds in all); SG_WAIT_LIMIT
+// overrides it (a test sets 0 to make a wait give up on purpose).
 long long wait_limit()
 {
     const char* e = getenv("SG_WAIT_LIMIT");
@@ -266,7 +266,7 @@ long long wait_limit()
         const long long v = atoll(e);
         if (v >= 0) return v;
     }
-    return 1ll << 26;
+    return 1ll << 24;
 }
 
 // Whether a PT batch goes to the cooperative kernel.  Knob SG_PT_COOP = 0 / 1 turns it
@@ -612,16 +612,17 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     if (unit_j && Wn == 1 && S > 0 && pt_coop_wanted(I, L, K)) cplan = pt_coop_plan(I, L, K, &coop_blocks, &coop_smem);
     const int Ccl = cplan.empty() && unit_j && Wn == 1 && S > 0 ? pt_cluster_blocks(I, L, K) : 0;
     if (!cplan.empty()) {
-        DevBuf d_cflags, d_csums, d_cabort, d_cpub, d_cplan;
+        DevBuf d_cflags, d_csums, d_cabort, d_carr, d_cpub, d_cplan;
         SG_RET(d_cflags.alloc(sizeof(int) * (size_t)coop_blocks, st));
         SG_RET(d_csums.alloc(sizeof(int) * (size_t)I * 3 * 32, st));
         SG_RET(d_cabort.alloc(sizeof(int), st));
+        SG_RET(d_carr.alloc(sizeof(int) * (size_t)I, st));
         SG_RET(d_cpub.alloc(sizeof(uint32_t) * (size_t)coop_blocks * 4 * L * (L / 2), st));
         SG_RET(d_cplan.alloc(sizeof(int) * cplan.size(), st));
         SG_TRY_CUDA(cudaMemcpyAsync(d_cplan.as<void>(), cplan.data(), sizeof(int) * cplan.size(),
                                     cudaMemcpyHostToDevice, st));
-        const CoopScratch cs{d_cflags.as<int>(), d_csums.as<int>(), d_cabort.as<int>(), d_cpub.as<uint32_t>(),
-                             d_cplan.as<int>()};
+        const CoopScratch cs{d_cflags.as<int>(), d_csums.as<int>(), d_cabort.as<int>(), d_carr.as<int>(),
+                             d_cpub.as<uint32_t>(), d_cplan.as<int>()};
         const ExchangeTablesDev xd{d_xtab.as<uint32_t>(), d_xoff.as<uint32_t>(), d_xlen.as<uint32_t>(),
                                    d_xtail.as<uint32_t>()};
         const long long limit = wait_limit();

@@ -96,38 +96,6 @@ __device__ __forceinline__ void update_word_unit(uint32_t self, const uint32_t (
     *tie = need & eq;
 }
 
-// The same update with the threshold planes read from shared memory where they are used:
-// tp4[j] = {plane j of k = 2, of k = 4, of k = 6, -} (j = 0 .. 7, least significant first),
-// and the coupling signs taken from the sign byte one bond at a time, so that few of the
-// word's values are live at once.
-__device__ __forceinline__ void update_word_unit_smem(uint32_t self, const uint32_t (&n)[6], uint32_t sbits,
-                                                      uint32_t valid, const uint4* tp4, const uint32_t (&A)[8],
-                                                      uint32_t* flip, uint32_t* tie, uint32_t* c0, uint32_t* c1,
-                                                      uint32_t* c2)
-{
-    uint32_t a[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) a[q] = self ^ n[q] ^ (0u - ((sbits >> q) & 1u));
-    const uint32_t s1 = a[0] ^ a[1] ^ a[2], k1 = maj3(a[0], a[1], a[2]);
-    const uint32_t s2 = a[3] ^ a[4] ^ a[5], k2 = maj3(a[3], a[4], a[5]);
-    *c0 = s1 ^ s2;
-    const uint32_t t = s1 & s2;
-    *c1 = k1 ^ k2 ^ t;
-    *c2 = maj3(k1, k2, t);
-    const uint32_t need = *c2 & valid;
-    const uint32_t free = ~*c2 & valid;
-    uint32_t lt = 0, eq = 0xFFFFFFFFu;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const uint4 p = tp4[j];
-        const uint32_t T = (*c1 & p.z) | (~*c1 & ((*c0 & p.y) | (~*c0 & p.x)));
-        lt = maj3(~A[j], T, lt);
-        eq &= ~(A[j] ^ T);
-    }
-    *flip = free | (need & lt);
-    *tie = need & eq;
-}
-
 // Satisfied-count planes after flipping `flip` (a flip turns c into 6 - c).
 __device__ __forceinline__ void count_after_flip(uint32_t flip, uint32_t c0, uint32_t& c1, uint32_t& c2)
 {

@@ -58,12 +58,24 @@ struct CoopArgs {
     int* flags;                     // [blocks] half sweeps each block has completed in this launch
     int* sums;                      // [I][3][32] slot energy sums, by sweep mod 3
     int* abort;                     // raised when a wait gave up
+    int* arrived;                   // [I] colour-1 arrivals of each instance's blocks
     uint32_t* pub;                  // [blocks][2 parity][2 side][L][L/2] published halo rows
     const int* plan;                // per block: instance, rank, first row, rows; per instance: first block, blocks
     int L, K, I, s_begin, s_end;
     long long wait_limit;           // polls before a wait gives up
     uint32_t Lmagic, Hmagic;        // ceil(2^32 / L), ceil(2^32 / (L / 2))
 };
+
+// 16 bytes global -> shared without registers (both addresses 16-byte aligned), cached in
+// L2 only; cp_async_wait waits for this thread's copies
+__device__ __forceinline__ void cp_async16(void* dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __device__ __forceinline__ int ld_acquire(const int* p)
 {
@@ -76,19 +88,18 @@ __device__ __forceinline__ void st_release(int* p, int v)
     asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Thread 0 only: waits until flags[f] >= target, polling at most `limit` times (and
-// stopping when the abort word is up).  False when it gave up.
-__device__ bool wait_flag(const CoopArgs& a, int f, int target)
+// Waits until *p >= target, polling at most wait_limit times (and stopping when the abort
+// word is up).  False when it gave up.
+__device__ bool wait_at_least(const CoopArgs& a, const int* p, int target)
 {
     long long polls = 0;
-    while (ld_acquire(a.flags + f) < target) {
+    while (ld_acquire(p) < target) {
         if (ld_acquire(a.abort) != 0) return false;
         if (++polls > a.wait_limit) {
             atomicExch(a.abort, 1);
             atomicExch(a.status, SG_ETIMEOUT);
             return false;
         }
-        __nanosleep(64);
     }
     return true;
 }
@@ -105,7 +116,6 @@ __global__ void __launch_bounds__(kThreads, 1) pt_coop_kernel(const CoopArgs a)
     const int first = iplan[2 * inst], nblk = iplan[2 * inst + 1];
     const int lower = first + (rank + nblk - 1) % nblk, upper = first + (rank + 1) % nblk;
     const int L = a.L, H = L >> 1, LL = L * L, R = LL, K = a.K;
-    const int items = nrows * H;  // sites of one colour in the block's rows (a multiple of 32)
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const RunKeys key = a.keys[inst];
     const uint32_t valid = pts::valid_bits(K);
@@ -133,10 +143,8 @@ __global__ void __launch_bounds__(kThreads, 1) pt_coop_kernel(const CoopArgs a)
     pts::build_thresholds(sh, warp, lane);
     __syncthreads();
 
-    // item q of a colour: its site, its words and its draws
-    auto fetch = [&](int q, int colour, pts::Work& w, const pts::Updater& u) {
-        const int lr = H == 1 ? q : (int)__umulhi((uint32_t)q, a.Hmagic);  // local row
-        const int j = q - lr * H;
+    // site j of local row lr in a half sweep of `colour`: its site, its words and its draws
+    auto fetch = [&](int lr, int j, int colour, pts::Work& w, const pts::Updater& u) {
         const int r = r0 + lr;
         const int z = (int)__umulhi((uint32_t)r, a.Lmagic), y = r - z * L;
         const int par = (y + z + colour) & 1;
@@ -155,6 +163,11 @@ __global__ void __launch_bounds__(kThreads, 1) pt_coop_kernel(const CoopArgs a)
         w.sbits = sgn[lr * L + 2 * j + par];
         u.draws(w);
     };
+    // The rows within L of either end of the block (the only ones that read halo rows, and
+    // the ones the neighbours' halos copy) are updated after the interior, so that the halo
+    // copies run while the interior is updated.
+    const int nbound = min(nrows, 2 * L);
+    auto boundary_row = [&](int k) { return k < L || nrows <= 2 * L ? k : nrows - 2 * L + k; };
     // the colour-`colour` half of local row lr (global row r0 + lr, periodic)
     auto half_of = [&](int lr, int colour) {
         const int r = (r0 + lr + R) % R;
@@ -171,49 +184,89 @@ __global__ void __launch_bounds__(kThreads, 1) pt_coop_kernel(const CoopArgs a)
             out[q] = words[(lr + L) * L + half_of(lr, colour) * H + j];
         }
     };
-    // copies the neighbours' published rows of `colour` into the halos
-    auto take_halos = [&](int h, int colour) {
+    // starts copying the neighbours' published rows of `colour` (half sweep h) into the
+    // halos: 16-byte asynchronous copies, completed by cp_async_wait before the halos are read
+    auto copy_halos_async = [&](int h, int colour) {
         const uint32_t* lo = a.pub + ((size_t)lower * 4 + (size_t)(h & 1) * 2 + 1) * L * H;  // its last L rows
         const uint32_t* hi = a.pub + ((size_t)upper * 4 + (size_t)(h & 1) * 2) * L * H;      // its first L rows
-        for (int q = tid; q < 2 * L * H; q += kThreads) {
-            const int side = q / (L * H), k = q - side * L * H;
-            const int row = k / H, j = k - row * H;
+        const int C4 = H / 4;  // 16-byte chunks of a half row
+        for (int q = tid; q < 2 * L * C4; q += kThreads) {
+            const int side = q / (L * C4), k = q - side * L * C4;
+            const int row = k / C4, c = k - row * C4;
             const int lr = side ? nrows + row : row - L;
-            words[(lr + L) * L + half_of(lr, colour) * H + j] = __ldcg((side ? hi : lo) + k);
+            cp_async16(words + (lr + L) * L + half_of(lr, colour) * H + 4 * c, (side ? hi : lo) + row * H + 4 * c);
         }
+        cp_async_commit();
     };
-    // publishes this block's flag for half sweep h and waits (thread 0) for the two
-    // neighbours, or for every block of the instance; true when the wait completed
-    auto signal_and_wait = [&](int h, bool all) -> bool {
+    // raises this block's flag: its boundary rows of half sweep h are published
+    auto raise_flag = [&](int h) {
         __syncthreads();
         if (tid == 0) {
             __threadfence();
             st_release(a.flags + b, h + 1);
+        }
+    };
+    // waits (two lanes side by side) until both neighbours have published half sweep h - 1;
+    // true when the wait completed
+    auto wait_neighbours = [&](int h) -> bool {
+        if (warp == 0) {
             bool done = true;
-            if (all) {
-                for (int f = first; f < first + nblk && done; ++f) done = wait_flag(a, f, h + 1);
-            } else {
-                done = wait_flag(a, lower, h + 1) && wait_flag(a, upper, h + 1);
+            if (lane < 2) done = wait_at_least(a, a.flags + (lane ? upper : lower), h);
+            done = __all_sync(0xFFFFFFFFu, done);
+            if (lane == 0) {
+                s_ok = done ? 1 : 0;
+                __threadfence();
             }
-            s_ok = done ? 1 : 0;
-            __threadfence();
         }
         __syncthreads();
         return s_ok != 0;
     };
+    // arrives at the instance's barrier (its energy sums are in) and waits for every block
+    // of the instance through the arrival counter; true when the wait completed
+    int barriers = 0;
+    auto instance_barrier = [&]() -> bool {
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(a.arrived + inst, 1);
+            s_ok = wait_at_least(a, a.arrived + inst, nblk * (barriers + 1)) ? 1 : 0;
+            __threadfence();
+        }
+        __syncthreads();
+        ++barriers;
+        return s_ok != 0;
+    };
+    // one phase of a half sweep: `nrow` rows, row k at local row row_of(k)
+    auto phase = [&](pts::Updater& u, int colour, int nrow, auto row_of) {
+        const int n = nrow * H;  // a multiple of 32
+        for (int it = warp; 32 * it < n; it += kWarps) {
+            const int q = 32 * it + lane;
+            const int k = H == 1 ? q : (int)__umulhi((uint32_t)q, a.Hmagic);
+            pts::Work w;
+            fetch(row_of(k), q - k * H, colour, w, u);
+            u.update(w);
+            u.maybe_resolve();
+        }
+        u.resolve();
+    };
 
     bool ok = true;
-    int h = 0;  // half sweeps completed in this launch
+    int h = 0;  // half sweeps begun in this launch
     for (uint32_t sweep = (uint32_t)a.s_begin; ok && (int)sweep < a.s_end; ++sweep) {
-        for (int colour = 0; colour < 2 && ok; ++colour, ++h) {
+        for (int colour = 0; colour < 2; ++colour, ++h) {
             pts::Updater u(sh, words, s_ties, key, valid, sweep, tid, colour == 1);
-            for (int it = warp; 32 * it < items; it += kWarps) {
-                pts::Work w;
-                fetch(32 * it + lane, colour, w, u);
-                u.update(w);
-                u.maybe_resolve();
+            if (h > 0) {  // the neighbours' rows of the previous half sweep into the halos
+                ok = wait_neighbours(h);
+                if (!ok) break;
+                copy_halos_async(h - 1, colour ^ 1);
             }
-            u.resolve();
+            phase(u, colour, nrows - nbound, [&](int k) { return L + k; });
+            cp_async_wait();
+            __syncthreads();
+            phase(u, colour, nbound, boundary_row);
+            __syncthreads();
+            publish(h, colour);
+            raise_flag(h);
             if (colour == 1) {
                 u.energy_to_block();
                 __syncthreads();
@@ -221,22 +274,15 @@ __global__ void __launch_bounds__(kThreads, 1) pt_coop_kernel(const CoopArgs a)
                     atomicAdd(a.sums + ((size_t)inst * 3 + sweep % 3) * 32 + tid, sh.E[tid]);
                     sh.E[tid] = 0;
                 }
-            } else {
-                __syncthreads();
-            }
-            publish(h, colour);
-            // colour 0: the two neighbours; colour 1: every block of the instance (their
-            // energy sums are complete), the neighbours among them
-            ok = signal_and_wait(h, colour == 1);
-            if (!ok) break;
-            take_halos(h, colour);
-            if (colour == 1) {
+                ok = instance_barrier();
+                if (!ok) break;
+                // the exchange, decided by every block from its instance's sums (App. D.2)
                 if (warp == 0) {
                     const int Eq = __ldcg(a.sums + ((size_t)inst * 3 + sweep % 3) * 32 + lane);
                     pts::exchange(sh, Eq, sweep, K, key, a.xtab, a.xoff, a.xlen, a.xtail, rank == 0, lane);
                     if (rank == 0) {
-                        // every block has read the sums of sweep - 1 (before it raised its flag
-                        // for this sweep's colour 0): clear that buffer for sweep + 2
+                        // every block read the sums of sweep - 1 before it arrived at this
+                        // sweep's barrier: clear that buffer for sweep + 2
                         a.sums[((size_t)inst * 3 + (sweep + 2) % 3) * 32 + lane] = 0;
                         if ((int)sweep + 1 == a.s_end) a.E[(size_t)inst * 32 + lane] = Eq;
                     }
@@ -266,15 +312,17 @@ size_t coop_smem(int L, int max_rows)
 }  // namespace
 
 // The block plan of a cooperative PT run of I instances of side L (K <= 32, unit
-// couplings): blocks per instance (as even as the SM count allows, at most L each, so that
-// every block holds at least L rows) and their row ranges (multiples of 32 / gcd(L/2, 32)
-// rows, so a block's sites of one colour fill whole warps).  Empty when the form does
+// couplings, L a multiple of 8): blocks per instance (as even as the SM count allows, at
+// most L each, so that every block holds at least L rows) and their row ranges (multiples
+// of 32 / gcd(L/2, 32) rows, so a block's sites of one colour fill whole warps).  Empty when the form does
 // not apply or its shared memory does not fit.
 std::vector<int> pt_coop_plan(int I, int L, int K, int* blocks, size_t* smem_bytes)
 {
     std::vector<int> plan;
     *blocks = 0;
-    if (K < 1 || K > 32 || L < 4 || (L & 1) || I < 1) return plan;
+    // L a multiple of 8: a block's first and last L rows then hold a multiple of 32 sites of
+    // a colour, so both phases of a half sweep fill whole warps
+    if (K < 1 || K > 32 || L < 8 || (L % 8) || I < 1) return plan;
     int dev = 0, sms = 0, smem = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
@@ -346,6 +394,7 @@ int32_t launch_pt_coop(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKe
     a.flags = cs.flags;
     a.sums = cs.sums;
     a.abort = cs.abort;
+    a.arrived = cs.arrived;
     a.pub = cs.pub;
     a.plan = cs.plan;
     a.L = L;
@@ -361,6 +410,7 @@ int32_t launch_pt_coop(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKe
     SG_TRY_CUDA(cudaMemsetAsync(cs.flags, 0, sizeof(int) * (size_t)blocks, st));
     SG_TRY_CUDA(cudaMemsetAsync(cs.sums, 0, sizeof(int) * (size_t)I * 3 * 32, st));
     SG_TRY_CUDA(cudaMemsetAsync(cs.abort, 0, sizeof(int), st));
+    SG_TRY_CUDA(cudaMemsetAsync(cs.arrived, 0, sizeof(int) * (size_t)I, st));
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(blocks, 1, 1);
     cfg.blockDim = dim3(kThreads, 1, 1);

@@ -40,6 +40,38 @@ struct Shared {
     int min;                        // lowest energy seen
 };
 
+// The same update with the threshold planes read from shared memory where they are used:
+// tp4[j] = {plane j of k = 2, of k = 4, of k = 6, -} (j = 0 .. 7, least significant first),
+// and the coupling signs taken from the sign byte one bond at a time, so that few of the
+// word's values are live at once.
+__device__ __forceinline__ void update_word_unit_smem(uint32_t self, const uint32_t (&n)[6], uint32_t sbits,
+                                                      uint32_t valid, const uint4* tp4, const uint32_t (&A)[8],
+                                                      uint32_t* flip, uint32_t* tie, uint32_t* c0, uint32_t* c1,
+                                                      uint32_t* c2)
+{
+    uint32_t a[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) a[q] = self ^ n[q] ^ (0u - ((sbits >> q) & 1u));
+    const uint32_t s1 = a[0] ^ a[1] ^ a[2], k1 = mp::maj3(a[0], a[1], a[2]);
+    const uint32_t s2 = a[3] ^ a[4] ^ a[5], k2 = mp::maj3(a[3], a[4], a[5]);
+    *c0 = s1 ^ s2;
+    const uint32_t t = s1 & s2;
+    *c1 = k1 ^ k2 ^ t;
+    *c2 = mp::maj3(k1, k2, t);
+    const uint32_t need = *c2 & valid;
+    const uint32_t free = ~*c2 & valid;
+    uint32_t lt = 0, eq = 0xFFFFFFFFu;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const uint4 p = tp4[j];
+        const uint32_t T = (*c1 & p.z) | (~*c1 & ((*c0 & p.y) | (~*c0 & p.x)));
+        lt = mp::maj3(~A[j], T, lt);
+        eq &= ~(A[j] ^ T);
+    }
+    *flip = free | (need & lt);
+    *tie = need & eq;
+}
+
 __device__ __forceinline__ uint32_t valid_bits(int K) { return K >= 32 ? 0xFFFFFFFFu : (1u << K) - 1u; }
 
 // Loads the slot map and thresholds of an instance; every thread of the block calls it.
@@ -159,7 +191,7 @@ struct Updater {
     __device__ __forceinline__ void update(const Work& w)
     {
         uint32_t flip, tie, c0, c1, c2;
-        mp::update_word_unit_smem(w.self, w.n, w.sbits, valid, sh.tp4, w.A, &flip, &tie, &c0, &c1, &c2);
+        update_word_unit_smem(w.self, w.n, w.sbits, valid, sh.tp4, w.A, &flip, &tie, &c0, &c1, &c2);
         {
             const uint4 z = sh.lz;
             tie &= (c1 & z.z) | (~c1 & ((c0 & z.y) | (~c0 & z.x)));  // the others reject

@@ -225,6 +225,7 @@ struct CoopScratch {
     int* flags;     // [blocks]
     int* sums;      // [I][3][32]
     int* abort;     // [1]
+    int* arrived;   // [I]
     uint32_t* pub;  // [blocks][2][2][L][L/2]
     const int* plan;
 };
