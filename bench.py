@@ -799,13 +799,17 @@ def main():
     if sw["launches"] and sw["device_ms"] > 0:
         per_launch_s = sw["device_ms"] / 1000.0 / sw["launches"]
         attempts_per_launch = sw["units"] / sw["launches"]
-        rec = _traffic_record()
+        # the row kernels launch twice per sweep; the cluster and cooperative forms once per
+        # chunk of up to 2000 sweeps (the traffic record covers the row kernel only)
+        rows = sw["launches"] >= 2 * S * args.steps
+        rec = _traffic_record() if rows else None
         roof = _roof(attempts_per_launch / per_launch_s, ATTEMPTS_PER_BLOCK, hbm_views(WORK.temps),
                      _philox_blocks_per_s(sg), sms, sm_mhz, peak, peak_kind,
                      traffic=rec["traffic_bytes_per_launch"] if rec else None,
                      traffic_unit="DRAM bytes per launch (ncu)",
                      algorithmic_bytes_per_launch=attempts_per_launch * BYTES_PER_ATTEMPT,
-                     kernel="sweep_bits_kernel<PT>", launch_ms=1000 * per_launch_s,
+                     kernel="sweep_bits_kernel<PT>" if rows else "pt_cluster_kernel or pt_coop_kernel",
+                     launch_ms=1000 * per_launch_s,
                      attempts_per_launch=attempts_per_launch, share_of_step=sw["device_ms"] / ms)
 
     # end to end: host couplings in, results out, inside the timed region
