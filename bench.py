@@ -522,11 +522,11 @@ def batched_line(sg, args, torch, clocks_cls, local):
 
 # ---------------------------------------------------------------- SA throughput leg
 
-def sa_line(sg, args, torch, clocks_cls, local):
-    """SA throughput: one L=16 instance, 1024 replicas, 1000 sweeps, beta linear 0.1 -> 3.0;
-    a step is one sg_sa_run: 32 words of 32 replicas per site, each word annealed by one
-    thread-block cluster for all 1000 sweeps in a single launch."""
-    w = wl.SA_L16
+def sa_line(sg, args, torch, clocks_cls, local, w=wl.SA_L16):
+    """SA throughput: one instance, R replicas, 1000 sweeps, beta linear 0.1 -> 3.0 (by
+    default L = 16 with 1024 replicas; wl.SA_L4 is L = 4 with 8); a step is one sg_sa_run:
+    each word of 32 replicas annealed by one thread-block cluster for all 1000 sweeps in
+    a single launch."""
     inst = sg.Instance.create(w.L, w.instance_seed(0), w.class_prob, True)
     attempts = w.L ** 3 * w.replicas * w.sweeps
     stream = torch.cuda.current_stream()
@@ -561,15 +561,17 @@ def sa_line(sg, args, torch, clocks_cls, local):
                      _philox_blocks_per_s(sg), sms, sm_mhz, peak, peak_kind, traffic=None,
                      kernel="sa_cluster_kernel" if sw["launches"] <= 4 * steps else "sweep_bits_kernel<SA>",
                      launch_ms=sw["device_ms"] / sw["launches"], share_of_step=sw["device_ms"] / ms,
-                     note="working set 0.5 MB of spin words: L2-resident, so HBM is not what limits it")
+                     note=f"working set {w.L ** 3 * 4 * ((w.replicas + 31) // 32) / 1e6:.3g} MB of spin words: "
+                          "L2-resident, so HBM is not what limits it")
     eps = out["eps"]
     return {"metric": METRIC, "value": attempts * steps / (ms / 1000.0), "unit": UNIT, "n_gpus": 1,
             "steps": steps, "warmup": max(args.warmup, 3), "ms_per_step": ms / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u32",
             "data": "synthetic",
             "config": {"workload": w.name, "L": w.L, "replicas": w.replicas, "sweeps": w.sweeps,
-                       "beta": f"linear {w.beta0}->{w.beta1}", "cache": "L2 flushed (256 MB written) before every timed step; the 0.5 MB of spins "
-                                "stay in L2 across the step's sweeps"},
+                       "beta": f"linear {w.beta0}->{w.beta1}",
+                       "cache": "L2 flushed (256 MB written) before every timed step; the spins then stay in L2 "
+                                "across the step's sweeps"},
             "roofline": roof, "gpu_launches": sum(v["launches"] for v in st.values()), "clocks": clk,
             "eps": {"min": float(min(eps)), "median": float(sorted(eps)[len(eps) // 2]),
                     "max": float(max(eps))}}
@@ -673,7 +675,7 @@ def main():
     ap.add_argument("--no-sub", action="store_true",
                     help="skip the SA L=16 and batched sub-lines of the pt line")
     ap.add_argument("--serve-seconds", type=float, default=None,
-                    help="arrival window (default: 10 s in the pt line, the workload's 60 s alone)")
+                    help="arrival window (default: the workload's 60 s)")
     ap.add_argument("--serve-baseline-seconds", type=float, default=None,
                     help="window of the one-request-at-a-time comparison (default 5 s / 10 s)")
     ap.add_argument("--serve-baseline-limit", type=float, default=30.0,
@@ -686,7 +688,7 @@ def main():
     args = ap.parse_args()
     alone = args.workload == "serving"
     if args.serve_seconds is None:
-        args.serve_seconds = wl.SERVING.duration_s if alone else 10.0
+        args.serve_seconds = wl.SERVING.duration_s
     if args.serve_baseline_seconds is None:
         args.serve_baseline_seconds = 10.0 if alone else 5.0
 
@@ -847,7 +849,8 @@ def main():
     # SA instances in one persistent launch
     sub_lines = None
     if rank == 0 and not args.no_sub:
-        sub_lines = {"sa_L16": sa_line(sg, args, torch, ClockSampler, local),
+        sub_lines = {"sa_L4": sa_line(sg, args, torch, ClockSampler, local, wl.SA_L4),
+                     "sa_L16": sa_line(sg, args, torch, ClockSampler, local),
                      "batched": batched_line(sg, args, torch, ClockSampler, local)}
     barrier()
 
