@@ -25,7 +25,12 @@ namespace cg = cooperative_groups;
 namespace sg {
 namespace {
 
-constexpr int kBlock = 256;
+constexpr int kBlock = 256;  // single runs: about one word per thread per half sweep at L = 16
+// Batches (planes of up to L = 48 per cluster, tens of words per thread per half sweep):
+// 768 threads per block measured fastest on the 512-instance uneven batch -- 1.95 s per
+// step against 2.10 at 512, 1.97 at 1024 and 2.89 at 256 -- although at 85 registers a
+// thread spills about 100 bytes: more warps hide the update's dependencies better.
+constexpr int kListBlock = 768;
 constexpr int kTieCap = 32;  // queued tie entries per warp
 
 struct ClusterArgs {
@@ -57,6 +62,7 @@ struct PlaneRun {
 
 // Called by every thread of every block of the cluster; slab: dynamic shared memory of
 // at least (L / C) * L * L words.  Ends with the plane written back and a cluster barrier.
+template <int NT>
 __device__ __forceinline__ void anneal_plane(const PlaneRun& p, const int C, uint32_t* slab, uint4* s_ties,
                                              int* s_tie_n)
 {
@@ -122,8 +128,8 @@ __device__ __forceinline__ void anneal_plane(const PlaneRun& p, const int C, uin
         if (sw < p.s_end && tid < items) mp::lead_planes((colour ? first1 : first0).i, (uint32_t)sw, (uint32_t)w, key, A0);
     };
 
-    for (int q = tid; q < slab_words; q += kBlock) slab[q] = g[(size_t)(z0 * LL + q) * p.stride];
-    if (tid < kBlock / 32) s_tie_n[tid] = 0;
+    for (int q = tid; q < slab_words; q += NT) slab[q] = g[(size_t)(z0 * LL + q) * p.stride];
+    if (tid < NT / 32) s_tie_n[tid] = 0;
     cluster.barrier_arrive();
     draws_ahead(p.s_begin, 0);
     cluster.barrier_wait();  // every slab loaded before any block reads its neighbours'
@@ -142,7 +148,7 @@ __device__ __forceinline__ void anneal_plane(const PlaneRun& p, const int C, uin
         }
         // one half sweep of colour `colour`; `fst`: this thread's first item of that colour
         auto half = [&](const int colour, const Site& fst) {
-            for (int q = tid; q < items; q += kBlock) {
+            for (int q = tid; q < items; q += NT) {
                 const Site t = q == tid ? fst : site_of(q, colour);
                 const uint32_t self = slab[t.is];
                 uint32_t n[6];
@@ -195,7 +201,7 @@ __device__ __forceinline__ void anneal_plane(const PlaneRun& p, const int C, uin
         half(0, first0);
         half(1, first1);
     }
-    for (int q = tid; q < slab_words; q += kBlock) g[(size_t)(z0 * LL + q) * p.stride] = slab[q];
+    for (int q = tid; q < slab_words; q += NT) g[(size_t)(z0 * LL + q) * p.stride] = slab[q];
     cluster.sync();  // no block goes on (or leaves) while another may still read its slab
 }
 
@@ -217,7 +223,7 @@ __global__ void __launch_bounds__(kBlock) sa_cluster_kernel(const ClusterArgs a)
     p.s_begin = 0;
     p.s_end = a.S;
     p.Hmagic = a.Hmagic;
-    anneal_plane(p, a.C, slab, s_ties, s_tie_n);
+    anneal_plane<kBlock>(p, a.C, slab, s_ties, s_tie_n);
 }
 
 // Persistent form for batches (batch.cu's planes of one word, [N][1]): clusters take
@@ -225,13 +231,13 @@ __global__ void __launch_bounds__(kBlock) sa_cluster_kernel(const ClusterArgs a)
 // every plane's side is a multiple of C.
 // (Registers are not capped: one block per SM without spills measured 8 % faster on the
 // uneven-batch workload than two per SM with a 128-register cap.)
-__global__ void __launch_bounds__(kBlock, 1) sa_cluster_list_kernel(const Plane* __restrict__ planes,
+__global__ void __launch_bounds__(kListBlock, 1) sa_cluster_list_kernel(const Plane* __restrict__ planes,
                                                                  const int* __restrict__ order, int n,
                                                                  unsigned* __restrict__ next, int C)
 {
     extern __shared__ uint32_t slab[];
-    __shared__ uint4 s_ties[(kBlock / 32) * kTieCap * 2];
-    __shared__ int s_tie_n[kBlock / 32];
+    __shared__ uint4 s_ties[(kListBlock / 32) * kTieCap * 2];
+    __shared__ int s_tie_n[kListBlock / 32];
     __shared__ int s_item;
     cg::cluster_group cluster = cg::this_cluster();
     const int r = (int)cluster.block_rank();
@@ -256,7 +262,7 @@ __global__ void __launch_bounds__(kBlock, 1) sa_cluster_list_kernel(const Plane*
         p.s_begin = q.s_begin;
         p.s_end = q.s_end;
         p.Hmagic = q.Hmagic;
-        anneal_plane(p, C, slab, s_ties, s_tie_n);  // ends with a cluster barrier
+        anneal_plane<kListBlock>(p, C, slab, s_ties, s_tie_n);  // ends with a cluster barrier
     }
 }
 
@@ -309,7 +315,7 @@ int sa_cluster_blocks(int I, int L, int Wn, int64_t half_sweep_attempts)
 
 namespace {
 // Resident clusters of C blocks with `smem` bytes each for `fn`, or 0.
-int active_clusters(const void* fn, int C, size_t smem)
+int active_clusters(const void* fn, int C, size_t smem, int threads)
 {
     if (smem > 48 * 1024 &&
         cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
@@ -318,7 +324,7 @@ int active_clusters(const void* fn, int C, size_t smem)
     }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(C, 1, 1);
-    cfg.blockDim = dim3(kBlock, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -347,7 +353,7 @@ int sa_cluster_list_blocks(const int* Ls, int n, int max_L)
         if (!ok) continue;
         const size_t bytes = (size_t)(max_L / C) * max_L * max_L * 4;
         if (bytes + 12 * 1024 > (size_t)smem) continue;
-        if (active_clusters((const void*)sa_cluster_list_kernel, C, bytes) > 0) return C;
+        if (active_clusters((const void*)sa_cluster_list_kernel, C, bytes, kListBlock) > 0) return C;
     }
     return 0;
 }
@@ -356,14 +362,14 @@ int32_t launch_sa_cluster_planes(const Plane* d_planes, const int* d_order, int 
                                  int max_L, cudaStream_t st)
 {
     const size_t smem = (size_t)(max_L / C) * max_L * max_L * 4;
-    const int clusters = active_clusters((const void*)sa_cluster_list_kernel, C, smem);
+    const int clusters = active_clusters((const void*)sa_cluster_list_kernel, C, smem, kListBlock);
     if (clusters < 1) {
         set_error("sa_cluster_list_kernel: no cluster of %d blocks with %zu bytes fits", C, smem);
         return SG_ECUDA;
     }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(C * std::min(clusters, n), 1, 1);
-    cfg.blockDim = dim3(kBlock, 1, 1);
+    cfg.blockDim = dim3(kListBlock, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
