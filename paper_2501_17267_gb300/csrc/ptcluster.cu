@@ -62,6 +62,7 @@ struct PtcArgs {
     const uint32_t* xtail;
     int* status;                    // SG_ETIMEOUT when a bounded wait gave up
     int L, K, C, s_begin, s_end;
+    const uint32_t* sweep_base;     // if set, sweeps run from *sweep_base + s_begin to *sweep_base + s_end
     uint32_t Hmagic, Lmagic;        // ceil(2^32 / (L / 2)), ceil(2^32 / L)
     int bulk;                       // slabs staged by bulk copies (else by plain loads)
     int bulk_signs;                 // the sign slab is 16-byte aligned: bulk copy (else plain loads)
@@ -222,8 +223,11 @@ __global__ void __launch_bounds__(kThreads, 1) pt_cluster_kernel(const PtcArgs a
         }
     };
 
+    // a sweep base in device memory lets a captured graph replay the launch for later sweeps
+    const uint32_t sb = a.sweep_base ? *a.sweep_base : 0u;
+    const uint32_t s_end = sb + (uint32_t)a.s_end;
     if (!fail) {
-        for (uint32_t sweep = (uint32_t)a.s_begin; (int)sweep < a.s_end; ++sweep) {
+        for (uint32_t sweep = sb + (uint32_t)a.s_begin; sweep < s_end; ++sweep) {
             half(0, sweep);
             cluster.sync();  // colour 0 complete in every slab
             // block 0 clears the other parity's buffer: every block read it after the
@@ -235,7 +239,7 @@ __global__ void __launch_bounds__(kThreads, 1) pt_cluster_kernel(const PtcArgs a
             if (warp == 0) {
                 const int Eq = Etot0[(sweep & 1u) * 32 + lane];
                 pts::exchange(sh, Eq, sweep, K, key, a.xtab, a.xoff, a.xlen, a.xtail, r == 0, lane);
-                if (r == 0 && (int)sweep + 1 == a.s_end) a.E[(size_t)inst * 32 + lane] = Eq;
+                if (r == 0 && sweep + 1 == s_end) a.E[(size_t)inst * 32 + lane] = Eq;
             }
             pts::build_thresholds(sh, warp, lane);
             __syncthreads();
@@ -327,9 +331,10 @@ int pt_cluster_blocks(int I, int L, int K)
 int32_t launch_pt_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKeys* keys, const uint32_t* thr,
                           uint8_t* rung_of_slot, uint8_t* slot_of_rung, int32_t* E, unsigned long long* accepts,
                           int32_t* minE, const ExchangeTablesDev& xt, int* status, int I, int L, int K, int C,
-                          int s_begin, int s_end, bool bulk_signs, cudaStream_t st)
+                          int s_begin, int s_end, bool bulk_signs, cudaStream_t st, const uint32_t* sweep_base)
 {
     PtcArgs a{};
+    a.sweep_base = sweep_base;
     a.spins = reinterpret_cast<uint32_t*>(spins);
     a.j1_ptrs = j1_ptrs;
     a.keys = keys;

@@ -100,6 +100,7 @@ struct Request {
     sg_result result{};
     std::unique_ptr<sg_instance, int32_t (*)(sg_instance*)> inst{nullptr, sg_instance_destroy};
     int mode = kPlanes;
+    int ptc = -1;              // PT: blocks per cluster of the cluster kernel, 0: row kernels (-1: not chosen yet)
     int L = 0, Wn = 0, Rp = 0, WG = 1;
     int64_t N = 0;
     int64_t target = 0;        // done when min energy <= target
@@ -414,9 +415,19 @@ int32_t capture_chunk(Request* q, int n, cudaGraphExec_t* out)
         xa.K = q->req.width;
         xa.sweep_base = base;
     }
+    // PT of a lattice the cluster kernel sweeps faster (its cost model; small L): the
+    // chunk is one launch of it instead of two launches per sweep
+    if (q->mode == kPT && q->ptc < 0)
+        q->ptc = unit && q->Wn == 1 ? pt_cluster_blocks(1, q->L, q->req.width) : 0;
     SG_TRY_CUDA(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     int32_t rc = SG_OK;
-    for (int c = 0; c < n && rc == SG_OK; ++c) {
+    if (q->mode == kPT && q->ptc > 0) {
+        const ExchangeTablesDev xd{xa.xtab, xa.xoff, xa.xlen, xa.xtail};
+        const bool aligned = (reinterpret_cast<uintptr_t>(q->at<uint8_t>(y.j1)) & 15u) == 0;
+        rc = launch_pt_cluster(spins, j1p, kp, thr, xa.rung_of_slot, xa.slot_of_rung, xa.E, xa.accepts, xa.minE, xd,
+                               status, 1, q->L, q->req.width, q->ptc, 0, n, aligned, st, base);
+    }
+    for (int c = 0; c < n && rc == SG_OK && !(q->mode == kPT && q->ptc > 0); ++c) {
         if (q->mode == kRowsSA) {
             for (int colour = 0; colour < 2 && rc == SG_OK; ++colour)
                 rc = launch_sweep_rows_sa(spins, j6p, j1p, kp, thr, unit, 1, q->L, q->Wn, q->req.width,

@@ -213,6 +213,7 @@ int32_t launch_pt_exchange(const ExchangeArgs& x, int I, uint32_t sweep, cudaStr
 // launch, one thread-block cluster of C blocks per instance (lattice in shared memory).
 // pt_cluster_blocks gives C, or 0 when the row kernels should run the batch.
 // bulk_signs: every instance's sign array is 16-byte aligned (slabs then come in by bulk copies).
+// sweep_base: if set, the sweeps are *sweep_base + [s_begin, s_end) (graph replays).
 struct ExchangeTablesDev {
     const uint32_t *tab, *off, *len, *tail;
 };
@@ -238,7 +239,8 @@ int32_t launch_pt_coop(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKe
 int32_t launch_pt_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKeys* keys, const uint32_t* thr,
                           uint8_t* rung_of_slot, uint8_t* slot_of_rung, int32_t* E, unsigned long long* accepts,
                           int32_t* minE, const ExchangeTablesDev& xt, int* status, int I, int L, int K, int C,
-                          int s_begin, int s_end, bool bulk_signs, cudaStream_t st);
+                          int s_begin, int s_end, bool bulk_signs, cudaStream_t st,
+                          const uint32_t* sweep_base = nullptr);
 int32_t launch_pt_setup(const unsigned long long* E64, int32_t* E, uint8_t* rung_of_slot,
                         uint8_t* slot_of_rung, unsigned long long* accepts, int32_t* minE,
                         int I, int Rp, int K, cudaStream_t st);

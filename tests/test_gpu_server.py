@@ -88,6 +88,21 @@ def test_pt_request_matches_pt_run(sg):
         assert res["min_eps"] == pytest.approx((exp["minE"] - exp["e_gs"]) / abs(exp["e_gs"]))
 
 
+def test_pt_request_on_clusters_matches_row_kernels(sg, monkeypatch):
+    """Small PT requests run as one cluster-kernel launch per chunk (sweep index in device
+    memory, replayed as a graph); the same requests run through the row kernels give the
+    same minimum energies and sweep counts (32 temperatures; L = 8 and 16)."""
+    chunk = 25
+    reqs = [sg.request(sg.SG_REQ_PT, L, seed=2024 + L, width=32, beta0=0.2, beta1=3.0, eps_target=0.0,
+                       sweep_cap=100, run_seed=3 + L) for L in (8, 16)]
+    got = _solve(sg, reqs, chunk)
+    monkeypatch.setenv("SG_PT_CLUSTER", "0")
+    for req, res in zip(reqs, got):
+        exp = _expected_pt(sg, req, chunk)
+        assert res["status"] == sg.SG_OK
+        assert (res["minE"], res["sweeps"], res["reached"]) == (exp["minE"], exp["sweeps"], exp["reached"])
+
+
 @pytest.mark.parametrize("R", [4, 8, 12, 32])  # plane widths 1, 2, 1 (three planes), 4 words
 def test_sa_request_matches_sa_run_restarts(sg, R):
     S = 30
