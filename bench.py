@@ -10,7 +10,7 @@ sweep, the energy recompute and the optimality gap eps of the minimum energy.
 
 Prints one JSON line (rank 0).  `value` is attempts/s with the instances already
 resident on the device; `e2e` is the same metric with host couplings uploaded
-and results read back inside the timed region; `roofline` covers the sweep kernel;
+and results read back inside the timed region; `roofline` covers the dominant sweep kernel;
 `cpu_baseline` times the CPU oracle on a bounded sample on the host cores.
 For N > 1 each rank runs its own 16 instances (weak scaling, no collective on the
 data path); value = all ranks' attempts / max-over-ranks time.
@@ -118,12 +118,13 @@ def _l2_flusher(torch):
     return flush
 
 
-def _traffic_record():
-    """DRAM bytes per sweep launch from the committed ncu capture, if the sweep kernel's
-    sources are unchanged since it was taken (else None)."""
+def _traffic_record(name):
+    """DRAM bytes per launch of a sweep kernel from the committed ncu capture
+    profiles/<name>.traffic.json, if the kernel's sources are unchanged since it was
+    taken (else None)."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, "profiles", "sweep_bits_pt_L64_I16_K32.traffic.json")) as f:
+        with open(os.path.join(ROOT, "profiles", name + ".traffic.json")) as f:
             rec = json.load(f)
         h = hashlib.sha256()
         for src in rec["sources"]:
@@ -498,7 +499,7 @@ def batched_line(sg, args, torch, clocks_cls, local):
     torch.cuda.synchronize()
     sg.stats_enable(False)
     st = sg.stats_read(reset=True)
-    sw = st["sweep"]
+    sw = st["sweep_chunk"] if st["sweep_chunk"]["launches"] else st["sweep"]
     peak, peak_kind, sm_mhz = _peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     roof = None
@@ -552,14 +553,15 @@ def sa_line(sg, args, torch, clocks_cls, local, w=wl.SA_L16):
     sg.stats_enable(False)
     st = sg.stats_read(reset=True)
     ms = ev0.elapsed_time(ev1)
-    sw = st["sweep"]
+    cluster = st["sweep_chunk"]["launches"] > 0
+    sw = st["sweep_chunk"] if cluster else st["sweep"]
     peak, peak_kind, sm_mhz = _peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     roof = None
     if sw["launches"] and sw["device_ms"] > 0:
         roof = _roof(sw["units"] / (sw["device_ms"] / 1000.0), ATTEMPTS_PER_BLOCK, hbm_views(w.replicas),
                      _philox_blocks_per_s(sg), sms, sm_mhz, peak, peak_kind, traffic=None,
-                     kernel="sa_cluster_kernel" if sw["launches"] <= 4 * steps else "sweep_bits_kernel<SA>",
+                     kernel="sa_cluster_kernel" if cluster else "sweep_bits_kernel<SA>",
                      launch_ms=sw["device_ms"] / sw["launches"], share_of_step=sw["device_ms"] / ms,
                      note=f"working set {w.L ** 3 * 4 * ((w.replicas + 31) // 32) / 1e6:.3g} MB of spin words: "
                           "L2-resident, so HBM is not what limits it")
@@ -791,28 +793,38 @@ def main():
     value = ranks.job_rate(attempts_per_step, world, args.steps, ms_max)
     launches = sum(v["launches"] for v in st.values())
 
-    # roofline of the sweep kernel, from its launches' CUDA-event durations in the timed
-    # region: attempts per launch / mean launch duration against the integer roof, with
-    # the HBM view (algorithmic bytes per launch / duration) beside it
-    sw = st["sweep"]
+    # roofline of the dominant sweep kernel -- the kind that made most of the attempts: the
+    # row kernels (two launches per sweep) or the cluster form (one launch per chunk of up to
+    # 2000 sweeps; with 16 instances at L = 64, 15 run on clusters while the row kernels run
+    # the 16th beside them) -- from its launches' CUDA-event durations in the timed region:
+    # attempts per launch / mean launch duration against the integer roof, with the HBM
+    # view (algorithmic bytes per launch / duration) beside it
+    chunk_kernel = "pt_coop_kernel" if os.environ.get("SG_PT_COOP") == "1" else "pt_cluster_kernel"
+    parts = {}
+    for kind, kname in (("sweep", "sweep_bits_kernel<PT>"), ("sweep_chunk", chunk_kernel)):
+        p = st[kind]
+        if p["launches"] and p["device_ms"] > 0:
+            parts[kname] = {"launches": p["launches"], "attempts": p["units"], "device_ms": p["device_ms"],
+                            "attempts_per_s": p["units"] / (p["device_ms"] / 1000.0),
+                            "share_of_attempts": p["units"] / (attempts_per_step * args.steps)}
+    rows = st["sweep"]["units"] >= st["sweep_chunk"]["units"]
+    sw = st["sweep"] if rows else st["sweep_chunk"]
     peak, peak_kind, sm_mhz = _peaks()
     sms = torch.cuda.get_device_properties(local).multi_processor_count
     roof = None
     if sw["launches"] and sw["device_ms"] > 0:
         per_launch_s = sw["device_ms"] / 1000.0 / sw["launches"]
         attempts_per_launch = sw["units"] / sw["launches"]
-        # the row kernels launch twice per sweep; the cluster and cooperative forms once per
-        # chunk of up to 2000 sweeps (the traffic record covers the row kernel only)
-        rows = sw["launches"] >= 2 * S * args.steps
-        rec = _traffic_record() if rows else None
+        rec = _traffic_record("sweep_bits_pt_L64_I16_K32" if rows else "pt_cluster_L64_I15_K32")
         roof = _roof(attempts_per_launch / per_launch_s, ATTEMPTS_PER_BLOCK, hbm_views(WORK.temps),
                      _philox_blocks_per_s(sg), sms, sm_mhz, peak, peak_kind,
                      traffic=rec["traffic_bytes_per_launch"] if rec else None,
                      traffic_unit="DRAM bytes per launch (ncu)",
                      algorithmic_bytes_per_launch=attempts_per_launch * BYTES_PER_ATTEMPT,
-                     kernel="sweep_bits_kernel<PT>" if rows else "pt_cluster_kernel or pt_coop_kernel",
+                     kernel="sweep_bits_kernel<PT>" if rows else chunk_kernel,
                      launch_ms=1000 * per_launch_s,
-                     attempts_per_launch=attempts_per_launch, share_of_step=sw["device_ms"] / ms)
+                     attempts_per_launch=attempts_per_launch, share_of_step=sw["device_ms"] / ms,
+                     parts=parts)
 
     # end to end: host couplings in, results out, inside the timed region
     e2e = None

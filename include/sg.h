@@ -352,18 +352,25 @@ int32_t sg_energy_noalloc(int32_t L, const int8_t* J3_dev, const int8_t* spins_d
 /* Launch statistics (diagnostics; no counterpart in the paper).             */
 /* ------------------------------------------------------------------------ */
 
-#define SG_KERNEL_INIT 0      /* initial spins */
-#define SG_KERNEL_ENERGY 1    /* full energy recompute */
-#define SG_KERNEL_SWEEP 2     /* Metropolis sweep kernels (the hot path) */
-#define SG_KERNEL_EXCHANGE 3  /* PT exchange */
-#define SG_KERNEL_OTHER 4     /* layout conversion, checks, set-up */
-#define SG_KERNEL_KINDS 5
+#define SG_KERNEL_INIT 0         /* initial spins */
+#define SG_KERNEL_ENERGY 1       /* full energy recompute */
+#define SG_KERNEL_SWEEP 2        /* Metropolis sweep kernels, one or two launches per sweep
+                                    (the row kernels; fragment waves) */
+#define SG_KERNEL_EXCHANGE 3     /* PT exchange */
+#define SG_KERNEL_OTHER 4        /* layout conversion, checks, set-up */
+#define SG_KERNEL_SWEEP_CHUNK 5  /* Metropolis sweep kernels that run many sweeps per launch
+                                    with the lattice in shared memory (thread-block cluster,
+                                    cooperative and persistent batch forms) */
+#define SG_KERNEL_KINDS 6
 
+/* A PT batch may run both sweep kinds at once on different streams (some instances on
+ * clusters, the others through the row kernels), so device_ms of one kind is the time of
+ * that kind's launches alone. */
 typedef struct sg_kernel_stats {
     int64_t launches[SG_KERNEL_KINDS];  /* kernels launched by this library, per kind */
     double device_ms[SG_KERNEL_KINDS];  /* summed launch durations (only while timing is on) */
-    int64_t units[SG_KERNEL_KINDS];     /* work units processed: spin-flip attempts for
-                                           SG_KERNEL_SWEEP, spin sites x replicas otherwise */
+    int64_t units[SG_KERNEL_KINDS];     /* work units processed: spin-flip attempts for the
+                                           two sweep kinds, spin sites x replicas otherwise */
 } sg_kernel_stats;
 
 /* timing = 1: every later launch is bracketed by CUDA events recorded on the

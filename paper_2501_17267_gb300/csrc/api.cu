@@ -439,7 +439,7 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
     int C = unit_j && S > 0 && !(ck && atoi(ck) == 0) ? sa_cluster_blocks(I, L, Wn, (int64_t)I * (N / 2) * R) : 0;
     if (ck && atoi(ck) == 1 && unit_j && S > 0 && C == 0) C = sa_cluster_blocks(I, L, Wn, 0);
     if (C > 0) {
-        SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * N * R * S, st, [&] {
+        SG_RET(log.run(SG_KERNEL_SWEEP_CHUNK, (int64_t)I * N * R * S, st, [&] {
             return launch_sa_cluster(spins, j1p, kp, d_thr.as<uint32_t>(), I, L, Wn, R, S, C, st);
         }));
     } else if (S >= kGraphMinSweeps) {
@@ -611,6 +611,10 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
     std::vector<int> cplan;
     if (unit_j && Wn == 1 && S > 0 && pt_coop_wanted(I, L, K)) cplan = pt_coop_plan(I, L, K, &coop_blocks, &coop_smem);
     const int Ccl = cplan.empty() && unit_j && Wn == 1 && S > 0 ? pt_cluster_blocks(I, L, K) : 0;
+    int Mh = 0, side_sms = 0;
+    const int Chy = cplan.empty() && Ccl == 0 && unit_j && Wn == 1 && S >= kGraphMinSweeps
+                        ? pt_cluster_split(I, L, K, &Mh, &side_sms)
+                        : 0;
     if (!cplan.empty()) {
         DevBuf d_cflags, d_csums, d_cabort, d_carr, d_cpub, d_cplan;
         SG_RET(d_cflags.alloc(sizeof(int) * (size_t)coop_blocks, st));
@@ -628,7 +632,7 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
         const long long limit = wait_limit();
         for (int s0 = 0; s0 < S; s0 += kClusterChunkSweeps) {
             const int s1 = std::min(S, s0 + kClusterChunkSweeps);
-            SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * N * K * (s1 - s0), st, [&] {
+            SG_RET(log.run(SG_KERNEL_SWEEP_CHUNK, (int64_t)I * N * K * (s1 - s0), st, [&] {
                 return launch_pt_coop(spins, j1p, kp, d_thr.as<uint32_t>(), perm, inv, E, acc, minE, xd,
                                       d_flag.as<int>() + 1, cs, I, L, K, coop_blocks, coop_smem, s0, s1, limit, st);
             }));
@@ -640,11 +644,70 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
                                    d_xtail.as<uint32_t>()};
         for (int s0 = 0; s0 < S; s0 += kClusterChunkSweeps) {
             const int s1 = std::min(S, s0 + kClusterChunkSweeps);
-            SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * N * K * (s1 - s0), st, [&] {
+            SG_RET(log.run(SG_KERNEL_SWEEP_CHUNK, (int64_t)I * N * K * (s1 - s0), st, [&] {
                 return launch_pt_cluster(spins, j1p, kp, d_thr.as<uint32_t>(), perm, inv, E, acc, minE, xd,
                                          d_flag.as<int>() + 1, I, L, K, Ccl, s0, s1, aligned, st);
             }));
         }
+    } else if (Chy > 0) {
+        // Instances [0, Mh) on clusters, on a stream of the highest priority so that their
+        // blocks are placed first; instances [Mh, I) through the row kernels on the
+        // caller's stream, shaped for the SMs the clusters leave.  Every per-instance array
+        // of the second part starts Mh instances in.  The guard joins the side stream into
+        // the caller's on every way out, so nothing is freed while a cluster launch runs.
+        struct Side {
+            cudaStream_t own, side = nullptr;
+            cudaEvent_t fork = nullptr, join = nullptr;
+            ~Side()
+            {
+                if (side && join && cudaEventRecord(join, side) == cudaSuccess) cudaStreamWaitEvent(own, join, 0);
+                if (side) cudaStreamDestroy(side);
+                if (fork) cudaEventDestroy(fork);
+                if (join) cudaEventDestroy(join);
+            }
+        } sd{st};
+        int prio_lo = 0, prio_hi = 0;
+        SG_TRY_CUDA(cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi));
+        SG_TRY_CUDA(cudaEventCreateWithFlags(&sd.fork, cudaEventDisableTiming));
+        SG_TRY_CUDA(cudaEventCreateWithFlags(&sd.join, cudaEventDisableTiming));
+        SG_TRY_CUDA(cudaStreamCreateWithPriority(&sd.side, cudaStreamNonBlocking, prio_hi));
+        SG_TRY_CUDA(cudaEventRecord(sd.fork, st));
+        SG_TRY_CUDA(cudaStreamWaitEvent(sd.side, sd.fork, 0));
+        bool aligned = true;
+        for (int a = 0; a < Mh; ++a) aligned &= (reinterpret_cast<uintptr_t>(jp[I + a]) & 15u) == 0;
+        const ExchangeTablesDev xd{d_xtab.as<uint32_t>(), d_xoff.as<uint32_t>(), d_xlen.as<uint32_t>(),
+                                   d_xtail.as<uint32_t>()};
+        for (int s0 = 0; s0 < S; s0 += kClusterChunkSweeps) {
+            const int s1 = std::min(S, s0 + kClusterChunkSweeps);
+            SG_RET(log.run(SG_KERNEL_SWEEP_CHUNK, (int64_t)Mh * N * K * (s1 - s0), sd.side, [&] {
+                return launch_pt_cluster(spins, j1p, kp, d_thr.as<uint32_t>(), perm, inv, E, acc, minE, xd,
+                                         d_flag.as<int>() + 1, Mh, L, K, Chy, s0, s1, aligned, sd.side);
+            }));
+        }
+        const size_t o = (size_t)Mh;
+        const int Ir = I - Mh;
+        int8_t* rspins = spins + o * (size_t)N * Wn * 4;
+        ExchangeArgs xg = xa;
+        xg.keys = kp + o;
+        xg.E = E + o * Rp;
+        xg.rung_of_slot = perm + o * Rp;
+        xg.slot_of_rung = inv + o * K;
+        xg.accepts = acc + o * (K - 1);
+        xg.minE = minE + o;
+        xg.sweep_base = d_base.as<uint32_t>();
+        SG_RET(run_sweep_graphs(S, d_base.as<uint32_t>(), st, log, 2, (int64_t)Ir * N * K,
+                                [&](cudaStream_t cs, int c) -> int32_t {
+                                    bool fused = false;
+                                    for (int colour = 0; colour < 2; ++colour)
+                                        SG_RET(launch_sweep_rows_pt(rspins, j6p + o, j1p + o, kp + o,
+                                                                    d_thr.as<uint32_t>(), perm + o * Rp, E + o * Rp,
+                                                                    unit_j, Ir, L, Wn, K, (uint32_t)c, colour,
+                                                                    colour == 1 ? &xg : nullptr, done + o,
+                                                                    colour == 1 ? &fused : nullptr, cs,
+                                                                    d_base.as<uint32_t>(), nullptr, side_sms));
+                                    if (!fused) SG_RET(launch_pt_exchange(xg, Ir, (uint32_t)c, cs));
+                                    return SG_OK;
+                                }));
     } else if (S >= kGraphMinSweeps) {
         ExchangeArgs xg = xa;
         xg.sweep_base = d_base.as<uint32_t>();
@@ -661,7 +724,7 @@ int32_t run_pt_group(const std::vector<int>& members, const sg_instance* const* 
                                     return SG_OK;
                                 }));
     }
-    for (int s = 0; s < (S >= kGraphMinSweeps || Ccl > 0 || !cplan.empty() ? 0 : S); ++s) {
+    for (int s = 0; s < (S >= kGraphMinSweeps || Ccl > 0 || Chy > 0 || !cplan.empty() ? 0 : S); ++s) {
         bool fused = false;
         for (int c = 0; c < 2; ++c)
             SG_RET(log.run(SG_KERNEL_SWEEP, (int64_t)I * (N / 2) * K, st, [&] {

@@ -824,7 +824,7 @@ int32_t run_sa_planes(const std::vector<int>& members, const sg_instance* const*
         float ms = 0.f;
         if (timed) cudaEventElapsedTime(&ms, ev[0], ev[1]);
         stats_add(SG_KERNEL_INIT, 1, cells, 0.0);
-        stats_add(SG_KERNEL_SWEEP, 1, attempts, (double)ms);
+        stats_add(SG_KERNEL_SWEEP_CHUNK, 1, attempts, (double)ms);
         stats_add(SG_KERNEL_ENERGY, 1, cells, 0.0);
         stats_add(SG_KERNEL_OTHER, 1, cells, 0.0);
     }

@@ -328,6 +328,67 @@ int pt_cluster_blocks(int I, int L, int K)
     return 0;
 }
 
+// A batch with more instances than clusters fit at once: the first M instances on clusters
+// (one wave), the other I - M through the row kernels on the SMs the clusters leave, both
+// at the same time.  With the rates above, M minimises the longer of the two parts' times
+// per sweep, and the split is taken when that beats the row kernels on the whole GPU.  At
+// L = 64 with 16 instances of 32 temperatures: 15 clusters of 8 blocks on 120 SMs, one
+// instance on the other 32.  Knob SG_PT_HYBRID = 0 turns the split off; SG_PT_CLUSTER = 0
+// turns off every cluster form.
+int pt_cluster_split(int I, int L, int K, int* M, int* side_sms)
+{
+    *M = 0;
+    *side_sms = 0;
+    const char* e = getenv("SG_PT_HYBRID");
+    if (e && atoi(e) == 0) return 0;
+    const char* c = getenv("SG_PT_CLUSTER");
+    if ((c && atoi(c) == 0) || K > 32 || K < 1 || L < 2 || (L & 1) || I < 2) return 0;
+    int dev = 0, smem = 0, sms = 1, clock_khz = 2070000;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev);
+    const double hz = 1e3 * (double)clock_khz;
+    const double work = (double)L * L * L * K;
+    const double t_rows = 10e-6 + I * work / (sms * 6.2 * hz);
+    double best = 0.95 * t_rows;
+    int bestC = 0;
+    for (int C = 8; C >= 1; --C) {
+        if (L % C) continue;
+        const size_t bytes = dyn_smem(L, C);
+        if (bytes + 16 * 1024 > (size_t)smem) continue;
+        if (cudaFuncSetAttribute(pt_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        cudaLaunchAttribute attr[1];
+        cudaLaunchConfig_t cfg = cluster_config(L, C, 1, attr);
+        int active = 0, per_sm = 0;
+        if (cudaOccupancyMaxActiveClusters(&active, pt_cluster_kernel, &cfg) != cudaSuccess ||
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pt_cluster_kernel, kThreads, bytes) !=
+                cudaSuccess) {
+            cudaGetLastError();
+            continue;
+        }
+        if (active >= I || active < 1 || per_sm < 1) continue;  // one wave: pt_cluster_blocks decides
+        const double t_cluster = 4e-6 + work / (C * 7.9 * hz);
+        for (int m = active; m >= 1; --m) {
+            const int left = sms - (m * C + per_sm - 1) / per_sm;
+            if (left < 1) continue;
+            const double t_side = 10e-6 + (I - m) * work / (left * 6.2 * hz);
+            const double t = t_cluster > t_side ? t_cluster : t_side;
+            if (t < best) {
+                best = t;
+                bestC = C;
+                *M = m;
+                *side_sms = left;
+            }
+        }
+    }
+    return bestC;
+}
+
 int32_t launch_pt_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKeys* keys, const uint32_t* thr,
                           uint8_t* rung_of_slot, uint8_t* slot_of_rung, int32_t* E, unsigned long long* accepts,
                           int32_t* minE, const ExchangeTablesDev& xt, int* status, int I, int L, int K, int C,

@@ -182,13 +182,14 @@ int32_t launch_sweep_rows_sa(int8_t* spins, const uint2* const* j6_ptrs,
 // PT: the colour-0 launch clears E [I][32*Wn] and the colour-1 launch sums every slot's
 // energy afresh.  xch != nullptr: the colour-1 launch also performs the exchange (last
 // block per instance); *fused reports whether it did.  done: [I] zeroed counters.
-// status: unused (no launch of this kernel waits).
+// status: unused (no launch of this kernel waits).  sms > 0: the launch shares the GPU
+// with other work and is shaped for about that many SMs.
 int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint8_t* const* j1_ptrs, const RunKeys* keys,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
                              const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st,
-                             const uint32_t* sweep_base = nullptr, int* status = nullptr);
+                             const uint32_t* sweep_base = nullptr, int* status = nullptr, int sms = 0);
 // cluster.cu: SA of small lattices, all sweeps in one launch, one thread-block cluster of C
 // blocks per (word, instance); sa_cluster_blocks gives C, or 0 when the row kernel should
 // run instead (long half sweeps, slabs too large, or more clusters than fit at once).
@@ -218,6 +219,10 @@ struct ExchangeTablesDev {
     const uint32_t *tab, *off, *len, *tail;
 };
 int pt_cluster_blocks(int I, int L, int K);
+// A batch too large for one wave of clusters but faster on them: C for the first *M
+// instances on clusters (M < I, all resident at once), the others through the row kernels
+// on the side_sms SMs the clusters leave; or 0.
+int pt_cluster_split(int I, int L, int K, int* M, int* side_sms);
 // ptcoop.cu: the same on one cooperative grid, each instance's rows split into row blocks
 // held in shared memory (one block per SM).  pt_coop_plan gives the per-block plan
 // (instance, rank, first row, rows; then per instance first block and block count; then

@@ -435,7 +435,8 @@ struct SweepShape {
     int G, rows_per_thread;
 };
 
-SweepShape sweep_shape(int I, int L, int Wn, int bps)
+// sms_hint > 0: the launch shares the GPU and gets about that many SMs
+SweepShape sweep_shape(int I, int L, int Wn, int bps, int sms_hint)
 {
     SweepShape sh;
     sh.G = Wn < 256 ? Wn : 256;
@@ -451,6 +452,7 @@ SweepShape sweep_shape(int I, int L, int Wn, int bps)
     int dev = 0, sms = 148;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms_hint > 0 && sms_hint < sms) sms = sms_hint;
     // rows per thread: about bps blocks per SM (as many as are resident), so that each
     // block fills its threshold tables and reduces its energies once for many rows
     long long rpt = ((long long)LL * I + (long long)TY * bps * sms - 1) / ((long long)TY * (long long)bps * sms);
@@ -464,10 +466,10 @@ SweepShape sweep_shape(int I, int L, int Wn, int bps)
 }
 
 template <bool PT>
-int32_t launch_rows(SweepArgs a, int I, bool unit_j, bool xch, bool* fused, cudaStream_t st)
+int32_t launch_rows(SweepArgs a, int I, bool unit_j, bool xch, bool* fused, cudaStream_t st, int sms_hint = 0)
 {
     const bool energy = PT && a.colour == 1;
-    const SweepShape sh = sweep_shape(I, a.L, a.Wn, PT && !energy ? SG_SWEEP_MINB : SG_SWEEP_MINB_E);
+    const SweepShape sh = sweep_shape(I, a.L, a.Wn, PT && !energy ? SG_SWEEP_MINB : SG_SWEEP_MINB_E, sms_hint);
     a.G = sh.G;
     a.rows_per_thread = sh.rows_per_thread;
     a.Lmagic = (uint32_t)((0x100000000ull + (uint64_t)a.L - 1) / (uint64_t)a.L);
@@ -539,7 +541,7 @@ int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const uint32_t* thr_rungs, const uint8_t* rung_of_slot, int32_t* E,
                              bool unit_j, int I, int L, int Wn, int K, uint32_t sweep, int colour,
                              const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st,
-                             const uint32_t* sweep_base, int* /*status*/)
+                             const uint32_t* sweep_base, int* /*status*/, int sms)
 {
     SweepArgs a{};
     a.spins = reinterpret_cast<uint32_t*>(spins);
@@ -557,7 +559,7 @@ int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
     if (xch) a.x = *xch;
     a.done = done;
     a.sweep_base = sweep_base;
-    return launch_rows<true>(a, I, unit_j, xch != nullptr && colour == 1, fused, st);
+    return launch_rows<true>(a, I, unit_j, xch != nullptr && colour == 1, fused, st, sms);
 }
 
 }  // namespace sg

@@ -70,12 +70,14 @@ class FragmentResult(ctypes.Structure):
     _fields_ = [("E", ctypes.c_int64), ("eps", ctypes.c_double), ("spins", _P), ("spins_mem", ctypes.c_int32)]
 
 
-KERNEL_KINDS = ("init", "energy", "sweep", "exchange", "other")
+# the SG_KERNEL_* kinds of sg.h, in order ("sweep_chunk": many sweeps per launch)
+KERNEL_KINDS = ("init", "energy", "sweep", "exchange", "other", "sweep_chunk")
+_NK = len(KERNEL_KINDS)
 
 
 class KernelStats(ctypes.Structure):
-    _fields_ = [("launches", ctypes.c_int64 * 5), ("device_ms", ctypes.c_double * 5),
-                ("units", ctypes.c_int64 * 5)]
+    _fields_ = [("launches", ctypes.c_int64 * _NK), ("device_ms", ctypes.c_double * _NK),
+                ("units", ctypes.c_int64 * _NK)]
 
 
 class ServerConfig(ctypes.Structure):

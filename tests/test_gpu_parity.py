@@ -429,6 +429,30 @@ def test_pt_cluster_kernel_chunks(sg, monkeypatch):
     assert a["minE"] == b["minE"]
 
 
+@pytest.mark.parametrize("I,K,S", [(16, 32, 30), (17, 17, 20)])
+def test_pt_split_between_clusters_and_rows_equals_row_kernels(sg, monkeypatch, I, K, S):
+    """More L = 64 instances than this GPU keeps clusters of 8 resident at once: the first
+    ones run on clusters while the row kernels run the others beside them on a second
+    stream (every per-instance array of the second part offset by the first part's size).
+    Identical to the row kernels alone; the launch statistics show both kinds ran."""
+    L = 64
+    insts = [sg.Instance.create(L, 9100 + k) for k in range(I)]
+    params = [dict(temps=K, sweeps=S, beta_min=0.2, beta_max=3.0, seed=47, instance_id=k) for k in range(I)]
+    for knob in ("SG_PT_CLUSTER", "SG_PT_HYBRID", "SG_PT_COOP"):
+        monkeypatch.delenv(knob, raising=False)
+    sg.stats_read(reset=True)
+    a = sg.pt_run_batch(insts, params, spins="host")
+    st = sg.stats_read(reset=True)
+    on_clusters = st["sweep_chunk"]["units"] / (I * K * L ** 3 * S)
+    assert st["sweep"]["launches"] > 0 and 0.5 < on_clusters < 1.0, st
+    monkeypatch.setenv("SG_PT_CLUSTER", "0")
+    b = sg.pt_run_batch(insts, params, spins="host")
+    for x, y in zip(a, b):
+        for k in ("spins", "E", "perm", "accepts"):
+            assert np.array_equal(x[k], y[k]), k
+        assert x["minE"] == y["minE"]
+
+
 # --------------------------------------------------------------------------- PT on one cooperative grid
 
 @pytest.mark.parametrize("L,K,S,I", [(8, 8, 20, 1), (16, 32, 12, 3), (32, 17, 10, 4), (48, 32, 4, 8),

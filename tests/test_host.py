@@ -33,6 +33,20 @@ def test_exports_every_declared_symbol(sg):
         assert hasattr(lib, name), name
 
 
+def test_kernel_kinds_follow_the_header(sg):
+    """The binding's launch-statistics kinds are the header's SG_KERNEL_* in index order,
+    and reading the counters (host state only) fills every kind."""
+    text = open(os.path.join(ROOT, "include", "sg.h")).read()
+    defs = {name: int(v) for name, v in re.findall(r"#define SG_KERNEL_(\w+) (\d+)", text)}
+    n = defs.pop("KINDS")
+    assert sorted(defs.values()) == list(range(n)) and len(sg.KERNEL_KINDS) == n
+    for name, idx in defs.items():
+        assert sg.KERNEL_KINDS[idx] == name.lower()
+    st = sg.stats_read(reset=True)
+    assert list(st) == list(sg.KERNEL_KINDS)
+    assert all(v["launches"] == 0 and v["units"] == 0 for v in st.values())
+
+
 @pytest.mark.parametrize("L", [2, 4, 6, 12, 16])
 @pytest.mark.parametrize("cp,gauge", [(wl.UNIFORM, True), ((0, 0, 1), True), ((0.3, 0.7, 0), False),
                                       ((0.5, 0, 0.5), True)])
