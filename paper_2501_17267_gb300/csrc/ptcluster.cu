@@ -206,11 +206,15 @@ __global__ void __launch_bounds__(kThreads, 1) pt_cluster_kernel(const PtcArgs a
     // one half sweep of `colour` over this block's slab: items q = tid, tid + kThreads, ...
     auto half = [&](const int colour, uint32_t sweep) {
         pts::Updater u(sh, slab, s_ties, key, valid, sweep, tid, colour == 1);
+        int m = 0;
         for (int q = tid; q < items; q += kThreads) {
             pts::Work w;
             fetch(q, colour, w, u);
             u.update(w);
-            if (uniform) u.maybe_resolve();
+            if (uniform && ++m == pts::kCheckEvery) {
+                m = 0;
+                u.maybe_resolve();
+            }
         }
         u.resolve();
         if (colour == 1) {
