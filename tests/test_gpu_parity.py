@@ -429,14 +429,15 @@ def test_pt_cluster_kernel_chunks(sg, monkeypatch):
     assert a["minE"] == b["minE"]
 
 
-@pytest.mark.parametrize("I,K,S", [(16, 32, 30), (17, 17, 20)])
-def test_pt_split_between_clusters_and_rows_equals_row_kernels(sg, monkeypatch, I, K, S):
-    """More L = 64 instances than this GPU keeps clusters of 8 resident at once: the first
-    ones run on clusters while the row kernels run the others beside them on a second
-    stream (every per-instance array of the second part offset by the first part's size).
-    Identical to the row kernels alone; the launch statistics show both kinds ran."""
-    L = 64
-    insts = [sg.Instance.create(L, 9100 + k) for k in range(I)]
+@pytest.mark.parametrize("L,I,K,S", [(64, 16, 32, 30), (64, 17, 17, 20), (48, 16, 32, 25), (64, 16, 32, 2100)])
+def test_pt_split_between_clusters_and_rows_equals_row_kernels(sg, monkeypatch, L, I, K, S):
+    """More instances than this GPU keeps clusters of 8 resident at once: the first ones
+    run on clusters while the row kernels run the others beside them on a second stream
+    (every per-instance array of the second part offset by the first part's size).
+    Identical to the row kernels alone; the launch statistics show both kinds ran.  Slabs
+    of 8 planes (L = 64) and 6 (L = 48), a ragged K, and a run of two cluster launches
+    (chunks of 2000 sweeps) beside 21 row-kernel graphs."""
+    insts = [sg.Instance.create(L, 9100 + 100 * L + k) for k in range(I)]
     params = [dict(temps=K, sweeps=S, beta_min=0.2, beta_max=3.0, seed=47, instance_id=k) for k in range(I)]
     for knob in ("SG_PT_CLUSTER", "SG_PT_HYBRID", "SG_PT_COOP"):
         monkeypatch.delenv(knob, raising=False)
