@@ -306,8 +306,10 @@ int pt_cluster_blocks(int I, int L, int K)
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     cudaDeviceGetAttribute(&clock_khz, cudaDevAttrClockRate, dev);
     const double hz = 1e3 * (double)clock_khz;
+    const char* fc = getenv("SG_PT_CLUSTER_C");  // tuning knob: force C (when it divides L and fits)
+    const int forced = fc ? atoi(fc) : 0;
     for (int C = 8; C >= 1; --C) {
-        if (L % C) continue;
+        if (L % C || (forced > 0 && C != forced)) continue;
         const size_t bytes = dyn_smem(L, C);
         if (bytes + 16 * 1024 > (size_t)smem) continue;
         if (cudaFuncSetAttribute(pt_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
@@ -315,7 +317,7 @@ int pt_cluster_blocks(int I, int L, int K)
             cudaGetLastError();
             continue;
         }
-        if (knob == 1) return C;
+        if (knob == 1 || forced > 0) return C;
         cudaLaunchAttribute attr[1];
         cudaLaunchConfig_t cfg = cluster_config(L, C, 1, attr);
         int active = 0;
