@@ -396,12 +396,14 @@ def test_planes_in_shared_memory_equal_global(sg, monkeypatch, L, R, S):
 # --------------------------------------------------------------------------- PT on clusters
 
 @pytest.mark.parametrize("L,K,S,I", [(2, 3, 10, 1), (4, 5, 30, 2), (6, 32, 7, 1), (8, 8, 20, 1),
-                                     (12, 17, 10, 1), (16, 32, 15, 3), (64, 32, 5, 2)])
+                                     (12, 17, 10, 1), (16, 32, 15, 3), (64, 32, 5, 2), (4, 1, 12, 2),
+                                     (8, 2, 16, 3)])
 def test_pt_cluster_kernel_equals_row_kernels_and_oracle(sg, monkeypatch, L, K, S, I):
     """PT with every sweep of a chunk in one launch, one thread-block cluster per instance
     holding the lattice in shared memory (exchange decided in every block from the
     cluster's energy sums): identical to the row kernels and to the oracle.  One z-plane
-    per block (L = 2, 6), uneven half rows (L = 12), several instances, ragged K."""
+    per block (L = 2, 6), uneven half rows (L = 12), several instances, ragged K, one rung
+    (no exchange pair) and two."""
     insts = [sg.Instance.create(L, 8800 + 10 * L + k) for k in range(I)]
     params = [dict(temps=K, sweeps=S, beta_min=0.2, beta_max=3.0, seed=41, instance_id=k) for k in range(I)]
     monkeypatch.setenv("SG_PT_CLUSTER", "1")
@@ -429,7 +431,8 @@ def test_pt_cluster_kernel_chunks(sg, monkeypatch):
     assert a["minE"] == b["minE"]
 
 
-@pytest.mark.parametrize("L,I,K,S", [(64, 16, 32, 30), (64, 17, 17, 20), (48, 16, 32, 25), (64, 16, 32, 2100)])
+@pytest.mark.parametrize("L,I,K,S", [(64, 16, 32, 30), (64, 17, 17, 20), (48, 16, 32, 25), (64, 16, 32, 2100),
+                                     (64, 16, 1, 20)])
 def test_pt_split_between_clusters_and_rows_equals_row_kernels(sg, monkeypatch, L, I, K, S):
     """More instances than this GPU keeps clusters of 8 resident at once: the first ones
     run on clusters while the row kernels run the others beside them on a second stream
