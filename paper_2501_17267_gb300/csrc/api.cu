@@ -436,11 +436,13 @@ int32_t run_sa_group(const std::vector<int>& members, const sg_instance* const* 
     // Small lattices with unit couplings: every sweep in one launch, a word per thread-block
     // cluster (cluster.cu).  Knob SG_SA_CLUSTER = 0 / 1 disables or forces it.
     const char* ck = getenv("SG_SA_CLUSTER");
-    int C = unit_j && S > 0 && !(ck && atoi(ck) == 0) ? sa_cluster_blocks(I, L, Wn, (int64_t)I * (N / 2) * R) : 0;
-    if (ck && atoi(ck) == 1 && unit_j && S > 0 && C == 0) C = sa_cluster_blocks(I, L, Wn, 0);
+    int threads = 256;
+    int C = unit_j && S > 0 && !(ck && atoi(ck) == 0) ? sa_cluster_blocks(I, L, Wn, (int64_t)I * (N / 2) * R, &threads)
+                                                      : 0;
+    if (ck && atoi(ck) == 1 && unit_j && S > 0 && C == 0) C = sa_cluster_blocks(I, L, Wn, 0, &threads);
     if (C > 0) {
         SG_RET(log.run(SG_KERNEL_SWEEP_CHUNK, (int64_t)I * N * R * S, st, [&] {
-            return launch_sa_cluster(spins, j1p, kp, d_thr.as<uint32_t>(), I, L, Wn, R, S, C, st);
+            return launch_sa_cluster(spins, j1p, kp, d_thr.as<uint32_t>(), I, L, Wn, R, S, C, threads, st);
         }));
     } else if (S >= kGraphMinSweeps) {
         // the kernel reads row *base + c of the whole [S][kThrRow] table

@@ -15,6 +15,7 @@
 #include <stdlib.h>
 
 #include <algorithm>
+#include <cstdint>
 
 #include "metropolis.cuh"
 #include "philox.cuh"
@@ -25,7 +26,7 @@ namespace cg = cooperative_groups;
 namespace sg {
 namespace {
 
-constexpr int kBlock = 256;  // single runs: about one word per thread per half sweep at L = 16
+// Single runs: 256 or 512 threads a block, chosen with the cluster size (sa_cluster_blocks).
 // Batches (planes of up to L = 48 per cluster, tens of words per thread per half sweep):
 // 768 threads per block measured fastest on the 512-instance uneven batch -- 1.95 s per
 // step against 2.10 at 512, 1.97 at 1024 and 2.89 at 256 -- although at 85 registers a
@@ -205,11 +206,12 @@ __device__ __forceinline__ void anneal_plane(const PlaneRun& p, const int C, uin
     cluster.sync();  // no block goes on (or leaves) while another may still read its slab
 }
 
-__global__ void __launch_bounds__(kBlock) sa_cluster_kernel(const ClusterArgs a)
+template <int NT>
+__global__ void __launch_bounds__(NT) sa_cluster_kernel(const ClusterArgs a)
 {
     extern __shared__ uint32_t slab[];  // [L / C][L][L] words of this block's slab, storage order
-    __shared__ uint4 s_ties[(kBlock / 32) * kTieCap * 2];  // per warp: {site, local, -, tie}, {c0, c1, word, -}
-    __shared__ int s_tie_n[kBlock / 32];
+    __shared__ uint4 s_ties[(NT / 32) * kTieCap * 2];  // per warp: {site, local, -, tie}, {c0, c1, word, -}
+    __shared__ int s_tie_n[NT / 32];
     const int w = blockIdx.y, inst = blockIdx.z;
     PlaneRun p;
     p.g = a.spins + (size_t)inst * a.L * a.L * a.L * a.Wn + w;
@@ -223,7 +225,7 @@ __global__ void __launch_bounds__(kBlock) sa_cluster_kernel(const ClusterArgs a)
     p.s_begin = 0;
     p.s_end = a.S;
     p.Hmagic = a.Hmagic;
-    anneal_plane<kBlock>(p, a.C, slab, s_ties, s_tie_n);
+    anneal_plane<NT>(p, a.C, slab, s_ties, s_tie_n);
 }
 
 // Persistent form for batches (batch.cu's planes of one word, [N][1]): clusters take
@@ -272,45 +274,76 @@ __global__ void __launch_bounds__(kListBlock, 1) sa_cluster_list_kernel(const Pl
 // run is better served by the row kernel: a divisor C <= 8 of L whose slab fits shared
 // memory, the largest for which all I * Wn clusters are resident at once (as the driver
 // reports for this kernel, so that the run is one wave).  Knob SG_SA_CLUSTER_C forces C.
-int sa_cluster_blocks(int I, int L, int Wn, int64_t half_sweep_attempts)
+const void* sa_cluster_fn(int threads)
 {
+    return threads == 512 ? (const void*)sa_cluster_kernel<512> : (const void*)sa_cluster_kernel<256>;
+}
+
+int sa_cluster_blocks(int I, int L, int Wn, int64_t half_sweep_attempts, int* threads)
+{
+    *threads = 256;
     if (half_sweep_attempts > ((int64_t)1 << 24)) return 0;  // long half sweeps: the row kernel
-    int dev = 0, smem = 0;
+    int dev = 0, smem = 0, sms = 1;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&smem, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int64_t clusters = (int64_t)I * Wn;
     const char* e = getenv("SG_SA_CLUSTER_C");
     const int forced = e ? atoi(e) : 0;
-    for (int C = 8; C >= 1; --C) {
-        if (L % C || (forced && C != forced)) continue;
-        const size_t bytes = (size_t)(L / C) * L * L * 4;
-        if (bytes + 12 * 1024 > (size_t)smem) continue;
-        if (forced) return C;
-        if (bytes > 48 * 1024 &&
-            cudaFuncSetAttribute(sa_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes) !=
-                cudaSuccess) {
-            cudaGetLastError();
-            continue;
+    const char* et = getenv("SG_SA_CLUSTER_THREADS");
+    const int forced_t = et ? atoi(et) : 0;
+    // For each block size, the largest C whose clusters are all resident at once (one wave);
+    // of the two, the one with fewer rounds of items a thread times blocks an SM runs (a
+    // half sweep's length), ties to 256 threads.  Measured at L = 16 with 1024 replicas:
+    // 512 threads at C = 4 (one block an SM) 3.80 ms a run against 3.93 for 256 threads at
+    // C = 8 (two blocks on most SMs); one cluster at L = 4: 1.98 ms with 256, 2.03 with 512.
+    int bestC = 0, bestT = 256;
+    int64_t best_cost = INT64_MAX;
+    for (const int t : {256, 512}) {
+        if (forced_t && t != forced_t) continue;
+        for (int C = 8; C >= 1; --C) {
+            if (L % C || (forced && C != forced)) continue;
+            const size_t bytes = (size_t)(L / C) * L * L * 4;
+            // static shared memory: t / 32 warps' tie queues (32 entries of 32 bytes) and more
+            if (bytes + (size_t)t * 32 + 4096 > (size_t)smem) continue;
+            if (!forced) {
+                if (bytes > 48 * 1024 && cudaFuncSetAttribute(sa_cluster_fn(t), cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                              (int)bytes) != cudaSuccess) {
+                    cudaGetLastError();
+                    continue;
+                }
+                cudaLaunchConfig_t cfg{};
+                cfg.gridDim = dim3(C, (unsigned)std::min<int64_t>(clusters, 65535), 1);
+                cfg.blockDim = dim3(t, 1, 1);
+                cfg.dynamicSmemBytes = bytes;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = C;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                int active = 0;
+                if (cudaOccupancyMaxActiveClusters(&active, sa_cluster_fn(t), &cfg) != cudaSuccess) {
+                    cudaGetLastError();
+                    continue;
+                }
+                if (active < clusters) continue;
+            }
+            const int64_t items = (int64_t)(L / C) * L * (L / 2);  // sites of one colour a block
+            const int64_t rounds = (items + t - 1) / t;
+            const int64_t per_sm = (clusters * C + sms - 1) / sms;
+            const int64_t cost = rounds * per_sm;
+            if (cost < best_cost) {
+                best_cost = cost;
+                bestC = C;
+                bestT = t;
+            }
+            break;
         }
-        cudaLaunchConfig_t cfg{};
-        cfg.gridDim = dim3(C, (unsigned)std::min<int64_t>(clusters, 65535), 1);
-        cfg.blockDim = dim3(kBlock, 1, 1);
-        cfg.dynamicSmemBytes = bytes;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeClusterDimension;
-        attr[0].val.clusterDim.x = C;
-        attr[0].val.clusterDim.y = 1;
-        attr[0].val.clusterDim.z = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        int active = 0;
-        if (cudaOccupancyMaxActiveClusters(&active, sa_cluster_kernel, &cfg) != cudaSuccess) {
-            cudaGetLastError();
-            continue;
-        }
-        if (active >= clusters) return C;
     }
-    return 0;
+    *threads = bestT;
+    return bestC;
 }
 
 namespace {
@@ -389,8 +422,12 @@ int32_t launch_sa_cluster_planes(const Plane* d_planes, const int* d_order, int 
 }
 
 int32_t launch_sa_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKeys* keys, const uint32_t* thr,
-                          int I, int L, int Wn, int R, int S, int C, cudaStream_t st)
+                          int I, int L, int Wn, int R, int S, int C, int threads, cudaStream_t st)
 {
+    if (threads != 256 && threads != 512) {
+        set_error("sa_cluster_kernel: %d threads a block (256 or 512)", threads);
+        return SG_EINVAL;
+    }
     ClusterArgs a{};
     a.spins = reinterpret_cast<uint32_t*>(spins);
     a.j1_ptrs = j1_ptrs;
@@ -405,14 +442,15 @@ int32_t launch_sa_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const Ru
     a.Hmagic = H == 1 ? 0u : (uint32_t)((0x100000000ull + (uint64_t)H - 1) / (uint64_t)H);
     const size_t smem = (size_t)(L / C) * L * L * 4;
     if (smem > 48 * 1024 &&
-        cudaFuncSetAttribute(sa_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess) {
+        cudaFuncSetAttribute(sa_cluster_fn(threads), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+            cudaSuccess) {
         cudaGetLastError();
         set_error("sa_cluster_kernel: cannot use %zu bytes of shared memory", smem);
         return SG_ECUDA;
     }
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(C, Wn, I);
-    cfg.blockDim = dim3(kBlock, 1, 1);
+    cfg.blockDim = dim3(threads, 1, 1);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -422,7 +460,8 @@ int32_t launch_sa_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const Ru
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    const cudaError_t e = cudaLaunchKernelEx(&cfg, sa_cluster_kernel, a);
+    const cudaError_t e = threads == 512 ? cudaLaunchKernelEx(&cfg, sa_cluster_kernel<512>, a)
+                                         : cudaLaunchKernelEx(&cfg, sa_cluster_kernel<256>, a);
     if (e != cudaSuccess) {
         cudaGetLastError();
         set_error("sa_cluster_kernel launch failed: %s", cudaGetErrorString(e));

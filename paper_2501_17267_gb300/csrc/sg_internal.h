@@ -191,12 +191,13 @@ int32_t launch_sweep_rows_pt(int8_t* spins, const uint2* const* j6_ptrs,
                              const ExchangeArgs* xch, unsigned* done, bool* fused, cudaStream_t st,
                              const uint32_t* sweep_base = nullptr, int* status = nullptr, int sms = 0);
 // cluster.cu: SA of small lattices, all sweeps in one launch, one thread-block cluster of C
-// blocks per (word, instance); sa_cluster_blocks gives C, or 0 when the row kernel should
-// run instead (long half sweeps, slabs too large, or more clusters than fit at once).
-int sa_cluster_blocks(int I, int L, int Wn, int64_t half_sweep_attempts);
+// blocks per (word, instance); sa_cluster_blocks gives C and the threads a block (256 or
+// 512), or 0 when the row kernel should run instead (long half sweeps, slabs too large, or
+// more clusters than fit at once).
+int sa_cluster_blocks(int I, int L, int Wn, int64_t half_sweep_attempts, int* threads);
 int32_t launch_sa_cluster(int8_t* spins, const uint8_t* const* j1_ptrs, const RunKeys* keys,
                           const uint32_t* thr /* [S][kThrRow] */, int I, int L, int Wn, int R, int S, int C,
-                          cudaStream_t st);
+                          int threads, cudaStream_t st);
 // The persistent cluster form for batches of one-word planes (batch.cu): C for planes of
 // sides Ls (every side a multiple of C, the slab of the largest fitting), or 0.
 int sa_cluster_list_blocks(const int* Ls, int n, int max_L);

@@ -240,6 +240,26 @@ def test_sa_cluster_kernel_equals_row_kernel_and_oracle(sg, monkeypatch, L, R, S
     assert np.array_equal(a["E"][reps], oE)
 
 
+@pytest.mark.parametrize("L,R,S", [(16, 1024, 25), (8, 64, 30), (12, 100, 20), (32, 64, 6), (4, 8, 40)])
+def test_sa_cluster_block_sizes_agree(sg, monkeypatch, L, R, S):
+    """The single-run cluster kernel with 256 and with 512 threads a block (each with the
+    largest cluster size that fits one wave; the library picks one of the two by the
+    items a thread updates and the blocks an SM runs) and the row kernel give the same
+    spins and energies."""
+    inst = sg.Instance.create(L, 8100 + L)
+    monkeypatch.setenv("SG_SA_CLUSTER", "1")
+    runs = []
+    for t in ("256", "512"):
+        monkeypatch.setenv("SG_SA_CLUSTER_THREADS", t)
+        runs.append(sg.sa_run(inst, R, S, 0.1, 3.0, "linear", 41, 3, spins="host"))
+    monkeypatch.delenv("SG_SA_CLUSTER_THREADS")
+    runs.append(sg.sa_run(inst, R, S, 0.1, 3.0, "linear", 41, 3, spins="host"))
+    monkeypatch.setenv("SG_SA_CLUSTER", "0")
+    runs.append(sg.sa_run(inst, R, S, 0.1, 3.0, "linear", 41, 3, spins="host"))
+    for other in runs[1:]:
+        assert np.array_equal(runs[0]["spins"], other["spins"]) and np.array_equal(runs[0]["E"], other["E"])
+
+
 def test_runs_longer_than_one_graph_chunk(sg):
     """Runs of 16 or more sweeps go through CUDA graphs of up to 100 sweeps with the
     sweep index on the device: 230 and 251 sweeps end in a shorter last chunk."""
